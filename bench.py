@@ -1,0 +1,369 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 randomized ID: one step = one whole ID (sketch,
+pivoted QR, triangular solve, probe error estimate) of the 32 GiB complex128
+matrix m = 262144, n = 8192 (k = 200, l = 208), inputs resident in HBM.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank decomposes
+its own matrix (independent problems, no collective on the data path) and
+the value is the total over ranks (weak scaling).  --impl reference times
+the CPU oracle on a bounded column slab of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 latency"
+# FP64 FMA peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA/clock
+# x 2 flops x 2.07 GHz maximum SM clock (a DFMA probe measured 1.20 TF/s).
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+NVSMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={NVSMI_FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, flag in zip(names, parts[5:9]):
+                    if flag.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def init_dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if _cuda_ok() else "gloo")
+    return world, rank, local
+
+
+def _cuda_ok():
+    import torch
+    return torch.cuda.is_available()
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle on a bounded column slab (the cpu_baseline and --impl reference)
+# ---------------------------------------------------------------------------
+def oracle_slab_setup(cfg, A_slab_host):
+    import oracle
+    Omega = oracle.gaussian_test_matrix(cfg.l, cfg.m, cfg.seed)   # untimed: plan creation
+    probes = oracle.probe_matrix(A_slab_host.shape[1], 8, 1)
+    return Omega, probes
+
+
+def oracle_slab_step(cfg, Omega, A_slab, probes):
+    import oracle
+    Y = oracle.randomize(Omega, A_slab)
+    R, tau, perm = oracle.qr_select(Y, cfg.k)
+    T = oracle.factor_r(R[:cfg.k, :cfg.k], R[:cfg.k, cfg.k:])
+    est, upper, _ = oracle.error_estimate(A_slab, perm, T, probes)
+    return est
+
+
+def cpu_cores():
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var):
+            return int(os.environ[var])
+    return os.cpu_count()
+
+
+def run_reference(args, cfg, world, rank):
+    """The oracle as it stands, on host cores, on a column slab of the workload."""
+    if rank != 0:
+        return
+    import numpy as np
+    import torch
+    import synth
+    ns = args.ref_cols
+    if _cuda_ok():
+        import synth.device
+        A = synth.device.device_matrix(cfg)
+        A_slab = np.asfortranarray(A[:, :ns].cpu().numpy())
+        del A
+        torch.cuda.empty_cache()
+    else:   # no GPU: the same recipe on the host at the slab's width
+        small = synth.scaled_config(cfg, cfg.m, ns)
+        A_slab = synth.host_matrix(small)
+    Omega, probes = oracle_slab_setup(cfg, A_slab)
+    for _ in range(args.warmup):
+        oracle_slab_step(cfg, Omega, A_slab, probes)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_slab_step(cfg, Omega, A_slab, probes)
+    dt = (time.perf_counter() - t0) / args.steps
+    bytes_per_step = 16 * cfg.m * ns
+    value = bytes_per_step / dt / 1e9
+    sample = f"oracle ID of the column slab A[:, :{ns}] (m={cfg.m}, k={cfg.k}, l={cfg.l}); Omega drawn untimed"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": workload_config(cfg, args),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(cfg, args):
+    return {"workload": f"{cfg.name}: complex128 A = U V^H + tail (sigma_j = 1 for j <= {cfg.rank}, "
+                        f"tail ~{cfg.eps:g}), m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
+                        f"{cfg.a_bytes / 2**30:.0f} GiB",
+            "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode,
+            "l2": "inputs larger than L2 (A is %.0f GiB, L2 129 MB)" % (cfg.a_bytes / 2**30)}
+
+
+# ---------------------------------------------------------------------------
+# The GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args, cfg, world, rank, local):
+    import torch
+    import synth
+    import synth.device
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
+    A = synth.device.device_matrix(cfg, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, mode=args.mode, stream=stream)
+    Y = rid.colmajor_empty(l, n, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    T = rid.colmajor_empty(k, n - k, device=dev)
+
+    def step(ev=None):
+        if ev: ev[0].record(stream)
+        plan.sketch(A, Y)
+        if ev: ev[1].record(stream)
+        plan.select(Y, perm)
+        if ev: ev[2].record(stream)
+        plan.solve(Y, T)
+        if ev: ev[3].record(stream)
+        res = plan.error(A, perm, T, args.nprobe, 1)
+        if ev: ev[4].record(stream)
+        return res
+
+    for _ in range(args.warmup):
+        step()
+    plan.sync_status()
+    events = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler.start()
+    start.record(stream)
+    for s in range(args.steps):
+        est, upper = step(events[s])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier(world)
+    plan.sync_status()
+    ms = max_over_ranks(start.elapsed_time(stop), world)
+    ms_step = ms / args.steps
+    per = {name: statistics.mean(ev[i].elapsed_time(ev[i + 1]) for ev in events)
+           for i, name in enumerate(("sketch", "select", "solve", "error"))}
+    st = plan.stats()
+    launches = args.steps * (st["sketch_launches"] + st["select_launches"] + st["solve_launches"] +
+                             st["error_launches"])
+    value = world * cfg.a_bytes / 1e9 / (ms_step / 1e3)
+
+    # roofline of the dominant kernel (the sketch) and of the whole ID
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    sketch_flops = 8.0 * l * m * n
+    if args.mode == "fp64":
+        achieved = sketch_flops / (per["sketch"] / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
+                "kernel": "sketch_fp64_kernel", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+    else:
+        achieved = sketch_flops / (per["sketch"] / 1e3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sketch_emulated"}
+    # whole-ID roofline: sum over steps of max(bytes / HBM, flops / FP64 peak)
+    p64 = FP64_PEAK_TFLOPS * 1e12
+    a_b = 16.0 * m * n
+    t_roof = (max(a_b / (hbm * 1e9), sketch_flops / p64) +
+              max(2 * 16.0 * l * n * k / (hbm * 1e9), 16.0 * n * (l * k - k * k / 2) / p64) +
+              4.0 * k * k * (n - k) / p64 +
+              max(a_b / (hbm * 1e9), 8.0 * m * n * args.nprobe / p64))
+    id_frac = t_roof / (ms_step / 1e3)
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, generated on the device)",
+        "config": workload_config(cfg, args),
+        "roofline": roof,
+        "id_roofline_frac": id_frac,
+        "step_ms": per,
+        "gpu_launches": launches,
+        "error_estimate": {"est": est, "upper": upper},
+        "clocks": clocks,
+    }
+
+    if args.e2e_steps > 0:
+        line["e2e"] = run_e2e(args, cfg, plan, A, Y, perm, T, stream, world)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, cfg, A)
+    plan.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
+    """Same metric with host buffers: every step copies A in from pinned host
+    memory and reads perm, T and the estimate back."""
+    import torch
+    A_host = torch.empty((cfg.n, cfg.m), dtype=A.dtype, pin_memory=True).t()
+    A_host.copy_(A)
+    perm_h = torch.empty(cfg.n, dtype=torch.int32, pin_memory=True)
+    T_h = torch.empty((cfg.n - cfg.k, cfg.k), dtype=torch.complex128, pin_memory=True).t()
+    torch.cuda.synchronize()
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    start.record(stream)
+    for _ in range(args.e2e_steps):
+        A.copy_(A_host, non_blocking=True)
+        plan.sketch(A, Y)
+        plan.select(Y, perm)
+        plan.solve(Y, T)
+        plan.error(A, perm, T, args.nprobe, 1)
+        perm_h.copy_(perm, non_blocking=True)
+        T_h.copy_(T, non_blocking=True)
+    stop.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(start.elapsed_time(stop), world) / args.e2e_steps
+    del A_host
+    h2d = cfg.a_bytes
+    d2h = 4 * cfg.n + 16 * cfg.k * (cfg.n - cfg.k) + 16
+    return {"value": world * cfg.a_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": args.e2e_steps}
+
+
+def cpu_baseline(args, cfg, A):
+    import numpy as np
+    ns = args.ref_cols
+    A_slab = np.asfortranarray(A[:, :ns].cpu().numpy())
+    Omega, probes = oracle_slab_setup(cfg, A_slab)
+    t0 = time.perf_counter()
+    oracle_slab_step(cfg, Omega, A_slab, probes)
+    dt = time.perf_counter() - t0
+    return {"value": 16 * cfg.m * ns / dt / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+            "sample": f"oracle ID of the column slab A[:, :{ns}] (m={cfg.m}, k={cfg.k}, l={cfg.l}), "
+                      f"{dt:.1f} s; Omega drawn untimed"}
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--config", default="large_tall")
+    ap.add_argument("--mode", default="fp64", choices=("fp64", "fp64_emulated"))
+    ap.add_argument("--nprobe", type=int, default=8)
+    ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    import synth
+    cfg = synth.CONFIGS[args.config]
+    world, rank, local = init_dist()
+    if args.impl == "reference":
+        run_reference(args, cfg, world, rank)
+    else:
+        run_ours(args, cfg, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

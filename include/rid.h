@@ -1,0 +1,157 @@
+/*
+ * rid.h -- C ABI of the GB300 randomized interpolative decomposition (ID).
+ *
+ * Method (Lucas, Stalzer & Feo, "Parallel implementation of fast randomized
+ * algorithms for the decomposition of low rank matrices", Sec. 2): an m x n
+ * complex matrix A of approximate rank k is factored as A ~= B P, where
+ * B = A(:, J) holds k columns of A and P = [I | T] Pi^T is k x n.  Four calls
+ * make one ID, in the paper's order:
+ *
+ *   rid_sketch  Y = Omega A           randomization (Sec. 2; Gaussian Omega,
+ *                                     the paper's "faster randomization")
+ *   rid_select  Y Pi ~= Q [R1 | R2]   truncated QR with column pivoting (Sec. 2)
+ *   rid_solve   R1 T = R2             the factorization of R (Sec. 2, Sec. 3.2)
+ *   rid_error   ||A - B P||_2         error of the ID (Sec. 3.3, Table 5)
+ *
+ * Conventions shared by every call:
+ *   - Matrices are complex, interleaved (re, im), COLUMN-MAJOR with a leading
+ *     dimension ld >= rows, except Omega, which is ROW-MAJOR (l x m, each row
+ *     contiguous along m).  complex128 = two doubles, complex64 = two floats.
+ *   - Unless a parameter says "host", pointers are DEVICE pointers owned by
+ *     the caller, and must stay valid until the plan's stream has run the work.
+ *   - Every call is asynchronous on the plan's stream, except rid_error and
+ *     rid_sync_status, which synchronize it.
+ *   - Argument errors are detected on the host before anything is launched
+ *     and return RID_EINVAL (bad size, null pointer, ld too small) or
+ *     RID_EUNSUPPORTED (dtype/mode combination not built); nothing is
+ *     written then.  CUDA launch or allocation errors return RID_ECUDA /
+ *     RID_ENOMEM.  Conditions found on the device (rank deficiency) are
+ *     recorded in the plan's device status word and reported by
+ *     rid_sync_status / rid_error.
+ *   - A plan is not thread-safe; different plans are independent.
+ */
+#ifndef RID_H
+#define RID_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RID_API __attribute__((visibility("default")))
+#else
+#define RID_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rid_plan_s* rid_plan_t;
+
+typedef enum {
+  RID_OK = 0,
+  RID_EINVAL = 1,        /* bad argument (size, pointer, leading dimension) */
+  RID_ENOMEM = 2,        /* device allocation failed */
+  RID_ECUDA = 3,         /* a CUDA call or kernel launch failed */
+  RID_ERANK = 4,         /* the sketch has rank < k (Sec. 2: redraw Omega, i.e. new seed) */
+  RID_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+  RID_EUNSUPPORTED = 6   /* dtype / mode combination not available */
+} rid_status;
+
+typedef enum {
+  RID_C128 = 0,          /* A is complex128 */
+  RID_C64 = 1            /* A is complex64 (mixed-precision sketch) */
+} rid_dtype;
+
+typedef enum {
+  RID_FP64_NATIVE = 0,   /* sketch with FP64 FMA on the CUDA cores */
+  RID_FP64_EMULATED = 1, /* sketch on tcgen05 tensor cores with exact BF16 slices, FP64-grade result */
+  RID_MIXED_BF16 = 2,    /* complex64 A: sketch from 3 BF16 slices, FP32 accumulation */
+  RID_MIXED_3XTF32 = 3   /* complex64 A: sketch from 3xTF32 splits, FP32 accumulation */
+} rid_mode;
+
+/* Create a plan for IDs of m x n matrices of rank k with an l x m test matrix.
+ *   Requires 1 <= k <= min(m, n, l); l >= k (Sec. 2: "l >= k"; the paper
+ *   uses l = 2k, the configurations here use l = k + p).
+ *   seed selects the Gaussian test matrix Omega: entry (i, j) is drawn from
+ *   Philox4x32-10 (Salmon et al., SC 2011) at counter (j mod 2^32, j div 2^32,
+ *   i, 3) under key (seed mod 2^32, seed div 2^32), then Box-Muller,
+ *   rho = sqrt(-log u1), Omega_ij = rho exp(2 pi i u2), so re and im are
+ *   iid N(0, 1/2).  u1, u2 are 53-bit uniforms built from the four words.
+ *   stream is a cudaStream_t (NULL = legacy default stream) on which every
+ *   call of this plan runs.
+ *   The plan allocates and owns Omega (l x m, row-major) and its workspace on
+ *   the current device; Omega is generated on the stream before return. */
+RID_API rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
+                           rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream);
+
+/* Free the plan's device memory (synchronizes its stream first).  NULL is a no-op. */
+RID_API rid_status rid_plan_destroy(rid_plan_t plan);
+
+/* Device pointer to the plan's Omega (complex128, l x m row-major) and its
+ * row stride ldo (elements).  Read-only for the caller. */
+RID_API rid_status rid_plan_omega(rid_plan_t plan, const void** omega, int64_t* ldo);
+
+/* Replace the plan's Omega by a caller-supplied l x m complex128 row-major
+ * device matrix with row stride ldo >= m (copied on the stream). */
+RID_API rid_status rid_plan_set_omega(rid_plan_t plan, const void* omega, int64_t ldo);
+
+/* Randomization, Sec. 2:  Y = Omega A.
+ *   A: m x n, column-major, leading dimension lda >= m, dtype of the plan.
+ *   Y: l x n complex128 output, column-major, ldy >= l.  Fully overwritten.
+ *   A is read once per l-tile; the result is deterministic (fixed reduction order). */
+RID_API rid_status rid_sketch(rid_plan_t plan, const void* A, int64_t lda, void* Y, int64_t ldy);
+
+/* Truncated QR with column pivoting of Y (Sec. 2, "Y ~= Q R"; the permutation
+ * the paper asks for is chosen by Businger-Golub pivoting):
+ *   k steps; at step j the pivot is the column of largest remaining norm
+ *   sum_{i>=j} |Y_ic|^2 (recomputed exactly, ties to the lowest index); the
+ *   reflector follows LAPACK zlarfg (real beta, H = I - tau v v^H).
+ *   Y (in/out, l x n complex128, ldy >= l): on return rows 0..k-1 hold
+ *   [R1 | R2] in pivoted column order, Householder vectors below the diagonal.
+ *   perm (out, int32[n]): perm[c] = original column of pivoted column c,
+ *   so J = perm[0..k-1] and B = A(:, J).
+ *   If the sketch has rank < k (a pivot norm is exactly zero) the status word
+ *   becomes RID_ERANK and later steps of this call are skipped. */
+RID_API rid_status rid_select(rid_plan_t plan, void* Y, int64_t ldy, int32_t* perm);
+
+/* Factorization of R, Sec. 2 "R2 = R1 T":  T = R1^-1 R2 by back substitution,
+ * every right-hand side column independent (Sec. 3.2).
+ *   Y: the output of rid_select (R1 = Y[0:k, 0:k] upper triangular,
+ *   R2 = Y[0:k, k:n]).  T: k x (n-k) complex128 output, column-major,
+ *   ldt >= k; column i of T belongs to original column perm[k+i], so
+ *   P(:, perm[j]) = e_j (j < k) and P(:, perm[k+i]) = T(:, i).  n == k is
+ *   allowed (T is empty). */
+RID_API rid_status rid_solve(rid_plan_t plan, const void* Y, int64_t ldy, void* T, int64_t ldt);
+
+/* Error of the ID (Sec. 3.3, Table 5 reports ||A - B P||_2), by Gaussian probes:
+ * for r = nprobe columns w_q of an n x r complex Gaussian matrix (Philox
+ * counter (q, 0, c, 4) for row c, key = probe_seed, Box-Muller as for Omega),
+ * E w = A w~ with w~(Jc) = w(Jc), w~(J) = -T w(Jc), in one pass over A.
+ *   out (HOST, double[2]): out[0] = max_q ||E w_q|| / ||w_q|| (never above
+ *   ||E||_2); out[1] = 10 sqrt(2/pi) max_q ||E w_q||, an upper bound on
+ *   ||E||_2 with probability >= 1 - 10^-r (Halko, Martinsson & Tropp 2011,
+ *   Lemma 4.1).  1 <= nprobe <= 16.  Synchronizes the stream; returns
+ *   RID_ERANK if the last rid_select found a rank-deficient sketch. */
+RID_API rid_status rid_error(rid_plan_t plan, const void* A, int64_t lda, const int32_t* perm,
+                     const void* T, int64_t ldt, int32_t nprobe, uint64_t probe_seed,
+                     double out[2]);
+
+/* Synchronize the plan's stream and return the device status word
+ * (RID_OK or RID_ERANK), or RID_ECUDA if the stream reported an error. */
+RID_API rid_status rid_sync_status(rid_plan_t plan);
+
+/* Plan facts for callers that account for work (no device work, no sync):
+ *   out[0] = kernel launches of one rid_sketch     out[1] = of one rid_select
+ *   out[2] = of one rid_solve                      out[3] = of one rid_error
+ *   out[4] = K-splits of the sketch                out[5] = device bytes the plan owns
+ *   out[6] = mode (rid_mode)                       out[7] = dtype (rid_dtype) */
+RID_API rid_status rid_plan_stats(rid_plan_t plan, int64_t out[8]);
+
+/* Static, human-readable name of a status code. */
+RID_API const char* rid_status_string(rid_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RID_H */

@@ -1,0 +1,193 @@
+"""GB300-native randomized interpolative decomposition (ID).
+
+Lucas, Stalzer & Feo, "Parallel implementation of fast randomized algorithms
+for the decomposition of low rank matrices", Sec. 2: A (m x n, complex) ~= B P
+with B = A(:, J) and P = [I | T] Pi^T, computed in four steps that each run as
+hand-written sm_103a CUDA kernels behind the C ABI of include/rid.h:
+
+    plan = Plan(m, n, k, l, seed)          # draws Omega on the device
+    Y    = plan.sketch(A)                  # Y = Omega A
+    perm = plan.select(Y)                  # pivoted QR, J = perm[:k]
+    T    = plan.solve(Y)                   # R1 T = R2
+    est, upper = plan.error(A, perm, T)    # ||A - B P||_2 by probes
+
+This module only marshals arguments: torch supplies device memory and streams.
+Matrices are column-major torch views (stride(0) == 1), e.g. colmajor_empty().
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native
+from ._native import RIDError, check
+
+__all__ = ["Plan", "RIDError", "colmajor_empty", "as_colmajor", "decompose", "MODES"]
+
+MODES = {
+    "fp64": _native.RID_FP64_NATIVE,
+    "fp64_emulated": _native.RID_FP64_EMULATED,
+    "bf16": _native.RID_MIXED_BF16,
+    "3xtf32": _native.RID_MIXED_3XTF32,
+}
+_DTYPES = {torch.complex128: _native.RID_C128, torch.complex64: _native.RID_C64}
+
+
+def colmajor_empty(rows, cols, dtype=torch.complex128, device="cuda"):
+    """Uninitialised rows x cols column-major tensor (a transposed contiguous one)."""
+    return torch.empty((cols, rows), dtype=dtype, device=device).t()
+
+
+def as_colmajor(x):
+    """x itself if it is column-major with stride(1) >= rows, else a column-major copy."""
+    if x.dim() == 2 and x.stride(0) == 1 and x.stride(1) >= max(1, x.shape[0]):
+        return x
+    return x.t().contiguous().t()
+
+
+def _ld(x):
+    return max(int(x.stride(1)), int(x.shape[0]), 1)
+
+
+class _CudaView:
+    """Minimal __cuda_array_interface__ holder for a device pointer owned elsewhere."""
+
+    def __init__(self, ptr, shape, strides_bytes, typestr):
+        self.__cuda_array_interface__ = {
+            "data": (int(ptr), True), "shape": tuple(shape), "strides": tuple(strides_bytes),
+            "typestr": typestr, "version": 3,
+        }
+
+
+class Plan:
+    """One ID shape (m, n, k, l) with its seeded Gaussian test matrix Omega."""
+
+    def __init__(self, m, n, k, l, seed=0, dtype=torch.complex128, mode="fp64", stream=None,
+                 device=None):
+        self._lib = _native.load()
+        self.m, self.n, self.k, self.l = int(m), int(n), int(k), int(l)
+        self.seed = int(seed)
+        self.dtype = dtype
+        self.mode = mode
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   torch.device(device).index or 0)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self._lib.rid_plan_create(ctypes.byref(handle), self.m, self.n, self.k, self.l,
+                                           _DTYPES[dtype], MODES[mode], self.seed & (2 ** 64 - 1),
+                                           ctypes.c_void_p(stream.cuda_stream))
+        check(st, "rid_plan_create")
+        self._h = handle
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rid_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- Omega -------------------------------------------------------------
+    def omega(self):
+        """A copy of the plan's Omega as an l x m complex128 tensor."""
+        ptr, ldo = ctypes.c_void_p(), ctypes.c_int64()
+        check(self._lib.rid_plan_omega(self._h, ctypes.byref(ptr), ctypes.byref(ldo)), "rid_plan_omega")
+        view = _CudaView(ptr.value, (self.l, self.m), (16 * ldo.value, 16), "<c16")
+        self.stream.synchronize()
+        return torch.as_tensor(view, device=self.device).clone()
+
+    def set_omega(self, omega):
+        """Use a caller-supplied l x m complex128 Omega (row-major, on the device)."""
+        omega = omega.to(device=self.device, dtype=torch.complex128)
+        if omega.stride(1) != 1:
+            omega = omega.contiguous()
+        assert tuple(omega.shape) == (self.l, self.m)
+        check(self._lib.rid_plan_set_omega(self._h, ctypes.c_void_p(omega.data_ptr()), omega.stride(0)),
+              "rid_plan_set_omega")
+        self._keep = omega
+
+    # -- the four steps --------------------------------------------------------
+    def sketch(self, A, Y=None):
+        """Y = Omega A (l x n complex128, column-major)."""
+        assert A.is_cuda and A.dtype == self.dtype and tuple(A.shape) == (self.m, self.n)
+        assert A.stride(0) == 1, "A must be column-major (use as_colmajor)"
+        if Y is None:
+            Y = colmajor_empty(self.l, self.n, torch.complex128, self.device)
+        check(self._lib.rid_sketch(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                   ctypes.c_void_p(Y.data_ptr()), _ld(Y)), "rid_sketch")
+        return Y
+
+    def select(self, Y, perm=None):
+        """Pivoted QR of Y in place; returns perm (int32[n], J = perm[:k])."""
+        assert Y.is_cuda and Y.dtype == torch.complex128 and Y.stride(0) == 1
+        if perm is None:
+            perm = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        check(self._lib.rid_select(self._h, ctypes.c_void_p(Y.data_ptr()), _ld(Y),
+                                   ctypes.c_void_p(perm.data_ptr())), "rid_select")
+        return perm
+
+    def solve(self, Y, T=None):
+        """T = R1^-1 R2 (k x (n-k) complex128, column-major)."""
+        assert Y.is_cuda and Y.dtype == torch.complex128 and Y.stride(0) == 1
+        if T is None:
+            T = colmajor_empty(self.k, self.n - self.k, torch.complex128, self.device)
+        ptr = T.data_ptr() if T.numel() else 0
+        check(self._lib.rid_solve(self._h, ctypes.c_void_p(Y.data_ptr()), _ld(Y), ctypes.c_void_p(ptr),
+                                  max(_ld(T), self.k)), "rid_solve")
+        return T
+
+    def error(self, A, perm, T, nprobe=8, probe_seed=1):
+        """(est, upper) of ||A - A(:, J) P||_2 by nprobe Gaussian probes (synchronizes)."""
+        assert A.is_cuda and A.stride(0) == 1
+        out = (ctypes.c_double * 2)()
+        ptr = T.data_ptr() if T.numel() else 0
+        check(self._lib.rid_error(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                  ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(ptr),
+                                  max(_ld(T), self.k), int(nprobe), int(probe_seed) & (2 ** 64 - 1),
+                                  out), "rid_error")
+        return float(out[0]), float(out[1])
+
+    def stats(self):
+        """Launch counts per call, K-splits and device bytes of the plan."""
+        out = (ctypes.c_int64 * 8)()
+        check(self._lib.rid_plan_stats(self._h, out), "rid_plan_stats")
+        keys = ("sketch_launches", "select_launches", "solve_launches", "error_launches", "split_k",
+                "device_bytes", "mode", "dtype")
+        return dict(zip(keys, [int(x) for x in out]))
+
+    def sync_status(self):
+        """Synchronize the plan's stream and raise RIDError on a device-side error."""
+        check(self._lib.rid_sync_status(self._h), "rid_sync_status")
+
+
+def decompose(A, k, l, seed=0, mode="fp64", nprobe=8, probe_seed=1, plan=None):
+    """The whole ID of a column-major device matrix A; returns a dict with
+    J, perm, T, Y (holding R) and the error estimate (est, upper)."""
+    m, n = A.shape
+    own = plan is None
+    if own:
+        plan = Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode)
+    try:
+        Y = plan.sketch(A)
+        perm = plan.select(Y)
+        T = plan.solve(Y)
+        est, upper = plan.error(A, perm, T, nprobe, probe_seed) if A.dtype == torch.complex128 else (None, None)
+        plan.sync_status()
+        return {"J": perm[:k], "perm": perm, "T": T, "Y": Y, "est": est, "upper": upper}
+    finally:
+        if own:
+            plan.close()

@@ -1,0 +1,289 @@
+// C ABI of the randomized ID: plans, argument checks and dispatch to the
+// kernels.  Every entry point validates its arguments on the host before it
+// launches anything.
+#include <stdlib.h>
+#include <string.h>
+
+#include "rid_internal.cuh"
+
+// Tensor-core paths (defined in rid_sketch_tc.cu).
+rid_status rid_tc_plan_init(rid_plan_s* p);
+void rid_tc_plan_free(rid_plan_s* p);
+cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+
+namespace {
+
+// Keeps the caller's current device and switches to the plan's one.
+struct DeviceGuard {
+  int old = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&old) != cudaSuccess) { ok = false; return; }
+    if (old != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (old >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != old) cudaSetDevice(old);
+  }
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+rid_status from_cuda(cudaError_t e) {
+  if (e == cudaSuccess) return RID_OK;
+  if (e == cudaErrorMemoryAllocation) return RID_ENOMEM;
+  return RID_ECUDA;
+}
+
+// Workspace layout of a plan: one allocation, carved into 256-byte aligned pieces.
+struct Layout {
+  size_t omega, status, sk_partial, qr_val, qr_idx, qr_counter, tau, probes, wtilde, wj_part,
+      ew_part, norm_part, err_out, total;
+};
+
+Layout plan_layout(const rid_plan_s* p) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t at = off; off += align256(bytes); return at; };
+  L.omega = take((size_t)p->l * p->ldo * sizeof(double2));
+  L.status = take(sizeof(int));
+  L.sk_partial = take(p->split_k > 1 ? (size_t)p->split_k * p->l * p->n * sizeof(double2) : 0);
+  L.qr_val = take((size_t)p->qr_grid * sizeof(double));
+  L.qr_idx = take((size_t)p->qr_grid * sizeof(int));
+  L.qr_counter = take(sizeof(unsigned));
+  L.tau = take((size_t)p->k * sizeof(double2));
+  L.probes = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
+  L.wtilde = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
+  L.wj_part = take((size_t)p->err_wj_grid * p->k * RID_MAX_PROBES * sizeof(double2));
+  L.ew_part = take((size_t)p->err_col_split * RID_MAX_PROBES * p->m * sizeof(double2));
+  L.norm_part = take((size_t)p->err_row_blocks * RID_MAX_PROBES * sizeof(double));
+  L.err_out = take(2 * sizeof(double));
+  L.total = off;
+  return L;
+}
+
+void choose_launch_shapes(rid_plan_s* p) {
+  const int64_t sms = p->num_sms;
+  // sketch: enough (l-tile, n-tile, K-split) CTAs for two waves
+  const int64_t tiles = ((p->l + 31) / 32) * ((p->n + 31) / 32);
+  int64_t split = 1;
+  if (tiles < 2 * sms) split = (2 * sms + tiles - 1) / tiles;
+  const int64_t max_split = (p->m + 255) / 256;
+  if (split > max_split) split = max_split;
+  if (split < 1) split = 1;
+  int64_t kps = (p->m + split - 1) / split;
+  kps = (kps + 15) / 16 * 16;
+  p->k_per_split = kps;
+  p->split_k = (int)((p->m + kps - 1) / kps);
+  // select: one warp per column, up to four CTAs per SM
+  int64_t g = (p->n + 7) / 8;
+  if (g > 4 * sms) g = 4 * sms;
+  p->qr_grid = (int)(g < 1 ? 1 : g);
+  // error
+  const int64_t ncols = p->n - p->k;
+  int64_t wg = (ncols + 63) / 64;
+  if (wg > 2 * sms) wg = 2 * sms;
+  p->err_wj_grid = (int)(wg < 1 ? 1 : wg);
+  p->err_row_blocks = (int)((p->m + 255) / 256);
+  int64_t cs = (2 * sms + p->err_row_blocks - 1) / p->err_row_blocks;
+  const int64_t max_cs = (p->n + 31) / 32;
+  if (cs > max_cs) cs = max_cs;
+  p->err_col_split = (int)(cs < 1 ? 1 : cs);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* rid_status_string(rid_status s) {
+  switch (s) {
+    case RID_OK: return "RID_OK";
+    case RID_EINVAL: return "RID_EINVAL: invalid argument";
+    case RID_ENOMEM: return "RID_ENOMEM: device allocation failed";
+    case RID_ECUDA: return "RID_ECUDA: CUDA error";
+    case RID_ERANK: return "RID_ERANK: sketch has rank < k (redraw with another seed)";
+    case RID_ETIMEOUT: return "RID_ETIMEOUT: device wait timed out";
+    case RID_EUNSUPPORTED: return "RID_EUNSUPPORTED: dtype/mode not available";
+  }
+  return "RID_?: unknown status";
+}
+
+rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
+                           rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream) {
+  if (!plan) return RID_EINVAL;
+  *plan = nullptr;
+  if (m < 1 || n < 1 || k < 1 || l < k || k > m || k > n) return RID_EINVAL;
+  if (n > 0x7fffffffLL || m > ((int64_t)1 << 40)) return RID_EINVAL;
+  if (l > 512) return RID_EUNSUPPORTED;   // the QR keeps a column's l entries in one warp's registers
+  if (dtype != RID_C128 && dtype != RID_C64) return RID_EINVAL;
+  if (mode < RID_FP64_NATIVE || mode > RID_MIXED_3XTF32) return RID_EINVAL;
+  if (dtype == RID_C128 && (mode == RID_MIXED_BF16 || mode == RID_MIXED_3XTF32)) return RID_EUNSUPPORTED;
+  if (dtype == RID_C64 && (mode == RID_FP64_NATIVE || mode == RID_FP64_EMULATED)) return RID_EUNSUPPORTED;
+  int nr = 0;
+  if (rid_solve_smem_bytes(k, &nr) > 200 * 1024) return RID_EUNSUPPORTED;
+
+  rid_plan_s* p = (rid_plan_s*)calloc(1, sizeof(rid_plan_s));
+  if (!p) return RID_ENOMEM;
+  p->m = m; p->n = n; p->k = k; p->l = l;
+  p->dtype = dtype; p->mode = mode; p->seed = seed;
+  p->stream = (cudaStream_t)stream;
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
+  if (e != cudaSuccess) { free(p); return RID_ECUDA; }
+  p->ldo = (m + 15) / 16 * 16;     // 256-byte aligned rows of Omega
+  choose_launch_shapes(p);
+
+  const Layout L = plan_layout(p);
+  char* base = nullptr;
+  e = cudaMalloc((void**)&base, L.total);
+  if (e != cudaSuccess) { free(p); cudaGetLastError(); return RID_ENOMEM; }
+  p->ws_bytes = L.total;
+  p->omega = (double2*)(base + L.omega);
+  p->status = (int*)(base + L.status);
+  p->sk_partial = (double2*)(base + L.sk_partial);
+  p->qr_val = (double*)(base + L.qr_val);
+  p->qr_idx = (int*)(base + L.qr_idx);
+  p->qr_counter = (unsigned*)(base + L.qr_counter);
+  p->tau = (double2*)(base + L.tau);
+  p->probes = (double2*)(base + L.probes);
+  p->wtilde = (double2*)(base + L.wtilde);
+  p->wj_part = (double2*)(base + L.wj_part);
+  p->ew_part = (double2*)(base + L.ew_part);
+  p->norm_part = (double*)(base + L.norm_part);
+  p->err_out = (double*)(base + L.err_out);
+
+  e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(p->qr_counter, 0, sizeof(unsigned), p->stream);
+  if (e == cudaSuccess)
+    e = rid_launch_gaussian(p->omega, l, m, p->ldo, 1, seed, RID_STREAM_OMEGA, p->stream);
+  if (e != cudaSuccess) {
+    cudaFree(base);
+    free(p);
+    return RID_ECUDA;
+  }
+  if (mode != RID_FP64_NATIVE) {
+    const rid_status s = rid_tc_plan_init(p);
+    if (s != RID_OK) {
+      cudaStreamSynchronize(p->stream);
+      cudaFree(base);
+      free(p);
+      return s;
+    }
+  }
+  *plan = p;
+  return RID_OK;
+}
+
+rid_status rid_plan_destroy(rid_plan_t p) {
+  if (!p) return RID_OK;
+  DeviceGuard g(p->device);
+  cudaStreamSynchronize(p->stream);
+  rid_tc_plan_free(p);
+  cudaFree((void*)p->omega);   // the omega piece is the start of the single allocation
+  free(p);
+  return RID_OK;
+}
+
+rid_status rid_plan_omega(rid_plan_t p, const void** omega, int64_t* ldo) {
+  if (!p || !omega || !ldo) return RID_EINVAL;
+  *omega = p->omega;
+  *ldo = p->ldo;
+  return RID_OK;
+}
+
+rid_status rid_plan_set_omega(rid_plan_t p, const void* omega, int64_t ldo) {
+  if (!p || !omega || ldo < p->m) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = cudaMemcpy2DAsync(p->omega, p->ldo * sizeof(double2), omega, ldo * sizeof(double2),
+                                    p->m * sizeof(double2), p->l, cudaMemcpyDeviceToDevice, p->stream);
+  if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
+    // the tensor-core paths keep Omega in split form: rebuild it
+    rid_tc_plan_free(p);
+    const rid_status s = rid_tc_plan_init(p);
+    if (s != RID_OK) return s;
+  }
+  return from_cuda(e);
+}
+
+rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t ldy) {
+  if (!p || !A || !Y || lda < p->m || ldy < p->l) return RID_EINVAL;
+  if (!aligned16(Y) || !aligned16(A)) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e;
+  if (p->mode == RID_FP64_NATIVE)
+    e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy);
+  else
+    e = rid_tc_sketch(p, A, lda, (double2*)Y, ldy);
+  return from_cuda(e);
+}
+
+rid_status rid_select(rid_plan_t p, void* Y, int64_t ldy, int32_t* perm) {
+  if (!p || !Y || !perm || ldy < p->l) return RID_EINVAL;
+  if (!aligned16(Y) || ((uintptr_t)perm & 3u)) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  return from_cuda(rid_launch_select(p, (double2*)Y, ldy, perm));
+}
+
+rid_status rid_solve(rid_plan_t p, const void* Y, int64_t ldy, void* T, int64_t ldt) {
+  if (!p || !Y || ldy < p->l || ldt < p->k) return RID_EINVAL;
+  if (p->n > p->k && !T) return RID_EINVAL;
+  if (!aligned16(Y) || (T && !aligned16(T))) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  return from_cuda(rid_launch_solve(p, (const double2*)Y, ldy, (double2*)T, ldt));
+}
+
+rid_status rid_error(rid_plan_t p, const void* A, int64_t lda, const int32_t* perm, const void* T,
+                     int64_t ldt, int32_t nprobe, uint64_t probe_seed, double out[2]) {
+  if (!p || !A || !perm || !out || lda < p->m || ldt < p->k) return RID_EINVAL;
+  if (p->n > p->k && !T) return RID_EINVAL;
+  if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  if (p->dtype != RID_C128) return RID_EUNSUPPORTED;
+  if (!aligned16(A) || (T && !aligned16(T))) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = rid_launch_error(p, (const double2*)A, lda, perm, (const double2*)T, ldt, nprobe,
+                                   probe_seed);
+  if (e != cudaSuccess) return from_cuda(e);
+  double host[2];
+  int status = 0;
+  e = cudaMemcpyAsync(host, p->err_out, sizeof(host), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  out[0] = host[0];
+  out[1] = host[1];
+  return status == RID_OK ? RID_OK : (rid_status)status;
+}
+
+rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
+  if (!p || !out) return RID_EINVAL;
+  out[0] = p->mode == RID_FP64_NATIVE ? (p->split_k > 1 ? 2 : 1) : p->tc_sketch_launches;
+  out[1] = 1 + p->k;
+  out[2] = p->n > p->k ? 1 : 0;
+  out[3] = p->n > p->k ? 6 : 5;
+  out[4] = p->split_k;
+  out[5] = (int64_t)(p->ws_bytes + p->tc_bytes);
+  out[6] = p->mode;
+  out[7] = p->dtype;
+  return RID_OK;
+}
+
+rid_status rid_sync_status(rid_plan_t p) {
+  if (!p) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  int status = 0;
+  cudaError_t e = cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  return (rid_status)status;
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// Error of the ID, ||A - B P||_2 (Sec. 3.3, Table 5), estimated with r
+// Gaussian probes in one pass over A.
+//
+// For a probe w, (A - A_J P) w = A_Jc w_Jc - A_J T w_Jc = A w~, where
+// w~(Jc) = w(Jc) and w~(J) = -T w(Jc).  So the probes are first modified with
+// one small product T w(Jc) (k x (n-k) times (n-k) x r), then A is streamed
+// once: one thread per row of A, 16-byte coalesced loads down each column,
+// the r modified probe entries of the column broadcast from shared memory.
+// All sums use a fixed order (no floating-point atomics).
+#include "rid_internal.cuh"
+
+namespace {
+
+constexpr int EW_THREADS = 256;
+constexpr int EW_COLS = 32;          // columns of A staged per shared-memory round
+constexpr int RM = RID_MAX_PROBES;
+
+__global__ void probes_kernel(double2* __restrict__ probes, double2* __restrict__ wtilde,
+                              int64_t n, int r, uint64_t seed) {
+  const int64_t total = n * r;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / r;
+    const int q = (int)(e - c * r);
+    const double2 v = philox_complex_normal((uint64_t)c, (uint64_t)q, seed, RID_STREAM_PROBES);
+    probes[c * RM + q] = v;
+    wtilde[c * RM + q] = v;
+  }
+}
+
+// Partial sums of T w(Jc) over a chunk of T's columns: part[g][i][q].
+__global__ void __launch_bounds__(EW_THREADS)
+wj_kernel(const double2* __restrict__ T, int64_t ldt, const int32_t* __restrict__ perm,
+          const double2* __restrict__ probes, int k, int64_t ncols, int r, int64_t chunk,
+          double2* __restrict__ part) {
+  __shared__ double2 s_w[EW_COLS][RM];
+  const int64_t t_begin = (int64_t)blockIdx.x * chunk;
+  int64_t t_end = t_begin + chunk;
+  if (t_end > ncols) t_end = ncols;
+  for (int i0 = 0; i0 < k; i0 += EW_THREADS) {
+    const int i = i0 + threadIdx.x;
+    double2 acc[RM];
+#pragma unroll
+    for (int q = 0; q < RM; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int64_t t0 = t_begin; t0 < t_end; t0 += EW_COLS) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < EW_COLS * r; e += EW_THREADS) {
+        const int tt = e / r, q = e - tt * r;
+        const int64_t t = t0 + tt;
+        s_w[tt][q] = (t < t_end) ? probes[(int64_t)perm[k + t] * RM + q] : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      if (i < k) {
+        const int64_t tn = (t_end - t0) < EW_COLS ? (t_end - t0) : EW_COLS;
+        for (int tt = 0; tt < tn; ++tt) {
+          const double2 a = T[i + (t0 + tt) * ldt];
+#pragma unroll
+          for (int q = 0; q < RM; ++q)
+            if (q < r) acc[q] = cfma(a, s_w[tt][q], acc[q]);
+        }
+      }
+    }
+    if (i < k) {
+#pragma unroll
+      for (int q = 0; q < RM; ++q)
+        if (q < r) part[((int64_t)blockIdx.x * k + i) * RM + q] = acc[q];
+    }
+  }
+}
+
+// w~(perm[i], q) = -sum_g part[g][i][q] for the k skeleton columns.
+__global__ void wj_finalize_kernel(const double2* __restrict__ part, int groups,
+                                   const int32_t* __restrict__ perm, int k, int r,
+                                   double2* __restrict__ wtilde) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= k * r) return;
+  const int i = e / r, q = e - i * r;
+  double2 s = make_double2(0.0, 0.0);
+  for (int g = 0; g < groups; ++g) {
+    const double2 v = part[((int64_t)g * k + i) * RM + q];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  wtilde[(int64_t)perm[i] * RM + q] = make_double2(-s.x, -s.y);
+}
+
+// E w~ for a block of rows and a range of columns: part[s][q][row].
+__global__ void __launch_bounds__(EW_THREADS)
+ew_kernel(const double2* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+          const double2* __restrict__ wtilde, int r, int64_t chunk, double2* __restrict__ part) {
+  __shared__ double2 s_w[EW_COLS][RM];
+  const int64_t i = (int64_t)blockIdx.x * EW_THREADS + threadIdx.x;
+  const int64_t c_begin = (int64_t)blockIdx.y * chunk;
+  int64_t c_end = c_begin + chunk;
+  if (c_end > n) c_end = n;
+  double2 acc[RM];
+#pragma unroll
+  for (int q = 0; q < RM; ++q) acc[q] = make_double2(0.0, 0.0);
+  for (int64_t c0 = c_begin; c0 < c_end; c0 += EW_COLS) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < EW_COLS * RM; e += EW_THREADS) {
+      const int cc = e / RM, q = e - cc * RM;
+      const int64_t c = c0 + cc;
+      s_w[cc][q] = (c < c_end && q < r) ? wtilde[c * RM + q] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    if (i < m) {
+      const int cn = (int)((c_end - c0) < EW_COLS ? (c_end - c0) : EW_COLS);
+      const double2* a_ptr = A + i + c0 * lda;
+      for (int cc = 0; cc < cn; ++cc) {
+        const double2 a = __ldg(a_ptr + cc * lda);
+#pragma unroll
+        for (int q = 0; q < RM; ++q)
+          if (q < r) acc[q] = cfma(a, s_w[cc][q], acc[q]);
+      }
+    }
+  }
+  if (i < m) {
+    double2* dst = part + (int64_t)blockIdx.y * RM * m;
+#pragma unroll
+    for (int q = 0; q < RM; ++q)
+      if (q < r) dst[q * m + i] = acc[q];
+  }
+}
+
+__device__ double block_sum_256(double x, double* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  return s;   // valid in thread 0
+}
+
+// Per row block: sum over column splits, then |E w_q|^2 summed over the rows.
+__global__ void __launch_bounds__(EW_THREADS)
+ew_norm_kernel(const double2* __restrict__ part, int splits, int64_t m, int r,
+               double* __restrict__ norm_part) {
+  __shared__ double red[EW_THREADS / 32];
+  const int64_t i = (int64_t)blockIdx.x * EW_THREADS + threadIdx.x;
+  for (int q = 0; q < r; ++q) {
+    double v = 0.0;
+    if (i < m) {
+      double2 s = make_double2(0.0, 0.0);
+      for (int t = 0; t < splits; ++t) {
+        const double2 x = part[(int64_t)t * RM * m + (int64_t)q * m + i];
+        s.x += x.x;
+        s.y += x.y;
+      }
+      v = cabs2(s);
+    }
+    const double tot = block_sum_256(v, red);
+    if (threadIdx.x == 0) norm_part[(int64_t)blockIdx.x * RM + q] = tot;
+  }
+}
+
+// One CTA: the estimate and the probabilistic upper bound.
+__global__ void __launch_bounds__(EW_THREADS)
+error_finalize_kernel(const double* __restrict__ norm_part, int blocks,
+                      const double2* __restrict__ probes, int64_t n, int r,
+                      double* __restrict__ out) {
+  __shared__ double red[EW_THREADS / 32];
+  __shared__ double e2[RM], w2[RM];
+  for (int q = 0; q < r; ++q) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < blocks; b += blockDim.x) s += norm_part[(int64_t)b * RM + q];
+    s = block_sum_256(s, red);
+    if (threadIdx.x == 0) e2[q] = s;
+    double t = 0.0;
+    for (int64_t c = threadIdx.x; c < n; c += blockDim.x) t += cabs2(probes[c * RM + q]);
+    t = block_sum_256(t, red);
+    if (threadIdx.x == 0) w2[q] = t;
+  }
+  if (threadIdx.x == 0) {
+    double est = 0.0, emax = 0.0;
+    for (int q = 0; q < r; ++q) {
+      const double en = sqrt(e2[q]);
+      const double ratio = en / sqrt(w2[q]);
+      if (ratio > est) est = ratio;
+      if (en > emax) emax = en;
+    }
+    out[0] = est;
+    out[1] = 10.0 * sqrt(0.63661977236758134308 /* 2 / pi */) * emax;
+  }
+}
+
+}  // namespace
+
+cudaError_t rid_launch_error(const rid_plan_s* p, const double2* A, int64_t lda,
+                             const int32_t* perm, const double2* T, int64_t ldt, int nprobe,
+                             uint64_t probe_seed) {
+  const int r = nprobe;
+  const int k = p->k;
+  const int64_t n = p->n, m = p->m, ncols = n - k;
+  {
+    int64_t blocks = (n * r + 255) / 256;
+    if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
+    probes_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->probes, p->wtilde, n, r, probe_seed);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ncols > 0) {
+    const int groups = p->err_wj_grid;
+    const int64_t chunk = (ncols + groups - 1) / groups;
+    const int used = (int)((ncols + chunk - 1) / chunk);
+    wj_kernel<<<used, EW_THREADS, 0, p->stream>>>(T, ldt, perm, p->probes, k, ncols, r, chunk,
+                                                 p->wj_part);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    wj_finalize_kernel<<<(k * r + 255) / 256, 256, 0, p->stream>>>(p->wj_part, used, perm, k, r,
+                                                                   p->wtilde);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  } else {
+    // n == k: A = B P exactly, w~(J) = 0
+    wj_finalize_kernel<<<(k * r + 255) / 256, 256, 0, p->stream>>>(p->wj_part, 0, perm, k, r,
+                                                                   p->wtilde);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const int row_blocks = p->err_row_blocks;
+  const int splits = p->err_col_split;
+  const int64_t chunk = (n + splits - 1) / splits;
+  ew_kernel<<<dim3(row_blocks, splits), EW_THREADS, 0, p->stream>>>(A, lda, m, n, p->wtilde, r,
+                                                                    chunk, p->ew_part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ew_norm_kernel<<<row_blocks, EW_THREADS, 0, p->stream>>>(p->ew_part, splits, m, r, p->norm_part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  error_finalize_kernel<<<1, EW_THREADS, 0, p->stream>>>(p->norm_part, row_blocks, p->probes, n, r,
+                                                         p->err_out);
+  return cudaGetLastError();
+}

@@ -1,0 +1,151 @@
+// Internal declarations of the GB300 randomized-ID library (not installed).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rid.h"
+
+// ---------------------------------------------------------------------------
+// Plan: sizes, the test matrix Omega and all device workspace of one ID shape.
+// ---------------------------------------------------------------------------
+struct rid_plan_s {
+  int64_t m, n;
+  int32_t k, l;
+  rid_dtype dtype;
+  rid_mode mode;
+  uint64_t seed;
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+
+  double2* omega;          // l x m complex128, row-major, row stride ldo
+  int64_t ldo;
+  int* status;             // device status word (RID_OK / RID_ERANK)
+
+  // sketch (native FP64): split-K partial sums, split_k x l x n (ld = l)
+  int split_k;
+  int64_t k_per_split;
+  double2* sk_partial;
+
+  // select: per-CTA argmax partials, last-CTA counter, reflector scalars
+  int qr_grid;
+  double* qr_val;
+  int* qr_idx;
+  unsigned* qr_counter;
+  double2* tau;            // k
+
+  // error: probes, modified probes, partial sums, result
+  int err_wj_grid;         // CTAs over the columns of T
+  int err_row_blocks;      // CTAs over the rows of A
+  int err_col_split;       // CTAs over the columns of A
+  double2* probes;         // n x RID_MAX_PROBES (row c holds the probes of column c)
+  double2* wtilde;         // n x RID_MAX_PROBES
+  double2* wj_part;        // err_wj_grid x k x RID_MAX_PROBES
+  double2* ew_part;        // err_col_split x RID_MAX_PROBES x m
+  double* norm_part;       // err_row_blocks x RID_MAX_PROBES
+  double* err_out;         // 2 doubles (device)
+
+  size_t ws_bytes;         // bytes of the plan's single workspace allocation
+
+  // emulated / mixed sketch state (owned by the tensor-core path)
+  void* tc_state;
+  size_t tc_bytes;
+  int tc_sketch_launches;
+};
+
+#define RID_MAX_PROBES 16
+#define RID_STREAM_OMEGA 3u
+#define RID_STREAM_PROBES 4u
+#define RID_STREAM_SRFT 5u
+
+// ---------------------------------------------------------------------------
+// Launchers (each returns cudaGetLastError() of its launches).
+// ---------------------------------------------------------------------------
+// Gaussian matrix: entry (i, j) at out[i * row_stride + j * col_stride].
+cudaError_t rid_launch_gaussian(double2* out, int64_t rows, int64_t cols, int64_t row_stride,
+                                int64_t col_stride, uint64_t seed, uint32_t stream_id,
+                                cudaStream_t stream);
+
+cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_t lda, double2* Y,
+                                   int64_t ldy);
+
+cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm);
+
+cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy, double2* T,
+                             int64_t ldt);
+size_t rid_solve_smem_bytes(int k, int* nr_out);
+
+cudaError_t rid_launch_error(const rid_plan_s* p, const double2* A, int64_t lda,
+                             const int32_t* perm, const double2* T, int64_t ldt, int nprobe,
+                             uint64_t probe_seed);
+
+// ---------------------------------------------------------------------------
+// Device helpers shared by the kernels.
+// ---------------------------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+// acc += a * b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+// acc += conj(a) * b
+__device__ __forceinline__ double2 cfma_conj(double2 a, double2 b, double2 acc) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(-a.y, b.x, acc.y);
+  return acc;
+}
+__device__ __forceinline__ double cabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
+
+// Complex division a / d by Smith's algorithm (R. L. Smith, "Algorithm 116:
+// Complex division", CACM 5(8), 1962): scale by the larger component of d.
+__device__ __forceinline__ double2 cdiv(double2 a, double2 d) {
+  if (fabs(d.x) >= fabs(d.y)) {
+    double r = d.y / d.x;
+    double den = fma(d.y, r, d.x);
+    return make_double2(fma(a.y, r, a.x) / den, fma(-a.x, r, a.y) / den);
+  } else {
+    double r = d.x / d.y;
+    double den = fma(d.x, r, d.y);
+    return make_double2(fma(a.x, r, a.y) / den, fma(a.y, r, -a.x) / den);
+  }
+}
+
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC 2011, Sec. 3.2).
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 key) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+    c = make_uint4(hi1 ^ c.y ^ key.x, lo1, hi0 ^ c.w ^ key.y, lo0);
+    key.x += 0x9E3779B9u;
+    key.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+// Complex normal (re, im iid N(0, 1/2)) from one Philox block: two 53-bit
+// uniforms u1 in (0, 1], u2 in [0, 1), Box-Muller rho = sqrt(-log u1),
+// angle 2 pi u2.
+__device__ __forceinline__ double2 philox_complex_normal(uint64_t row, uint64_t col,
+                                                         uint64_t seed, uint32_t stream_id) {
+  const uint4 ctr = make_uint4((uint32_t)col, (uint32_t)(col >> 32), (uint32_t)row, stream_id);
+  const uint4 w = philox4x32_10(ctr, make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+  const uint64_t a = ((uint64_t)(w.x >> 5) << 26) + (uint64_t)(w.y >> 6);
+  const uint64_t b = ((uint64_t)(w.z >> 5) << 26) + (uint64_t)(w.w >> 6);
+  const double u1 = ((double)a + 1.0) * 0x1p-53;
+  const double u2 = (double)b * 0x1p-53;
+  const double rho = sqrt(-log(u1));
+  double s, c;
+  sincospi(2.0 * u2, &s, &c);
+  return make_double2(rho * c, rho * s);
+}
+#endif

@@ -1,0 +1,76 @@
+// Factorization of R (Sec. 2, "R2 = R1 T"): T = R1^-1 R2 by back substitution.
+//
+// The right-hand sides are independent (Sec. 3.2: the paper gives each
+// processor its own column), so each CTA takes a block of NR columns of R2
+// into shared memory and eliminates from the last row up: row j of the block
+// is divided by R1_jj, then column j of R1 (rows 0..j-1, staged in shared
+// memory) updates every row above it.  R1 (k x k, at most a few hundred KB)
+// stays in L2 for all CTAs.
+#include "rid_internal.cuh"
+
+namespace {
+
+constexpr int SOLVE_THREADS = 256;
+constexpr size_t SOLVE_SMEM_BUDGET = 200 * 1024;
+
+__global__ void __launch_bounds__(SOLVE_THREADS)
+solve_kernel(const double2* __restrict__ Y, int64_t ldy, int k, int64_t n, int nr,
+             double2* __restrict__ T, int64_t ldt) {
+  extern __shared__ double2 smem[];
+  double2* rhs = smem;                  // k x nr, row i at rhs[i * nr]
+  double2* rcol = smem + (size_t)k * nr; // column j of R1, rows 0..j-1
+  const int tid = threadIdx.x;
+  const int64_t c0 = (int64_t)blockIdx.x * nr;      // first column of T in this block
+  const int64_t ncols = n - k;
+  int nvalid = (int)((ncols - c0) < nr ? (ncols - c0) : nr);
+
+  for (int e = tid; e < k * nr; e += SOLVE_THREADS) {
+    const int c = e / k, i = e - c * k;
+    rhs[i * nr + c] = (c < nvalid) ? Y[i + (k + c0 + c) * ldy] : make_double2(0.0, 0.0);
+  }
+  for (int j = k - 1; j >= 0; --j) {
+    __syncthreads();
+    if (tid < nr) rhs[j * nr + tid] = cdiv(rhs[j * nr + tid], Y[j + (int64_t)j * ldy]);
+    for (int i = tid; i < j; i += SOLVE_THREADS) rcol[i] = Y[i + (int64_t)j * ldy];
+    __syncthreads();
+    for (int e = tid; e < j * nr; e += SOLVE_THREADS) {
+      const int i = e / nr, c = e - i * nr;
+      const double2 r = rcol[i], t = rhs[j * nr + c];
+      double2 x = rhs[e];
+      x.x = fma(-r.x, t.x, x.x);
+      x.x = fma(r.y, t.y, x.x);
+      x.y = fma(-r.x, t.y, x.y);
+      x.y = fma(-r.y, t.x, x.y);
+      rhs[e] = x;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < k * nr; e += SOLVE_THREADS) {
+    const int c = e / k, i = e - c * k;
+    if (c < nvalid) T[i + (c0 + c) * ldt] = rhs[i * nr + c];
+  }
+}
+
+}  // namespace
+
+size_t rid_solve_smem_bytes(int k, int* nr_out) {
+  int nr = 32;
+  while (nr > 1 && (size_t)(k * nr + k) * sizeof(double2) > SOLVE_SMEM_BUDGET) nr >>= 1;
+  if (nr_out) *nr_out = nr;
+  return (size_t)(k * nr + k) * sizeof(double2);
+}
+
+cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy, double2* T,
+                             int64_t ldt) {
+  const int64_t ncols = p->n - p->k;
+  if (ncols <= 0) return cudaSuccess;
+  int nr = 0;
+  const size_t smem = rid_solve_smem_bytes(p->k, &nr);
+  if (smem > SOLVE_SMEM_BUDGET) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const unsigned blocks = (unsigned)((ncols + nr - 1) / nr);
+  solve_kernel<<<blocks, SOLVE_THREADS, smem, p->stream>>>(Y, ldy, p->k, p->n, nr, T, ldt);
+  return cudaGetLastError();
+}
