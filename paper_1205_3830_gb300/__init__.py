@@ -47,6 +47,8 @@ def as_colmajor(x):
 
 
 def _ld(x):
+    if x.dim() < 2:
+        return max(int(x.shape[0]) if x.dim() else 1, 1)
     return max(int(x.stride(1)), int(x.shape[0]), 1)
 
 
@@ -55,7 +57,7 @@ class _CudaView:
 
     def __init__(self, ptr, shape, strides_bytes, typestr):
         self.__cuda_array_interface__ = {
-            "data": (int(ptr), True), "shape": tuple(shape), "strides": tuple(strides_bytes),
+            "data": (int(ptr), False), "shape": tuple(shape), "strides": tuple(strides_bytes),
             "typestr": typestr, "version": 3,
         }
 

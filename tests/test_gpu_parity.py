@@ -135,7 +135,7 @@ def test_error_estimate_matches_oracle(rid, shape, nprobe):
     est_o, up_o, Ew = oracle.error_estimate(A, perm, T, omega)
     with rid.Plan(m, n, k, l, seed=6) as plan:
         est, up = plan.error(to_dev_colmajor(A), torch.from_numpy(perm.astype(np.int32)).cuda(),
-                             to_dev_colmajor(T) if T.size else torch.empty(0, dtype=torch.complex128).cuda(),
+                             to_dev_colmajor(T) if T.size else torch.empty((k, 0), dtype=torch.complex128).cuda(),
                              nprobe=nprobe, probe_seed=77)
     # rounding bound on E w: |A| (|w~| + |T| |w_Jc| on J) times gamma_(n+k)
     w_abs = np.abs(omega)
