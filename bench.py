@@ -352,9 +352,14 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--m", type=int, default=0, help="override m (profiling of smaller cases)")
+    ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()
+    import dataclasses
     import synth
     cfg = synth.CONFIGS[args.config]
+    if args.m or args.n:
+        cfg = dataclasses.replace(cfg, m=args.m or cfg.m, n=args.n or cfg.n)
     world, rank, local = init_dist()
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)

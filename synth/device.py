@@ -9,9 +9,10 @@ from __future__ import annotations
 
 import math
 
+import numpy as np
 import torch
 
-from . import IDConfig
+from . import IDConfig, orthonormal_columns
 
 
 def _colmajor_randn(rows, cols, gen, device, dtype=torch.complex128):
@@ -37,8 +38,10 @@ def device_matrix(cfg: IDConfig, device="cuda"):
         # tail = eps / (sqrt(m) + sqrt(n)) * G, whose largest singular value is
         # about eps (edge of the Marchenko-Pastur law), so sigma_j = 1 for j <= r
         # and sigma_j <~ eps after.
-        U = torch.linalg.qr(torch.randn((m, r), generator=gen, dtype=c128, device=device))[0]
-        V = torch.linalg.qr(torch.randn((n, r), generator=gen, dtype=c128, device=device))[0]
+        # (the thin QRs run in numpy on the host: tall-skinny, a second or two)
+        rng = np.random.default_rng(int(cfg.seed))
+        U = torch.from_numpy(orthonormal_columns(rng, m, r)).to(device)
+        V = torch.from_numpy(orthonormal_columns(rng, n, r)).to(device)
         A = _colmajor_randn(m, n, gen, device).mul_(cfg.eps / (math.sqrt(m) + math.sqrt(n)))
         A.addmm_(U, V.conj().t())
         del U, V
