@@ -147,6 +147,23 @@ RID_API rid_status rid_sync_status(rid_plan_t plan);
  *   out[6] = mode (rid_mode)                       out[7] = dtype (rid_dtype) */
 RID_API rid_status rid_plan_stats(rid_plan_t plan, int64_t out[8]);
 
+/* Allocation-free pivoted QR (the paper has no counterpart: this is a service
+ * for callers that cannot call cudaMalloc, e.g. code running under another
+ * allocator's lock, or real-time loops that forbid allocation after start-up).
+ * Same computation and results as rid_select, without a plan:
+ *   Y (in/out, l x n complex128, column-major, ldy >= l), perm (out, int32[n]),
+ *   status (out, DEVICE int32: RID_OK, or RID_ERANK if the sketch has rank < k),
+ *   stream: cudaStream_t (NULL = legacy default stream).  Asynchronous.
+ *   Scratch: a fixed 20736-byte array inside this library (per device, held
+ *   until the process exits); nothing is allocated.  Limits: 1 <= k <= l <= 512,
+ *   k <= n; larger sizes return RID_EINVAL before any work.
+ *   All calls share the scratch array: calls whose work overlaps on the GPU
+ *   (other streams, other host threads) race; calls on one stream are safe.
+ *   The first call on a device looks up the array's device address; make that
+ *   first call before any stream capture. */
+RID_API rid_status rid_select_noalloc(void* Y, int64_t ldy, int32_t l, int64_t n, int32_t k,
+                                      int32_t* perm, int32_t* status, void* stream);
+
 /* Static, human-readable name of a status code. */
 RID_API const char* rid_status_string(rid_status status);
 

@@ -247,3 +247,88 @@ cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int3
   }
   return cudaSuccess;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free pivoted QR.
+//
+// Some callers cannot call cudaMalloc: code that runs inside another
+// allocator's critical section, real-time loops that forbid allocation after
+// start-up, or hosts whose device memory is fully owned by a pool they do not
+// control.  rid_select_noalloc gives them the select step without a plan:
+// its scratch (per-CTA argmax pairs, the last-CTA counter and the reflector
+// scalars tau) lives in the fixed-size array below, which every GPU that
+// loads this library holds until the process exits.  Every call shares that
+// array, so calls whose work overlaps on the GPU (different streams, or
+// different host threads on one device) race; calls on one stream are
+// ordered and safe.  The array keeps the last call's contents; each call
+// clears the counter it relies on before its first launch.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+namespace {
+
+constexpr int NOALLOC_MAX_GRID = 1024;                 // CTAs of one select launch
+constexpr int NOALLOC_MAX_STEPS = 32 * QR_PER_LANE;    // reflectors: k <= l <= 512
+constexpr size_t NOALLOC_OFF_VAL = 0;
+constexpr size_t NOALLOC_OFF_IDX = NOALLOC_OFF_VAL + NOALLOC_MAX_GRID * sizeof(double);
+constexpr size_t NOALLOC_OFF_TAU = NOALLOC_OFF_IDX + NOALLOC_MAX_GRID * sizeof(int);
+constexpr size_t NOALLOC_OFF_CNT = NOALLOC_OFF_TAU + NOALLOC_MAX_STEPS * sizeof(double2);
+constexpr size_t NOALLOC_SCRATCH_BYTES = (NOALLOC_OFF_CNT + sizeof(unsigned) + 255) / 256 * 256;
+static_assert(NOALLOC_SCRATCH_BYTES == 20736, "scratch layout changed: update include/rid.h");
+
+static __device__ __align__(256) unsigned char g_select_scratch[NOALLOC_SCRATCH_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_scratch_mutex;
+unsigned char* g_scratch_addr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of g_select_scratch on the current device (looked up once per device).
+cudaError_t scratch_address(unsigned char** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_select_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_addr[dev] = (unsigned char*)ptr;
+  }
+  *out = g_scratch_addr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" RID_API rid_status rid_select_noalloc(void* Y, int64_t ldy, int32_t l, int64_t n, int32_t k,
+                                                 int32_t* perm, int32_t* status, void* stream) {
+  if (!Y || !perm || !status) return RID_EINVAL;
+  if (l < 1 || n < 1 || k < 1 || k > l || k > n || ldy < l || n > 0x7fffffffLL) return RID_EINVAL;
+  if (l > NOALLOC_MAX_STEPS) return RID_EINVAL;        // beyond the static scratch / register tile
+  if (((uintptr_t)Y & 15u) || ((uintptr_t)perm & 3u) || ((uintptr_t)status & 3u)) return RID_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  unsigned char* scratch = nullptr;
+  if (scratch_address(&scratch) != cudaSuccess) return RID_ECUDA;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return RID_ECUDA;
+  int64_t grid = (n + 7) / 8;
+  if (grid > 4 * (int64_t)sms) grid = 4 * (int64_t)sms;
+  if (grid > NOALLOC_MAX_GRID) grid = NOALLOC_MAX_GRID;
+  SelectArgs a{(double2*)Y, ldy, l, k, n, perm,
+               (double*)(scratch + NOALLOC_OFF_VAL), (int*)(scratch + NOALLOC_OFF_IDX),
+               (unsigned*)(scratch + NOALLOC_OFF_CNT), (double2*)(scratch + NOALLOC_OFF_TAU),
+               (int*)status};
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(a.counter, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return RID_ECUDA;
+  select_init_kernel<<<(unsigned)grid, QR_THREADS, 0, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return RID_ECUDA;
+  for (int j = 0; j < k; ++j) {
+    select_step_kernel<<<(unsigned)grid, QR_THREADS, 0, s>>>(a, j);
+    if (cudaGetLastError() != cudaSuccess) return RID_ECUDA;
+  }
+  return RID_OK;
+}
