@@ -10,6 +10,7 @@
 rid_status rid_tc_plan_init(rid_plan_s* p);
 void rid_tc_plan_free(rid_plan_s* p);
 cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+int rid_tc_error_word(const rid_plan_s* p);
 
 namespace {
 
@@ -259,6 +260,7 @@ rid_status rid_error(rid_plan_t p, const void* A, int64_t lda, const int32_t* pe
   if (e != cudaSuccess) return from_cuda(e);
   out[0] = host[0];
   out[1] = host[1];
+  if (p->mode != RID_FP64_NATIVE && rid_tc_error_word(p) != 0) return RID_ETIMEOUT;
   return status == RID_OK ? RID_OK : (rid_status)status;
 }
 
@@ -283,6 +285,7 @@ rid_status rid_sync_status(rid_plan_t p) {
   cudaError_t e = cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
   if (e != cudaSuccess) return from_cuda(e);
+  if (p->mode != RID_FP64_NATIVE && rid_tc_error_word(p) != 0) return RID_ETIMEOUT;
   return (rid_status)status;
 }
 

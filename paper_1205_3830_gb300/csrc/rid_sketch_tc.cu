@@ -1,14 +1,610 @@
-// Tensor-core sketch paths (FP64-emulated and mixed precision).
-#include "rid_internal.cuh"
+// Randomization Y = Omega A (Sec. 2) on the tcgen05 tensor cores with an
+// FP64-grade result: an exact-slice (Ozaki-type) emulation of the complex128
+// product from BF16 digits with FP32 accumulation.
+//
+// Real view.  With A and Omega stored as interleaved complex numbers, the
+// complex product is the real product Y' = Omega' A' of a (2l x 2m) matrix
+// Omega' (row 2i = (Re w, -Im w, ...), row 2i+1 = (Im w, Re w, ...)) with the
+// (2m x n) matrix A' whose column j is A's column j read as 2m doubles.  Y'
+// column j is Y's column j read as 2l doubles, so no data is reordered.
+//
+// Digits.  Each real value x in a 256-long chunk c of a column (of A') or in a
+// row (of Omega') is written x = 2^(e-8) sum_s v_s with e the chunk's (row's)
+// binary exponent (|x| < 2^e), v_s = d_s 2^(-8s), d_0 in [0, 256] and
+// d_s in [-128, 127] for s >= 1 (balanced base-256 digits of x rounded to
+// 8S bits).  Every v_s is exact in BF16.  The products of a slice pair (s, t)
+// carry the scale 2^(-8(s+t)); pairs with s + t <= S-1 are kept.
+//
+// Exact accumulation.  Within one chunk (256 products per pair) the tensor
+// core's FP32 sums are exact for the diagonals s+t = 0, 1 and 2 kept apart
+// (|sum| < 2^24 units of each diagonal's last bit); the diagonals s+t >= 3 go
+// to a fourth accumulator whose rounding error is below 2^-48 of the chunk's
+// leading term.  So a CTA holds four TMEM accumulators of 128 x 128 FP32
+// (all 512 columns).  After each chunk the flush warps read the four groups,
+// scale them by 2^(e_A(j,c) - E_A(j)) (E_A = the column's largest chunk
+// exponent) and add them to a double-FP32 (hi + lo) running sum.  The
+// groups are released to the MMA warp one by one, in the order the next
+// chunk needs them, so flushing overlaps the next chunk's products.
+//
+// Tiles.  M = 128 columns of A (TMEM lanes), N <= 128 rows of Omega' (TMEM
+// columns; N = 128 runs at the full tensor rate), K in 16-element stages with
+// the 32-byte swizzle: one stage holds S A-slice tiles and S Omega-slice
+// tiles (4 KB each).  A K-split over CTAs balances the waves; partial sums are
+// reduced in a fixed order, so results are deterministic.
+#include <climits>
+#include <cudaTypedefs.h>
 
-rid_status rid_tc_plan_init(rid_plan_s* p) {
-  (void)p;
-  return RID_EUNSUPPORTED;
+#include "rid_internal.cuh"
+#include "rid_tc.cuh"
+
+using namespace rid_tc;
+
+namespace {
+
+constexpr int TC_S = 7;                 // digits per value: 56 bits
+constexpr int TC_G = 4;                 // accumulator groups
+constexpr int TC_KC = 256;              // chunk of the reduction with exact FP32 sums
+constexpr int TC_KS = 16;               // K per pipeline stage (one MMA per slice pair)
+constexpr int TC_STAGES = 4;
+constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // 4 KB: 128 rows x 32 bytes
+constexpr int TC_STAGE_BYTES = 2 * TC_S * TC_TILE_BYTES;
+constexpr int TC_THREADS = 512;         // warps 0-11 flush, 12 TMA, 13 MMA + TMEM, 14-15 idle
+constexpr int TC_FLUSH_WARPS = 12;
+constexpr int TC_LAUNCH_REGS = 128;    // 65536 / 512: the pool the setmaxnreg split assumes
+constexpr int TC_EXP_ZERO = -30000;     // exponent of an all-zero chunk / row
+constexpr long long TC_WAIT_BUDGET = 4000000000ll;   // clock cycles (~2 s)
+
+struct TcState {
+  int S;
+  int64_t KP;             // padded reduction length (multiple of TC_KC)
+  int NC;                 // chunks
+  int l2;                 // 2l rows of Omega'
+  int ntiles;             // N-tiles of <= 128 rows
+  int nblocks;            // column blocks of 128
+  int ksplit;             // K-splits
+  int chunks_per_split;
+  uint16_t* om_slices;    // [S][l2][KP] bf16
+  int* om_exp;            // [l2]
+  uint16_t* a_slices;     // [S][n][KP] bf16
+  int* a_exp;             // [n][NC]
+  int* a_exp_max;         // [n]
+  float2* partial;        // [ksplit][n][l2p]: (hi, lo) of each running sum
+  int l2p;
+  int* err;               // device error word
+  CUtensorMap map_a, map_om;
+};
+
+// ---- digits --------------------------------------------------------------------
+// Exponent e of x (|x| < 2^e, x = f 2^e with 1/2 <= |f| < 1); subnormals and
+// zero count as zero.
+__device__ __forceinline__ int exp_of(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  return ex == 0 ? TC_EXP_ZERO : ex - 1022;
 }
 
-void rid_tc_plan_free(rid_plan_s* p) { (void)p; }
+// Balanced base-256 digits of x relative to exponent e (|x| < 2^e):
+// round(|x| 2^(8S-e)) = sum_s d_s 256^(S-1-s), d_0 in [0, 256], others in
+// [-128, 127]; stored as BF16 bits of +-d_s 2^(-8s).
+__device__ __forceinline__ void digits_of(double x, int e, uint16_t (&out)[TC_S]) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long q = 0;
+  if (ex != 0 && e != TC_EXP_ZERO) {
+    const unsigned long long mant = (unsigned long long)(b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (ex - 1075) + 8 * TC_S - e;
+    if (sh >= 0) {
+      q = mant << sh;
+    } else if (sh > -62) {
+      q = (mant + (1ull << (-sh - 1))) >> (-sh);
+    }
+  }
+  const bool neg = b < 0;
+  int d[TC_S];
+#pragma unroll
+  for (int s = TC_S - 1; s >= 1; --s) {
+    int v = (int)(q & 0xFF);
+    q >>= 8;
+    if (v >= 128) {
+      v -= 256;
+      q += 1;
+    }
+    d[s] = v;
+  }
+  d[0] = (int)q;
+#pragma unroll
+  for (int s = 0; s < TC_S; ++s) {
+    float f = (float)(neg ? -d[s] : d[s]);
+    f = __fmul_rn(f, __int_as_float((127 - 8 * s) << 23));   // * 2^(-8s)
+    out[s] = (uint16_t)(__float_as_uint(f) >> 16);
+  }
+}
 
-cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy) {
-  (void)p; (void)A; (void)lda; (void)Y; (void)ldy;
-  return cudaErrorNotSupported;
+// ---- Omega' slices (plan time) ---------------------------------------------------
+// Row exponent of Omega' rows 2i and 2i+1 (same values): max over the row.
+__global__ void omega_exp_kernel(const double2* __restrict__ om, int64_t ldo, int64_t m, int* __restrict__ om_exp) {
+  __shared__ int red[8];
+  const int i = blockIdx.x;
+  int e = TC_EXP_ZERO;
+  for (int64_t r = threadIdx.x; r < m; r += blockDim.x) {
+    const double2 w = om[i * ldo + r];
+    e = max(e, max(exp_of(w.x), exp_of(w.y)));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int v = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = max(v, red[w]);
+    om_exp[2 * i] = v;
+    om_exp[2 * i + 1] = v;
+  }
+}
+
+// Digits of Omega' rows: row 2i = (Re w_r, -Im w_r), row 2i+1 = (Im w_r, Re w_r).
+__global__ void omega_slice_kernel(const double2* __restrict__ om, int64_t ldo, int64_t m, int l, int64_t KP,
+                                   const int* __restrict__ om_exp, uint16_t* __restrict__ slices) {
+  const int64_t per_row = KP / 2;      // complex positions per row, incl. padding
+  const int64_t total = (int64_t)l * per_row;
+  const int64_t slice_stride = (int64_t)2 * l * KP;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int i = (int)(e / per_row);
+    const int64_t r = e - (int64_t)i * per_row;
+    const double2 w = r < m ? om[i * ldo + r] : make_double2(0.0, 0.0);
+    const int ex = om_exp[2 * i];
+    uint16_t re[TC_S], nim[TC_S], im[TC_S];
+    digits_of(w.x, ex, re);
+    digits_of(-w.y, ex, nim);
+    digits_of(w.y, ex, im);
+    for (int s = 0; s < TC_S; ++s) {
+      uint16_t* row0 = slices + s * slice_stride + (int64_t)(2 * i) * KP + 2 * r;
+      uint16_t* row1 = row0 + KP;
+      *(uint32_t*)row0 = (uint32_t)re[s] | ((uint32_t)nim[s] << 16);
+      *(uint32_t*)row1 = (uint32_t)im[s] | ((uint32_t)re[s] << 16);
+    }
+  }
+}
+
+// ---- A' slices (every call) -------------------------------------------------------
+// One warp per (column j, chunk c): 128 complex rows = 256 real values.
+__global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict__ A, int64_t lda, int64_t m,
+                                                      int64_t n, int NC, int64_t KP,
+                                                      uint16_t* __restrict__ slices, int* __restrict__ a_exp,
+                                                      int* __restrict__ a_exp_max) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tasks = n * NC;
+  const int64_t slice_stride = n * KP;
+  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks;
+       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t j = t / NC;
+    const int c = (int)(t - j * NC);
+    double2 x[4];
+    int e = TC_EXP_ZERO;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = (int64_t)c * 128 + lane + 32 * u;
+      x[u] = r < m ? __ldg(A + j * lda + r) : make_double2(0.0, 0.0);
+      e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
+    }
+    e = __reduce_max_sync(0xffffffffu, e);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int64_t r = (int64_t)c * 128 + lane + 32 * u;
+      uint16_t re[TC_S], im[TC_S];
+      digits_of(x[u].x, e, re);
+      digits_of(x[u].y, e, im);
+#pragma unroll
+      for (int s = 0; s < TC_S; ++s)
+        *(uint32_t*)(slices + s * slice_stride + j * KP + 2 * r) = (uint32_t)re[s] | ((uint32_t)im[s] << 16);
+    }
+    if (lane == 0) {
+      a_exp[j * NC + c] = e;
+      atomicMax(a_exp_max + j, e);
+    }
+  }
+}
+
+// ---- the tensor-core product ----------------------------------------------------------
+__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
+struct TcArgs {
+  int n, l2, l2p, NC, chunks_per_split, ntiles;
+  const int* a_exp;
+  const int* a_exp_max;
+  float2* partial;
+  int* err;
+};
+
+__device__ __forceinline__ int group_of(int d) { return d >= 3 ? 3 : d; }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_om, TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
+  __shared__ uint64_t acc_full[TC_G], acc_empty[TC_G], mma_done;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_abort;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // blockIdx.x walks the N-tiles of one column block first, so the CTAs that
+  // share an A tile run together and read it from L2
+  const int nb = blockIdx.x % a.ntiles, jb = blockIdx.x / a.ntiles, ks = blockIdx.y;
+  const int c_begin = ks * a.chunks_per_split;
+  const int c_end = min(a.NC, c_begin + a.chunks_per_split);
+  const int nchunks = max(0, c_end - c_begin);
+  const int row0 = nb * 128;
+  const int n_tile = min(128, a.l2 - row0);
+  const int n_mma = (n_tile + 15) & ~15;
+
+  if (warp == 13) tmem_alloc(&tmem_slot, 512);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TC_STAGES; ++i) {
+      mbar_init(&full_bar[i], 1);
+      mbar_init(&empty_bar[i], 1);
+    }
+    for (int g = 0; g < TC_G; ++g) {
+      mbar_init(&acc_full[g], 1);
+      mbar_init(&acc_empty[g], TC_FLUSH_WARPS);
+    }
+    mbar_init(&mma_done, 1);
+    fence_barrier_init();
+    s_abort = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  auto a_tile = [&](int slot, int s) { return smem + slot * TC_STAGE_BYTES + s * TC_TILE_BYTES; };
+  auto o_tile = [&](int slot, int s) { return smem + slot * TC_STAGE_BYTES + (TC_S + s) * TC_TILE_BYTES; };
+  auto fail = [&](int code) {
+    s_abort = 1;
+    atomicCAS(a.err, 0, code);
+  };
+
+  if (warp >= 12) {
+    // Warpgroup 3 (producer, MMA, two idle warps) gives registers to the flush
+    // warpgroups: 128 x 56 + 384 x 152 = 512 x 128, the launch allocation.
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
+    if (warp == 12 && lane == 0) {
+      // ---------------- TMA producer ----------------
+      prefetch_tensormap(&map_a);
+      prefetch_tensormap(&map_om);
+      const int iters = nchunks * (TC_KC / TC_KS);
+      int it = 0;
+      for (; it < iters && !s_abort; ++it) {
+        const int slot = it % TC_STAGES, round = it / TC_STAGES;
+        if (round > 0 && !mbar_wait(&empty_bar[slot], (round - 1) & 1, TC_WAIT_BUDGET)) {
+          fail(11);
+          break;
+        }
+        const int c = c_begin + it / (TC_KC / TC_KS);
+        const int x = c * TC_KC + (it % (TC_KC / TC_KS)) * TC_KS;
+        mbar_arrive_expect_tx(&full_bar[slot], TC_STAGE_BYTES);
+#pragma unroll
+        for (int s = 0; s < TC_S; ++s) tma_load_3d(&map_a, &full_bar[slot], a_tile(slot, s), x, jb * 128, s);
+#pragma unroll
+        for (int s = 0; s < TC_S; ++s) tma_load_3d(&map_om, &full_bar[slot], o_tile(slot, s), x, row0, s);
+      }
+      // wind-down: every issued load must land before the CTA may exit
+      for (int k = max(0, it - TC_STAGES); k < it; ++k)
+        if (!mbar_wait(&full_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET)) fail(12);
+    } else if (warp == 13 && lane == 0) {
+      // ---------------- MMA issuer ----------------
+      const uint32_t idesc = idesc_bf16_f32(128, n_mma);
+      const int stages_per_chunk = TC_KC / TC_KS;
+      for (int cl = 0; cl < nchunks && !s_abort; ++cl) {
+        for (int b = 0; b < stages_per_chunk && !s_abort; ++b) {
+          const int it = cl * stages_per_chunk + b;
+          const int slot = it % TC_STAGES, round = it / TC_STAGES;
+          if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET)) {
+            fail(21);
+            break;
+          }
+          tc_fence_after();
+#pragma unroll
+          for (int d = TC_S - 1; d >= 0; --d) {
+            const int g = group_of(d);
+            const bool group_start = (d == TC_S - 1) || (d < 3);   // first diagonal of its group
+            if (b == 0 && group_start && cl > 0) {
+              if (!mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)) {
+                fail(22);
+                break;
+              }
+              tc_fence_after();
+            }
+#pragma unroll
+            for (int s = 0; s <= d; ++s) {
+              const int t = d - s;
+              if (s >= TC_S || t >= TC_S) continue;
+              const uint32_t acc = (b == 0 && group_start && s == 0) ? 0u : 1u;
+              mma_bf16(tmem + (uint32_t)(g * 128), desc_sw32(a_tile(slot, t)), desc_sw32(o_tile(slot, s)), idesc,
+                       acc);
+            }
+            const bool group_end = (d <= 3);     // last diagonal of its group in this stage
+            if (b == stages_per_chunk - 1 && group_end) mma_commit(&acc_full[g]);
+          }
+          mma_commit(&empty_bar[slot]);
+        }
+      }
+      mma_commit(&mma_done);
+    }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 152;\n" ::: "memory");
+    // ---------------- flush warps (0..11) ----------------
+    // Warp w reads TMEM lanes 32 (w % 4) .. +31 (the hardware's lane quarter
+    // of the warp) and tile columns 48 (w / 4) .. : 48, 48 and 32 columns.
+    const int quarter = warp & 3, third = warp >> 2;
+    const int col0 = third * 48;
+    const int nblk = third < 2 ? 3 : 2;              // 16-column blocks of this warp
+    const int64_t j = (int64_t)jb * 128 + quarter * 32 + lane;
+    const bool j_ok = j < a.n;
+    const int emax = j_ok ? a.a_exp_max[j] : TC_EXP_ZERO;
+    float hi[48], lo[48];
+#pragma unroll
+    for (int i = 0; i < 48; ++i) {
+      hi[i] = 0.f;
+      lo[i] = 0.f;
+    }
+    const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
+    for (int cl = 0; cl < nchunks && !s_abort; ++cl) {
+      const int c = c_begin + cl;
+      const int e = j_ok ? a.a_exp[j * a.NC + c] : TC_EXP_ZERO;
+      const int delta = e - emax;
+      const float scale = delta >= -126 ? __int_as_float((127 + delta) << 23) : 0.f;
+      for (int gi = 0; gi < TC_G; ++gi) {
+        const int g = TC_G - 1 - gi;
+        const bool ok = mbar_wait(&acc_full[g], cl & 1, TC_WAIT_BUDGET);
+        __syncwarp();
+        if (!ok) {
+          fail(31);
+          break;
+        }
+        tc_fence_after();
+#pragma unroll
+        for (int h2 = 0; h2 < 3; ++h2) {
+          if (h2 < nblk) {
+            uint32_t r[16];
+            tmem_ld16(lane_base + (uint32_t)(g * 128 + h2 * 16), r);
+            tmem_ld_wait();
+            if (h2 == nblk - 1) {        // all columns read: the group may be overwritten
+              tc_fence_before();
+              __syncwarp();
+              if (lane == 0) mbar_arrive(&acc_empty[g]);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+              const int i = h2 * 16 + q;
+              const float v = __fmul_rn(__uint_as_float(r[q]), scale);
+              const float s = __fadd_rn(hi[i], v);
+              const float bp = __fsub_rn(s, hi[i]);
+              const float err = __fadd_rn(__fsub_rn(hi[i], __fsub_rn(s, bp)), __fsub_rn(v, bp));
+              hi[i] = s;
+              lo[i] = __fadd_rn(lo[i], err);
+            }
+          }
+        }
+      }
+    }
+    if (!s_abort && j_ok) {
+      float2* dst = a.partial + ((int64_t)ks * a.n + j) * a.l2p + row0 + col0;
+#pragma unroll
+      for (int i = 0; i < 48; ++i)
+        if (i < nblk * 16 && col0 + i < n_tile) dst[i] = make_float2(hi[i], lo[i]);
+    }
+  }
+
+  // ---------------- teardown ----------------
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 13) {
+    if (!mbar_wait(&mma_done, 0, TC_WAIT_BUDGET)) fail(91);
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+// Y(i, j) = 2^(E_om + E_A - 16) sum_split partial, rows 2i / 2i+1 -> Re / Im.
+__global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit, int64_t n, int l, int l2p,
+                                 const int* __restrict__ om_exp, const int* __restrict__ a_exp_max,
+                                 double2* __restrict__ Y, int64_t ldy) {
+  const int64_t total = n * l;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / l;
+    const int i = (int)(e - j * l);
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < ksplit; ++s) {
+      const float2* p = partial + ((int64_t)s * n + j) * l2p + 2 * i;
+      re += (double)p[0].x + (double)p[0].y;
+      im += (double)p[1].x + (double)p[1].y;
+    }
+    const int ea = a_exp_max[j];
+    Y[i + j * ldy] = make_double2(ea == TC_EXP_ZERO ? 0.0 : ldexp(re, om_exp[2 * i] + ea - 16),
+                                  ea == TC_EXP_ZERO ? 0.0 : ldexp(im, om_exp[2 * i + 1] + ea - 16));
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  }
+  return enc;
+}
+
+// 3D bf16 tensor [slices][rows][KP] with a box of 16 x 128 x 1 and the 32-byte swizzle.
+int make_slice_map(CUtensorMap* map, const void* base, int64_t KP, int64_t rows, int slices) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return -1;
+  cuuint64_t gdim[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)slices};
+  cuuint64_t gstride[2] = {(cuuint64_t)KP * 2, (cuuint64_t)(KP * 2 * rows)};
+  cuuint32_t box[3] = {TC_KS, 128, 1};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, gdim, gstride, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? 0 : (int)r;
+}
+
+int choose_ksplit(int units, int NC, int sms) {
+  int best = 1;
+  double best_eff = 0.0;
+  const int max_split = max(1, NC / 8);
+  for (int ks = 1; ks <= min(max_split, 64); ++ks) {
+    const double waves = (double)units * ks / sms;
+    const double eff = waves / ceil(waves);
+    // prefer fuller waves; among equals, fewer splits
+    if (eff > best_eff + 1e-9 && (waves >= 1.0 || ks == max_split)) {
+      best_eff = eff;
+      best = ks;
+    }
+    if (best_eff > 0.999) break;
+  }
+  if (best_eff == 0.0) best = min(max_split, (sms + units - 1) / units);
+  return best;
+}
+
+}  // namespace
+
+void rid_tc_plan_free(rid_plan_s* p);
+
+rid_status rid_tc_plan_init(rid_plan_s* p) {
+  if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
+  TcState* st = (TcState*)calloc(1, sizeof(TcState));
+  if (!st) return RID_ENOMEM;
+  st->S = TC_S;
+  st->NC = (int)((2 * p->m + TC_KC - 1) / TC_KC);
+  st->KP = (int64_t)st->NC * TC_KC;
+  st->l2 = 2 * p->l;
+  st->ntiles = (st->l2 + 127) / 128;
+  st->l2p = st->ntiles * 128;
+  st->nblocks = (int)((p->n + 127) / 128);
+  st->ksplit = choose_ksplit(st->ntiles * st->nblocks, st->NC, p->num_sms);
+  st->chunks_per_split = (st->NC + st->ksplit - 1) / st->ksplit;
+  st->ksplit = (st->NC + st->chunks_per_split - 1) / st->chunks_per_split;
+
+  const size_t om_bytes = (size_t)TC_S * st->l2 * st->KP * 2;
+  const size_t a_bytes = (size_t)TC_S * p->n * st->KP * 2;
+  const size_t aexp_bytes = (size_t)p->n * st->NC * 4;
+  const size_t part_bytes = (size_t)st->ksplit * p->n * st->l2p * 8;
+  auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
+  const size_t total = al(om_bytes) + al(a_bytes) + al(aexp_bytes) + al((size_t)p->n * 4) +
+                       al((size_t)st->l2 * 4) + al(part_bytes) + al(4);
+  char* base = nullptr;
+  if (cudaMalloc((void**)&base, total) != cudaSuccess) {
+    cudaGetLastError();
+    free(st);
+    return RID_ENOMEM;
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) { char* ptr = base + off; off += al(bytes); return ptr; };
+  st->om_slices = (uint16_t*)take(om_bytes);
+  st->a_slices = (uint16_t*)take(a_bytes);
+  st->a_exp = (int*)take(aexp_bytes);
+  st->a_exp_max = (int*)take((size_t)p->n * 4);
+  st->om_exp = (int*)take((size_t)st->l2 * 4);
+  st->partial = (float2*)take(part_bytes);
+  st->err = (int*)take(4);
+  p->tc_state = st;
+  p->tc_bytes = total;
+  p->tc_sketch_launches = 3;
+
+  if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S) ||
+      make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S)) {
+    rid_tc_plan_free(p);
+    return RID_ECUDA;
+  }
+  cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
+  if (e == cudaSuccess) {
+    omega_exp_kernel<<<p->l, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, st->om_exp);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) {
+    int64_t blocks = ((int64_t)p->l * (st->KP / 2) + 255) / 256;
+    if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
+    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, p->l, st->KP,
+                                                                 st->om_exp, st->om_slices);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             TC_STAGES * TC_STAGE_BYTES + 1024);
+  if (e == cudaSuccess) {
+    // setmaxnreg moves registers between warpgroups inside the launch
+    // allocation; it is only safe if the kernel launches with exactly the
+    // 128 registers per thread the split adds up to.
+    cudaFuncAttributes fa;
+    e = cudaFuncGetAttributes(&fa, sketch_tc_kernel);
+    if (e == cudaSuccess && fa.numRegs != TC_LAUNCH_REGS) {
+      rid_tc_plan_free(p);
+      return RID_EUNSUPPORTED;
+    }
+  }
+  if (e != cudaSuccess) {
+    rid_tc_plan_free(p);
+    return RID_ECUDA;
+  }
+  return RID_OK;
+}
+
+void rid_tc_plan_free(rid_plan_s* p) {
+  TcState* st = (TcState*)p->tc_state;
+  if (!st) return;
+  cudaStreamSynchronize(p->stream);
+  cudaFree(st->om_slices);   // start of the single allocation
+  free(st);
+  p->tc_state = nullptr;
+  p->tc_bytes = 0;
+}
+
+cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
+  const TcState* st = (const TcState*)p->tc_state;
+  if (!st) return cudaErrorNotSupported;
+  const double2* A = (const double2*)A_;
+  // 0x80808080 is below every exponent: the running maximum starts there
+  cudaError_t e = cudaMemsetAsync(st->a_exp_max, 0x80, (size_t)p->n * 4, p->stream);
+  if (e != cudaSuccess) return e;
+  {
+    const int64_t tasks = p->n * (int64_t)st->NC;
+    int64_t blocks = (tasks * 32 + 255) / 256;
+    if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
+    a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, p->n, st->NC, st->KP, st->a_slices,
+                                                             st->a_exp, st->a_exp_max);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles,
+              st->a_exp, st->a_exp_max, st->partial, st->err};
+  const dim3 grid((unsigned)(st->ntiles * st->nblocks), (unsigned)st->ksplit);
+  sketch_tc_kernel<<<grid, TC_THREADS, TC_STAGES * TC_STAGE_BYTES + 1024, p->stream>>>(st->map_a, st->map_om, args);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    const int64_t total = p->n * (int64_t)p->l;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
+    tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->l, st->l2p,
+                                                               st->om_exp, st->a_exp_max, Y, ldy);
+    e = cudaGetLastError();
+  }
+  return e;
+}
+
+int rid_tc_error_word(const rid_plan_s* p) {
+  const TcState* st = (const TcState*)p->tc_state;
+  if (!st) return 0;
+  int h = 0;
+  cudaMemcpyAsync(&h, st->err, 4, cudaMemcpyDeviceToHost, p->stream);
+  cudaStreamSynchronize(p->stream);
+  return h;
 }

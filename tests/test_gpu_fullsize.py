@@ -46,6 +46,8 @@ def run_case(rid, cfg, mode):
         Om = oracle.gaussian_test_matrix(l, m, cfg.seed)
         Yo = oracle.randomize(Om, A_h)
         bound = 4 * (2 * m * U64) * np.outer(np.linalg.norm(Om, axis=1), np.linalg.norm(A_h, axis=0))
+        if mode != "fp64":    # emulation: 2^-46 (2m) max|Omega_i| max|A_j|
+            bound = bound + 2.0 ** -46 * (2 * m) * np.outer(np.abs(Om).max(axis=1), np.abs(A_h).max(axis=0))
         assert np.all(np.abs(Y_h - Yo) <= bound)
         Ro, _, perm_o = oracle.qr_select(Yo, k)
         To = oracle.factor_r(Ro[:k, :k], Ro[:k, k:])
@@ -65,8 +67,9 @@ def run_case(rid, cfg, mode):
         assert est <= 10 * math.sqrt(1 + k * (n - k)) * 1.1 * cfg.eps
 
 
-def test_large_tall_32gib(rid):
-    run_case(rid, synth.CONFIGS["large_tall"], "fp64")
+@pytest.mark.parametrize("mode", ["fp64", "fp64_emulated"])
+def test_large_tall_32gib(rid, mode):
+    run_case(rid, synth.CONFIGS["large_tall"], mode)
 
 
 def test_large_square_16gib(rid):

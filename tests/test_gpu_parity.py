@@ -60,23 +60,62 @@ def test_omega_matches_oracle(rid, shape):
     assert np.all(np.abs(Om - Oo) <= 1e-14 * (1 + np.abs(Oo)))
 
 
+MODES = ["fp64", "fp64_emulated"]
+
+
+def emulation_bound(Om, A):
+    """Extra error of the tensor-core emulation: 56-bit digits of every value
+    (relative to its row / chunk maximum), the dropped slice pairs and the
+    double-FP32 running sums stay below 2^-46 (2m) max|Omega_i| max|A_j|."""
+    m = A.shape[0]
+    return 2.0 ** -46 * (2 * m) * np.outer(np.abs(Om).max(axis=1), np.abs(A).max(axis=0))
+
+
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", SHAPES, ids=str)
-def test_sketch_matches_oracle(rid, shape):
+def test_sketch_matches_oracle(rid, shape, mode):
     m, n, k, l = shape
     A = lowrank(m, n, k)
     Oo = oracle.gaussian_test_matrix(l, m, 5)
-    with rid.Plan(m, n, k, l, seed=5) as plan:
+    with rid.Plan(m, n, k, l, seed=5, mode=mode) as plan:
         plan.set_omega(torch.from_numpy(Oo).cuda())
         Y = to_host(plan.sketch(to_dev_colmajor(A)))
+        plan.sync_status()
     Yo = oracle.randomize(Oo, A)
-    assert np.all(np.abs(Y - Yo) <= dot_bound(Oo, A))
+    tol = dot_bound(Oo, A) + (emulation_bound(Oo, A) if mode != "fp64" else 0.0)
+    assert np.all(np.abs(Y - Yo) <= tol)
 
 
-def test_sketch_integer_inputs_bit_exact(rid):
+@pytest.mark.parametrize("mode", MODES)
+def test_sketch_wide_dynamic_range(rid, mode):
+    """Rows of A scaled by 2^-40 .. 2^40, zero columns and a zero row block:
+    the per-chunk exponents keep every chunk at full relative precision."""
+    m, n, k, l = 1200, 300, 10, 16
+    A = lowrank(m, n, k, eps=1e-3)
+    A *= (2.0 ** np.linspace(-40, 40, m))[:, None]
+    A[:, [0, 7, 299]] = 0.0
+    A[256:512, :] = 0.0
+    Oo = oracle.gaussian_test_matrix(l, m, 8)
+    with rid.Plan(m, n, k, l, seed=8, mode=mode) as plan:
+        plan.set_omega(torch.from_numpy(Oo).cuda())
+        Y = to_host(plan.sketch(to_dev_colmajor(A)))
+        plan.sync_status()
+    Yo = oracle.randomize(Oo, A)
+    assert np.all(Y[:, [0, 7, 299]] == 0)
+    # chunk-relative bound: each 128-row chunk contributes at its own scale
+    chunk_max = np.zeros_like(np.abs(A))
+    for c0 in range(0, m, 128):
+        chunk_max[c0:c0 + 128] = np.abs(A[c0:c0 + 128]).max(axis=0, keepdims=True)
+    tol = dot_bound(Oo, A) + 2.0 ** -46 * 256 * np.abs(Oo).max(axis=1)[:, None] * chunk_max.sum(axis=0)[None, :]
+    assert np.all(np.abs(Y - Yo) <= tol)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_sketch_integer_inputs_bit_exact(rid, mode):
     m, n, k, l = 1500, 700, 20, 37
     A = synth.integer_valued(m, n, 64, seed=1)
     Oi = np.ascontiguousarray(synth.integer_valued(m, l, 64, seed=2).T)
-    with rid.Plan(m, n, k, l, seed=1) as plan:
+    with rid.Plan(m, n, k, l, seed=1, mode=mode) as plan:
         plan.set_omega(torch.from_numpy(Oi).cuda())
         Y = to_host(plan.sketch(to_dev_colmajor(A)))
     assert np.array_equal(Y, oracle.randomize(Oi, A))
@@ -147,14 +186,15 @@ def test_error_estimate_matches_oracle(rid, shape, nprobe):
     assert abs(up - up_o) <= 10 * math.sqrt(2 / math.pi) * np.max(bound_q) + 1e-14 * up_o
 
 
+@pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("shape", SHAPES, ids=str)
-def test_whole_id_matches_oracle(rid, shape):
+def test_whole_id_matches_oracle(rid, shape, mode):
     m, n, k, l = shape
     seed = 20 + m
     A = lowrank(m, n, k)
     out = oracle.rid(A, k, l, seed=seed)
     Ad = to_dev_colmajor(A)
-    res = rid.decompose(Ad, k, l, seed=seed, nprobe=8, probe_seed=3)
+    res = rid.decompose(Ad, k, l, seed=seed, nprobe=8, probe_seed=3, mode=mode)
     perm, T = to_host(res["perm"]), to_host(res["T"])
     assert np.array_equal(perm[:k], out["J"])
     if T.size:
@@ -188,10 +228,11 @@ def test_rank_deficient_sketch_reports_erank(rid):
         assert res["perm"].shape == (n,)
 
 
-def test_results_are_deterministic(rid):
+@pytest.mark.parametrize("mode", MODES)
+def test_results_are_deterministic(rid, mode):
     m, n, k, l = 2048, 1024, 32, 40
     A = to_dev_colmajor(lowrank(m, n, k))
-    r1 = rid.decompose(A, k, l, seed=2)
-    r2 = rid.decompose(A, k, l, seed=2)
+    r1 = rid.decompose(A, k, l, seed=2, mode=mode)
+    r2 = rid.decompose(A, k, l, seed=2, mode=mode)
     assert torch.equal(r1["perm"], r2["perm"]) and torch.equal(r1["T"], r2["T"])
     assert r1["est"] == r2["est"]
