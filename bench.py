@@ -29,6 +29,21 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 # FP64 FMA peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA/clock
 # x 2 flops x 2.07 GHz maximum SM clock (a DFMA probe measured 1.20 TF/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+# DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
+# valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
+TC_TRAFFIC = {"bytes_per_launch": 77.6e9,   # 16 x (4.799 + 0.053) GB, profiles/sketch_tc_kernel_65536x2048.md
+              "source_sha1": "2b7ec8cf42eb4c58ebd1ccba1133b588f05e41bd"}
+
+
+def tc_source_unchanged():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "paper_1205_3830_gb300", "csrc", "rid_sketch_tc.cu"), "rb") as f:
+            return TC_TRAFFIC["source_sha1"] == hashlib.sha1(f.read()).hexdigest()
+    except OSError:
+        return False
+
+
 NVSMI_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -211,6 +226,7 @@ def run_ours(args, cfg, world, rank, local):
     A = synth.device.device_matrix(cfg, device=dev)
     stream = torch.cuda.current_stream(dev)
     plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, mode=args.mode, stream=stream)
+    plan.enable_timing()
     Y = rid.colmajor_empty(l, n, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     T = rid.colmajor_empty(k, n - k, device=dev)
@@ -237,8 +253,10 @@ def run_ours(args, cfg, world, rank, local):
     torch.cuda.synchronize()
     sampler.start()
     start.record(stream)
+    kernel_ms = []
     for s in range(args.steps):
-        est, upper = step(events[s])
+        est, upper = step(events[s])          # rid_error has synchronized the stream
+        kernel_ms.append(plan.sketch_times())
     stop.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -253,23 +271,37 @@ def run_ours(args, cfg, world, rank, local):
                              st["error_launches"])
     value = world * cfg.a_bytes / 1e9 / (ms_step / 1e3)
 
-    # roofline of the dominant kernel (the sketch) and of the whole ID
+    # roofline of the dominant kernel (the sketch's product) and of the whole ID
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
-    sketch_flops = 8.0 * l * m * n
+    bf16_sust = float(peaks.get("bf16_tflops_sustained", 1724.5))
+    sketch_flops = 8.0 * l * m * n                       # complex l x m x n product
+    k_ms = [statistics.mean(t[i] for t in kernel_ms) for i in range(3)]
+    t_prod = k_ms[1] / 1e3
+    fp64_equiv = {"achieved": sketch_flops / t_prod / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
+    fp64_equiv["frac"] = fp64_equiv["achieved"] / FP64_PEAK_TFLOPS
     if args.mode == "fp64":
-        achieved = sketch_flops / (per["sketch"] / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "kernel": "sketch_fp64_kernel", "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz"}
+        roof = {"bound": "alu", "achieved": fp64_equiv["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": fp64_equiv["frac"], "traffic": None, "kernel": "sketch_fp64_kernel",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (a DFMA probe measured 1.20)",
+                "per_launch": "8 l m n flops (complex product)"}
+        tc_flops = None
     else:
-        achieved = sketch_flops / (per["sketch"] / 1e3) / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "sketch_emulated"}
-    # whole-ID roofline: sum over steps of max(bytes / HBM, flops / FP64 peak)
+        # the emulation's own work: 28 BF16 slice-pair products of the real
+        # (2l x 2m) x (2m x n) problem, 2 flops per multiply-add
+        tc_flops = 28 * 2.0 * (2 * l) * (2 * m) * n
+        achieved = tc_flops / t_prod / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
+                "frac": achieved / bf16_sust, "traffic": TC_TRAFFIC.get("bytes_per_launch") if tc_source_unchanged() else None,
+                "kernel": "sketch_tc_kernel",
+                "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
+                "per_launch": "28 slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
+    # whole-ID roofline: sum over steps of max(bytes / HBM, flops / the peak of the pipe used)
     p64 = FP64_PEAK_TFLOPS * 1e12
     a_b = 16.0 * m * n
-    t_roof = (max(a_b / (hbm * 1e9), sketch_flops / p64) +
+    sketch_roof = (max(a_b / (hbm * 1e9), sketch_flops / p64) if tc_flops is None
+                   else max(a_b / (hbm * 1e9), tc_flops / (bf16_sust * 1e12)))
+    t_roof = (sketch_roof +
               max(2 * 16.0 * l * n * k / (hbm * 1e9), 16.0 * n * (l * k - k * k / 2) / p64) +
               4.0 * k * k * (n - k) / p64 +
               max(a_b / (hbm * 1e9), 8.0 * m * n * args.nprobe / p64))
@@ -283,6 +315,7 @@ def run_ours(args, cfg, world, rank, local):
         "roofline": roof,
         "id_roofline_frac": id_frac,
         "step_ms": per,
+        "sketch_kernel_ms": {"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2]},
         "gpu_launches": launches,
         "error_estimate": {"est": est, "upper": upper},
         "clocks": clocks,
@@ -347,7 +380,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--config", default="large_tall")
-    ap.add_argument("--mode", default="fp64", choices=("fp64", "fp64_emulated"))
+    ap.add_argument("--mode", default="fp64_emulated", choices=("fp64", "fp64_emulated"))
     ap.add_argument("--nprobe", type=int, default=8)
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)

@@ -147,6 +147,15 @@ RID_API rid_status rid_sync_status(rid_plan_t plan);
  *   out[6] = mode (rid_mode)                       out[7] = dtype (rid_dtype) */
 RID_API rid_status rid_plan_stats(rid_plan_t plan, int64_t out[8]);
 
+/* Per-kernel device time of this plan's rid_sketch, for performance accounting.
+ *   enable != 0 creates CUDA events (once) and from then on every rid_sketch
+ *   records them on the plan's stream around its kernels.  If out (HOST,
+ *   double[3]) is not NULL, waits for the last rid_sketch and returns its
+ *   times in ms: out[0] = digit slicing of A (0 in the native mode),
+ *   out[1] = the product kernel, out[2] = the split-K reduction.
+ *   RID_EINVAL if out is given before timing was enabled. */
+RID_API rid_status rid_plan_timing(rid_plan_t plan, int32_t enable, double out[3]);
+
 /* Allocation-free pivoted QR (the paper has no counterpart: this is a service
  * for callers that cannot call cudaMalloc, e.g. code running under another
  * allocator's lock, or real-time loops that forbid allocation after start-up).

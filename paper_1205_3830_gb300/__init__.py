@@ -171,6 +171,16 @@ class Plan:
                 "device_bytes", "mode", "dtype")
         return dict(zip(keys, [int(x) for x in out]))
 
+    def enable_timing(self):
+        """Record CUDA events around the sketch's kernels from now on."""
+        check(self._lib.rid_plan_timing(self._h, 1, None), "rid_plan_timing")
+
+    def sketch_times(self):
+        """(slicing, product, reduction) ms of the last sketch (waits for it)."""
+        out = (ctypes.c_double * 3)()
+        check(self._lib.rid_plan_timing(self._h, 0, out), "rid_plan_timing")
+        return tuple(float(x) for x in out)
+
     def sync_status(self):
         """Synchronize the plan's stream and raise RIDError on a device-side error."""
         check(self._lib.rid_sync_status(self._h), "rid_sync_status")

@@ -30,6 +30,7 @@ SIGNATURES = {
                                  ctypes.POINTER(ctypes.c_double)]),
     "rid_sync_status": (ctypes.c_int, [_c_plan]),
     "rid_plan_stats": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64)]),
+    "rid_plan_timing": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(ctypes.c_double)]),
     "rid_select_noalloc": (ctypes.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p]),
     "rid_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }

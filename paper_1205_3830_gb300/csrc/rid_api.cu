@@ -181,6 +181,8 @@ rid_status rid_plan_destroy(rid_plan_t p) {
   if (!p) return RID_OK;
   DeviceGuard g(p->device);
   cudaStreamSynchronize(p->stream);
+  if (p->timing)
+    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
   rid_tc_plan_free(p);
   cudaFree((void*)p->omega);   // the omega piece is the start of the single allocation
   free(p);
@@ -274,6 +276,26 @@ rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   out[5] = (int64_t)(p->ws_bytes + p->tc_bytes);
   out[6] = p->mode;
   out[7] = p->dtype;
+  return RID_OK;
+}
+
+rid_status rid_plan_timing(rid_plan_t p, int32_t enable, double out[3]) {
+  if (!p) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  if (out) {
+    if (!p->timing) return RID_EINVAL;
+    float ms[3] = {0.f, 0.f, 0.f};
+    cudaError_t e = cudaEventSynchronize(p->ev[3]);
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
+    if (e != cudaSuccess) return from_cuda(e);
+    for (int i = 0; i < 3; ++i) out[i] = ms[i];
+  }
+  if (enable && !p->timing) {
+    for (int i = 0; i < 4; ++i)
+      if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return RID_ECUDA;
+    p->timing = 1;
+  }
   return RID_OK;
 }
 

@@ -48,6 +48,10 @@ struct rid_plan_s {
 
   size_t ws_bytes;         // bytes of the plan's single workspace allocation
 
+  // optional per-kernel timing of rid_sketch (CUDA events on the plan's stream)
+  int timing;
+  cudaEvent_t ev[4];
+
   // emulated / mixed sketch state (owned by the tensor-core path)
   void* tc_state;
   size_t tc_bytes;

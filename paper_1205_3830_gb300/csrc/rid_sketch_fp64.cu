@@ -92,9 +92,17 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
                                    int64_t ldy) {
   const dim3 grid((unsigned)((p->l + BL - 1) / BL), (unsigned)((p->n + BN - 1) / BN),
                   (unsigned)p->split_k);
+  if (p->timing) {
+    cudaEventRecord(p->ev[0], p->stream);
+    cudaEventRecord(p->ev[1], p->stream);
+  }
   if (p->split_k == 1) {
     sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, Y, ldy, 0, p->l,
                                                     p->m, p->n, p->k_per_split);
+    if (p->timing) {
+      cudaEventRecord(p->ev[2], p->stream);
+      cudaEventRecord(p->ev[3], p->stream);
+    }
     return cudaGetLastError();
   }
   const int64_t stride = (int64_t)p->l * p->n;
@@ -104,7 +112,9 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
   if (e != cudaSuccess) return e;
   int64_t blocks = (stride + 255) / 256;
   if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
+  if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->sk_partial, stride,
                                                                 p->split_k, Y, ldy, p->l, p->n);
+  if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return cudaGetLastError();
 }

@@ -44,9 +44,9 @@ namespace {
 constexpr int TC_S = 7;                 // digits per value: 56 bits
 constexpr int TC_G = 4;                 // accumulator groups
 constexpr int TC_KC = 256;              // chunk of the reduction with exact FP32 sums
-constexpr int TC_KS = 16;               // K per pipeline stage (one MMA per slice pair)
-constexpr int TC_STAGES = 4;
-constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // 4 KB: 128 rows x 32 bytes
+constexpr int TC_KS = 32;               // K per pipeline stage: 64-byte tile rows, 2 MMAs per slice pair
+constexpr int TC_STAGES = TC_KS == 16 ? 4 : 2;
+constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // 128 rows x (2 TC_KS) bytes
 constexpr int TC_STAGE_BYTES = 2 * TC_S * TC_TILE_BYTES;
 constexpr int TC_THREADS = 512;         // warps 0-11 flush, 12 TMA, 13 MMA + TMEM, 14-15 idle
 constexpr int TC_FLUSH_WARPS = 12;
@@ -59,10 +59,13 @@ struct TcState {
   int64_t KP;             // padded reduction length (multiple of TC_KC)
   int NC;                 // chunks
   int l2;                 // 2l rows of Omega'
-  int ntiles;             // N-tiles of <= 128 rows
+  int ntiles;             // N-tiles of tile_w <= 128 rows (balanced: the cluster runs at the widest)
+  int tile_w;             // rows of Omega' per N-tile, a multiple of 16
   int nblocks;            // column blocks of 128
   int ksplit;             // K-splits
   int chunks_per_split;
+  int cx, cy;             // cluster shape (N-tiles x column blocks)
+  int nblocks_p;          // column blocks padded to a multiple of cy
   uint16_t* om_slices;    // [S][l2][KP] bf16
   int* om_exp;            // [l2]
   uint16_t* a_slices;     // [S][n][KP] bf16
@@ -213,7 +216,9 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* ba
 }
 
 struct TcArgs {
-  int n, l2, l2p, NC, chunks_per_split, ntiles;
+  int n, l2, l2p, NC, chunks_per_split, ntiles, tile_w;
+  uint32_t stage_bytes;   // bytes landing in one stage: S A tiles of 128 rows + S Omega tiles of tile_w rows
+  int cx, cy;             // cluster: cx N-tiles (share A tiles) x cy column blocks (share Omega tiles)
   const int* a_exp;
   const int* a_exp_max;
   float2* partial;
@@ -221,6 +226,9 @@ struct TcArgs {
 };
 
 __device__ __forceinline__ int group_of(int d) { return d >= 3 ? 3 : d; }
+
+// Descriptor of a 128-row tile of TC_KS bf16 per row (swizzle matching the tensor map).
+__device__ __forceinline__ uint64_t tile_desc(const void* p) { return TC_KS == 16 ? desc_sw32(p) : desc_sw64(p); }
 
 __global__ void __launch_bounds__(TC_THREADS, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_om, TcArgs a) {
@@ -232,21 +240,29 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // blockIdx.x walks the N-tiles of one column block first, so the CTAs that
-  // share an A tile run together and read it from L2
-  const int nb = blockIdx.x % a.ntiles, jb = blockIdx.x / a.ntiles, ks = blockIdx.y;
+  // Grid (N-tiles, column blocks, K-splits); a cluster of cx x cy CTAs covers
+  // all N-tiles of cy column blocks.  Each A tile is loaded once per cluster
+  // row and multicast to the cx CTAs that use it; each Omega tile once per
+  // cluster column and multicast to the cy CTAs that use it.
+  const int nb = blockIdx.x, jb = blockIdx.y, ks = blockIdx.z;
+  const int rx = nb % a.cx, ry = jb % a.cy;
+  const uint32_t my_rank = (uint32_t)(rx + ry * a.cx);
+  const uint16_t row_mask = (uint16_t)(((1u << a.cx) - 1u) << (ry * a.cx));
+  uint16_t col_mask = 0;
+  for (int y = 0; y < a.cy; ++y) col_mask |= (uint16_t)(1u << (rx + y * a.cx));
+  const uint16_t all_mask = (uint16_t)((1u << (a.cx * a.cy)) - 1u);
   const int c_begin = ks * a.chunks_per_split;
   const int c_end = min(a.NC, c_begin + a.chunks_per_split);
   const int nchunks = max(0, c_end - c_begin);
-  const int row0 = nb * 128;
-  const int n_tile = min(128, a.l2 - row0);
+  const int row0 = nb * a.tile_w;
+  const int n_tile = min(a.tile_w, a.l2 - row0);
   const int n_mma = (n_tile + 15) & ~15;
 
   if (warp == 13) tmem_alloc(&tmem_slot, 512);
   if (threadIdx.x == 0) {
     for (int i = 0; i < TC_STAGES; ++i) {
       mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], 1);
+      mbar_init(&empty_bar[i], a.cx * a.cy);   // every CTA of the cluster releases the slot
     }
     for (int g = 0; g < TC_G; ++g) {
       mbar_init(&acc_full[g], 1);
@@ -254,10 +270,11 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     }
     mbar_init(&mma_done, 1);
     fence_barrier_init();
-    s_abort = 0;
+    s_abort = cluster_rank() != my_rank ? 1 : 0;      // grid and cluster layout disagree
+    if (s_abort) atomicCAS(a.err, 0, 1);
   }
   tc_fence_before();
-  __syncthreads();
+  cluster_sync();          // barriers of every CTA initialised before any multicast
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -286,15 +303,21 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
         }
         const int c = c_begin + it / (TC_KC / TC_KS);
         const int x = c * TC_KC + (it % (TC_KC / TC_KS)) * TC_KS;
-        mbar_arrive_expect_tx(&full_bar[slot], TC_STAGE_BYTES);
-#pragma unroll
-        for (int s = 0; s < TC_S; ++s) tma_load_3d(&map_a, &full_bar[slot], a_tile(slot, s), x, jb * 128, s);
-#pragma unroll
-        for (int s = 0; s < TC_S; ++s) tma_load_3d(&map_om, &full_bar[slot], o_tile(slot, s), x, row0, s);
+        // the stage's 2S tiles arrive here whoever issued them
+        mbar_arrive_expect_tx(&full_bar[slot], a.stage_bytes);
+        for (int s = rx; s < TC_S; s += a.cx)
+          tma_load_3d_multicast(&map_a, &full_bar[slot], a_tile(slot, s), x, jb * 128, s, row_mask);
+        for (int s = ry; s < TC_S; s += a.cy)
+          tma_load_3d_multicast(&map_om, &full_bar[slot], o_tile(slot, s), x, row0, s, col_mask);
       }
-      // wind-down: every issued load must land before the CTA may exit
-      for (int k = max(0, it - TC_STAGES); k < it; ++k)
-        if (!mbar_wait(&full_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET)) fail(12);
+      // tail: before the CTA may exit, every slot must have been released by
+      // every CTA of the cluster (their commits arrive here), or, after an
+      // error, every load issued into this CTA must have landed
+      for (int k = max(0, it - TC_STAGES); k < it; ++k) {
+        const bool ok = s_abort ? mbar_wait(&full_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET)
+                                : mbar_wait(&empty_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET);
+        if (!ok) fail(12);
+      }
     } else if (warp == 13 && lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = idesc_bf16_f32(128, n_mma);
@@ -323,14 +346,17 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             for (int s = 0; s <= d; ++s) {
               const int t = d - s;
               if (s >= TC_S || t >= TC_S) continue;
-              const uint32_t acc = (b == 0 && group_start && s == 0) ? 0u : 1u;
-              mma_bf16(tmem + (uint32_t)(g * 128), desc_sw32(a_tile(slot, t)), desc_sw32(o_tile(slot, s)), idesc,
-                       acc);
+              const uint64_t da = tile_desc(a_tile(slot, t)), db = tile_desc(o_tile(slot, s));
+#pragma unroll
+              for (int kk = 0; kk < TC_KS / 16; ++kk) {   // K16 steps are 32 bytes apart in a row
+                const uint32_t acc = (b == 0 && group_start && s == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+              }
             }
             const bool group_end = (d <= 3);     // last diagonal of its group in this stage
             if (b == stages_per_chunk - 1 && group_end) mma_commit(&acc_full[g]);
           }
-          mma_commit(&empty_bar[slot]);
+          mma_commit_multicast(&empty_bar[slot], all_mask);
         }
       }
       mma_commit(&mma_done);
@@ -402,7 +428,8 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 
   // ---------------- teardown ----------------
   tc_fence_before();
-  __syncthreads();
+  cluster_sync();          // no CTA of the cluster sends anything after this
+
   if (warp == 13) {
     if (!mbar_wait(&mma_done, 0, TC_WAIT_BUDGET)) fail(91);
     __syncwarp();
@@ -444,20 +471,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return enc;
 }
 
-// 3D bf16 tensor [slices][rows][KP] with a box of 16 x 128 x 1 and the 32-byte swizzle.
-int make_slice_map(CUtensorMap* map, const void* base, int64_t KP, int64_t rows, int slices) {
+// 3D bf16 tensor [slices][rows][KP] with a box of TC_KS x box_rows x 1 and the matching swizzle.
+int make_slice_map(CUtensorMap* map, const void* base, int64_t KP, int64_t rows, int slices, int box_rows) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return -1;
   cuuint64_t gdim[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)slices};
   cuuint64_t gstride[2] = {(cuuint64_t)KP * 2, (cuuint64_t)(KP * 2 * rows)};
-  cuuint32_t box[3] = {TC_KS, 128, 1};
+  cuuint32_t box[3] = {TC_KS, (cuuint32_t)box_rows, 1};
   cuuint32_t es[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, gdim, gstride, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_32B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, TC_KS == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
+// K-splits so that the clusters fill whole waves; `slots` = clusters resident at once.
 int choose_ksplit(int units, int NC, int sms) {
   int best = 1;
   double best_eff = 0.0;
@@ -489,9 +517,40 @@ rid_status rid_tc_plan_init(rid_plan_s* p) {
   st->KP = (int64_t)st->NC * TC_KC;
   st->l2 = 2 * p->l;
   st->ntiles = (st->l2 + 127) / 128;
-  st->l2p = st->ntiles * 128;
+  st->tile_w = ((st->l2 + st->ntiles - 1) / st->ntiles + 15) / 16 * 16;
+  st->l2p = st->ntiles * st->tile_w;
   st->nblocks = (int)((p->n + 127) / 128);
-  st->ksplit = choose_ksplit(st->ntiles * st->nblocks, st->NC, p->num_sms);
+  if (st->ntiles > 8) {
+    free(st);
+    return RID_EUNSUPPORTED;
+  }
+  // Clusters span the N-tiles of one column block (they share its A tiles).
+  // Sharing Omega tiles across column blocks too (cy > 1) measured slower:
+  // larger clusters pack GPCs less densely and run in lockstep.
+  st->cx = st->ntiles;
+  st->cy = 1;
+  st->nblocks_p = (st->nblocks + st->cy - 1) / st->cy * st->cy;
+  {
+    // how many clusters of this shape are resident at once
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3(st->cx, st->nblocks_p, 1);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TC_STAGES * TC_STAGE_BYTES + 1024;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = st->cx;
+    attr[0].val.clusterDim.y = st->cy;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int clusters = 0;
+    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_STAGES * TC_STAGE_BYTES + 1024);
+    if (cudaOccupancyMaxActiveClusters(&clusters, sketch_tc_kernel, &cfg) != cudaSuccess || clusters < 1) {
+      cudaGetLastError();
+      clusters = p->num_sms / (st->cx * st->cy);
+    }
+    st->ksplit = choose_ksplit(st->nblocks_p / st->cy, st->NC, clusters > 0 ? clusters : 1);
+  }
   st->chunks_per_split = (st->NC + st->ksplit - 1) / st->ksplit;
   st->ksplit = (st->NC + st->chunks_per_split - 1) / st->chunks_per_split;
 
@@ -521,8 +580,8 @@ rid_status rid_tc_plan_init(rid_plan_s* p) {
   p->tc_bytes = total;
   p->tc_sketch_launches = 3;
 
-  if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S) ||
-      make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S)) {
+  if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S, 128) ||
+      make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S, st->tile_w)) {
     rid_tc_plan_free(p);
     return RID_ECUDA;
   }
@@ -573,6 +632,7 @@ cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, doub
   const TcState* st = (const TcState*)p->tc_state;
   if (!st) return cudaErrorNotSupported;
   const double2* A = (const double2*)A_;
+  if (p->timing) cudaEventRecord(p->ev[0], p->stream);
   // 0x80808080 is below every exponent: the running maximum starts there
   cudaError_t e = cudaMemsetAsync(st->a_exp_max, 0x80, (size_t)p->n * 4, p->stream);
   if (e != cudaSuccess) return e;
@@ -584,11 +644,27 @@ cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, doub
                                                              st->a_exp, st->a_exp_max);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles,
+  if (p->timing) cudaEventRecord(p->ev[1], p->stream);
+  TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
+              (uint32_t)(TC_S * TC_TILE_BYTES + TC_S * st->tile_w * TC_KS * 2), st->cx, st->cy,
               st->a_exp, st->a_exp_max, st->partial, st->err};
-  const dim3 grid((unsigned)(st->ntiles * st->nblocks), (unsigned)st->ksplit);
-  sketch_tc_kernel<<<grid, TC_THREADS, TC_STAGES * TC_STAGE_BYTES + 1024, p->stream>>>(st->map_a, st->map_om, args);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    cfg.gridDim = dim3((unsigned)st->ntiles, (unsigned)st->nblocks_p, (unsigned)st->ksplit);
+    cfg.blockDim = dim3(TC_THREADS);
+    cfg.dynamicSmemBytes = TC_STAGES * TC_STAGE_BYTES + 1024;
+    cfg.stream = p->stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = st->cx;
+    attr[0].val.clusterDim.y = st->cy;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, sketch_tc_kernel, st->map_a, st->map_om, args);
+    if (e != cudaSuccess) return e;
+  }
+  if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   {
     const int64_t total = p->n * (int64_t)p->l;
     int64_t blocks = (total + 255) / 256;
@@ -597,6 +673,7 @@ cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, doub
                                                                st->om_exp, st->a_exp_max, Y, ldy);
     e = cudaGetLastError();
   }
+  if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return e;
 }
 

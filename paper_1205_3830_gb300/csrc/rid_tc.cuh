@@ -109,6 +109,19 @@ __device__ __forceinline__ uint64_t desc_sw32(const void* smem_ptr) {
   return d;
 }
 
+// 64-byte rows (32 bf16 of K per row) with the 64-byte swizzle: 8-row atoms of
+// 512 bytes; the second K16 step starts 32 bytes into the row.
+__device__ __forceinline__ uint64_t desc_sw64(const void* smem_ptr) {
+  const uint64_t addr = smem_u32(smem_ptr);
+  uint64_t d = 0;
+  d |= (addr & 0x3FFFFull) >> 4;
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;         // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;                  // 64-byte swizzle
+  return d;
+}
+
 // Instruction descriptor: BF16 x BF16 -> FP32, both operands K-major, M x N.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                          // D format: F32
@@ -132,6 +145,36 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+// Same, arriving on the barrier at this offset in every CTA of `cta_mask`.
+__device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(cta_mask)
+      : "memory");
+}
+
+// ---- clusters ----------------------------------------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// All threads of all CTAs of the cluster (release / acquire).
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// 3D tile load delivered to the same shared-memory offset (and the same
+// barrier offset) in every CTA of `cta_mask`.
+__device__ __forceinline__ void tma_load_3d_multicast(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
+                                                      int z, uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
+      "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(cta_mask)
+      : "memory");
 }
 
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp gets lane
