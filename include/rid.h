@@ -95,6 +95,16 @@ RID_API rid_status rid_plan_omega(rid_plan_t plan, const void** omega, int64_t* 
  * device matrix with row stride ldo >= m (copied on the stream). */
 RID_API rid_status rid_plan_set_omega(rid_plan_t plan, const void* omega, int64_t ldo);
 
+/* Replace the plan's Omega by the paper's own randomization (Sec. 2, "Y = S F D A"):
+ * row q of S F D, Omega(q, j) = exp(-2 pi i s_q j / m) exp(2 pi i phi_j), with
+ * D = diag(exp(2 pi i phi_j)) random phases (phi_j uniform on [0, 1)), F the
+ * m x m DFT (0-based, F_jk = exp(-2 pi i j k / m)) and S sampling rows
+ * s_q uniform on {0..m-1}.  phi_j = u2 of the Philox4x32-10 block at counter
+ * (j mod 2^32, j div 2^32, 0, 5), s_q = floor(m u2) of the block at counter
+ * (q, 0, 1, 5), key = srft_seed.  Generated on the plan's stream.  The
+ * subsampled DFT is applied as this dense l x m matrix by rid_sketch. */
+RID_API rid_status rid_plan_use_srft(rid_plan_t plan, uint64_t srft_seed);
+
 /* Randomization, Sec. 2:  Y = Omega A.
  *   A: m x n, column-major, leading dimension lda >= m, dtype of the plan.
  *   Y: l x n complex128 output, column-major, ldy >= l.  Fully overwritten.

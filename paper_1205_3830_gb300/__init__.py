@@ -122,6 +122,10 @@ class Plan:
               "rid_plan_set_omega")
         self._keep = omega
 
+    def use_srft(self, srft_seed):
+        """Use the paper's randomization Omega = S F D (subsampled DFT with random phases)."""
+        check(self._lib.rid_plan_use_srft(self._h, int(srft_seed) & (2 ** 64 - 1)), "rid_plan_use_srft")
+
     # -- the four steps --------------------------------------------------------
     def sketch(self, A, Y=None):
         """Y = Omega A (l x n complex128, column-major)."""
@@ -197,7 +201,7 @@ def decompose(A, k, l, seed=0, mode="fp64", nprobe=8, probe_seed=1, plan=None):
         Y = plan.sketch(A)
         perm = plan.select(Y)
         T = plan.solve(Y)
-        est, upper = plan.error(A, perm, T, nprobe, probe_seed) if A.dtype == torch.complex128 else (None, None)
+        est, upper = plan.error(A, perm, T, nprobe, probe_seed)
         plan.sync_status()
         return {"J": perm[:k], "perm": perm, "T": T, "Y": Y, "est": est, "upper": upper}
     finally:

@@ -23,6 +23,7 @@ SIGNATURES = {
     "rid_plan_destroy": (ctypes.c_int, [_c_plan]),
     "rid_plan_omega": (ctypes.c_int, [_c_plan, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
     "rid_plan_set_omega": (ctypes.c_int, [_c_plan, _p, _i64]),
+    "rid_plan_use_srft": (ctypes.c_int, [_c_plan, _u64]),
     "rid_sketch": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),
     "rid_select": (ctypes.c_int, [_c_plan, _p, _i64, _p]),
     "rid_solve": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),

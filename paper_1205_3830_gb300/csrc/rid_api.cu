@@ -6,11 +6,36 @@
 
 #include "rid_internal.cuh"
 
-// Tensor-core paths (defined in rid_sketch_tc.cu).
-rid_status rid_tc_plan_init(rid_plan_s* p);
-void rid_tc_plan_free(rid_plan_s* p);
-cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
-int rid_tc_error_word(const rid_plan_s* p);
+// Tensor-core paths: FP64-emulated (rid_sketch_tc.cu) and mixed precision
+// (rid_sketch_mixed.cu).
+rid_status rid_tc_plan_init_fp64(rid_plan_s* p);
+void rid_tc_plan_free_fp64(rid_plan_s* p);
+cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+int rid_tc_error_word_fp64(const rid_plan_s* p);
+rid_status rid_mx_plan_init(rid_plan_s* p);
+void rid_mx_plan_free(rid_plan_s* p);
+cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+int rid_mx_error_word(const rid_plan_s* p);
+
+static rid_status rid_tc_plan_init(rid_plan_s* p) {
+  if (p->mode == RID_FP64_EMULATED) return rid_tc_plan_init_fp64(p);
+  if (p->mode == RID_MIXED_BF16) return rid_mx_plan_init(p);
+  return RID_EUNSUPPORTED;
+}
+static void rid_tc_plan_free(rid_plan_s* p) {
+  if (p->mode == RID_FP64_EMULATED) rid_tc_plan_free_fp64(p);
+  else if (p->mode == RID_MIXED_BF16) rid_mx_plan_free(p);
+}
+static cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy) {
+  if (p->mode == RID_FP64_EMULATED) return rid_tc_sketch_fp64(p, A, lda, Y, ldy);
+  if (p->mode == RID_MIXED_BF16) return rid_mx_sketch(p, A, lda, Y, ldy);
+  return cudaErrorNotSupported;
+}
+static int rid_tc_error_word(const rid_plan_s* p) {
+  if (p->mode == RID_FP64_EMULATED) return rid_tc_error_word_fp64(p);
+  if (p->mode == RID_MIXED_BF16) return rid_mx_error_word(p);
+  return 0;
+}
 
 namespace {
 
@@ -211,9 +236,22 @@ rid_status rid_plan_set_omega(rid_plan_t p, const void* omega, int64_t ldo) {
   return from_cuda(e);
 }
 
+rid_status rid_plan_use_srft(rid_plan_t p, uint64_t srft_seed) {
+  if (!p) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = rid_launch_srft(p->omega, p->l, p->m, p->ldo, srft_seed, p->stream);
+  if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
+    rid_tc_plan_free(p);          // the tensor-core paths keep Omega in split form
+    const rid_status s = rid_tc_plan_init(p);
+    if (s != RID_OK) return s;
+  }
+  return from_cuda(e);
+}
+
 rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t ldy) {
   if (!p || !A || !Y || lda < p->m || ldy < p->l) return RID_EINVAL;
-  if (!aligned16(Y) || !aligned16(A)) return RID_EINVAL;
+  if (!aligned16(Y) || ((uintptr_t)A & (p->dtype == RID_C128 ? 15u : 7u))) return RID_EINVAL;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
   cudaError_t e;
@@ -246,12 +284,10 @@ rid_status rid_error(rid_plan_t p, const void* A, int64_t lda, const int32_t* pe
   if (!p || !A || !perm || !out || lda < p->m || ldt < p->k) return RID_EINVAL;
   if (p->n > p->k && !T) return RID_EINVAL;
   if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
-  if (p->dtype != RID_C128) return RID_EUNSUPPORTED;
-  if (!aligned16(A) || (T && !aligned16(T))) return RID_EINVAL;
+  if (((uintptr_t)A & (p->dtype == RID_C128 ? 15u : 7u)) || (T && !aligned16(T))) return RID_EINVAL;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
-  cudaError_t e = rid_launch_error(p, (const double2*)A, lda, perm, (const double2*)T, ldt, nprobe,
-                                   probe_seed);
+  cudaError_t e = rid_launch_error(p, A, lda, perm, (const double2*)T, ldt, nprobe, probe_seed);
   if (e != cudaSuccess) return from_cuda(e);
   double host[2];
   int status = 0;

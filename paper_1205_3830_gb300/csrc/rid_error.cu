@@ -84,9 +84,17 @@ __global__ void wj_finalize_kernel(const double2* __restrict__ part, int groups,
   wtilde[(int64_t)perm[i] * RM + q] = make_double2(-s.x, -s.y);
 }
 
-// E w~ for a block of rows and a range of columns: part[s][q][row].
+__device__ __forceinline__ double2 load_a(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 load_a(const float2* p) {
+  const float2 v = __ldg(p);
+  return make_double2((double)v.x, (double)v.y);
+}
+
+// E w~ for a block of rows and a range of columns: part[s][q][row].  A is
+// complex128 or complex64; the arithmetic is FP64 either way.
+template <typename TA>
 __global__ void __launch_bounds__(EW_THREADS)
-ew_kernel(const double2* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+ew_kernel(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
           const double2* __restrict__ wtilde, int r, int64_t chunk, double2* __restrict__ part) {
   __shared__ double2 s_w[EW_COLS][RM];
   const int64_t i = (int64_t)blockIdx.x * EW_THREADS + threadIdx.x;
@@ -106,9 +114,9 @@ ew_kernel(const double2* __restrict__ A, int64_t lda, int64_t m, int64_t n,
     __syncthreads();
     if (i < m) {
       const int cn = (int)((c_end - c0) < EW_COLS ? (c_end - c0) : EW_COLS);
-      const double2* a_ptr = A + i + c0 * lda;
+      const TA* a_ptr = A + i + c0 * lda;
       for (int cc = 0; cc < cn; ++cc) {
-        const double2 a = __ldg(a_ptr + cc * lda);
+        const double2 a = load_a(a_ptr + cc * lda);
 #pragma unroll
         for (int q = 0; q < RM; ++q)
           if (q < r) acc[q] = cfma(a, s_w[cc][q], acc[q]);
@@ -190,7 +198,7 @@ error_finalize_kernel(const double* __restrict__ norm_part, int blocks,
 
 }  // namespace
 
-cudaError_t rid_launch_error(const rid_plan_s* p, const double2* A, int64_t lda,
+cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
                              const int32_t* perm, const double2* T, int64_t ldt, int nprobe,
                              uint64_t probe_seed) {
   const int r = nprobe;
@@ -222,8 +230,12 @@ cudaError_t rid_launch_error(const rid_plan_s* p, const double2* A, int64_t lda,
   const int row_blocks = p->err_row_blocks;
   const int splits = p->err_col_split;
   const int64_t chunk = (n + splits - 1) / splits;
-  ew_kernel<<<dim3(row_blocks, splits), EW_THREADS, 0, p->stream>>>(A, lda, m, n, p->wtilde, r,
-                                                                    chunk, p->ew_part);
+  if (p->dtype == RID_C64)
+    ew_kernel<float2><<<dim3(row_blocks, splits), EW_THREADS, 0, p->stream>>>((const float2*)A, lda, m, n,
+                                                                             p->wtilde, r, chunk, p->ew_part);
+  else
+    ew_kernel<double2><<<dim3(row_blocks, splits), EW_THREADS, 0, p->stream>>>((const double2*)A, lda, m, n,
+                                                                              p->wtilde, r, chunk, p->ew_part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ew_norm_kernel<<<row_blocks, EW_THREADS, 0, p->stream>>>(p->ew_part, splits, m, r, p->norm_part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;

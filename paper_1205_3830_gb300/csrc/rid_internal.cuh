@@ -71,6 +71,9 @@ cudaError_t rid_launch_gaussian(double2* out, int64_t rows, int64_t cols, int64_
                                 int64_t col_stride, uint64_t seed, uint32_t stream_id,
                                 cudaStream_t stream);
 
+// Omega = rows s_1..s_l of F D (the paper's subsampled randomized Fourier transform).
+cudaError_t rid_launch_srft(double2* out, int64_t l, int64_t m, int64_t ldo, uint64_t seed, cudaStream_t stream);
+
 cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_t lda, double2* Y,
                                    int64_t ldy);
 
@@ -80,7 +83,7 @@ cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy,
                              int64_t ldt);
 size_t rid_solve_smem_bytes(int k, int* nr_out);
 
-cudaError_t rid_launch_error(const rid_plan_s* p, const double2* A, int64_t lda,
+cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
                              const int32_t* perm, const double2* T, int64_t ldt, int nprobe,
                              uint64_t probe_seed);
 

@@ -386,10 +386,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
       const float scale = delta >= -126 ? __int_as_float((127 + delta) << 23) : 0.f;
       for (int gi = 0; gi < TC_G; ++gi) {
         const int g = TC_G - 1 - gi;
-        const bool ok = mbar_wait(&acc_full[g], cl & 1, TC_WAIT_BUDGET);
-        __syncwarp();
-        if (!ok) {
-          fail(31);
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[g], cl & 1, TC_WAIT_BUDGET));
+        if (!ok) {                       // the whole warp leaves together
+          if (lane == 0) fail(31);
           break;
         }
         tc_fence_after();
@@ -506,9 +505,9 @@ int choose_ksplit(int units, int NC, int sms) {
 
 }  // namespace
 
-void rid_tc_plan_free(rid_plan_s* p);
+void rid_tc_plan_free_fp64(rid_plan_s* p);
 
-rid_status rid_tc_plan_init(rid_plan_s* p) {
+rid_status rid_tc_plan_init_fp64(rid_plan_s* p) {
   if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
   TcState* st = (TcState*)calloc(1, sizeof(TcState));
   if (!st) return RID_ENOMEM;
@@ -582,7 +581,7 @@ rid_status rid_tc_plan_init(rid_plan_s* p) {
 
   if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S, 128) ||
       make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S, st->tile_w)) {
-    rid_tc_plan_free(p);
+    rid_tc_plan_free_fp64(p);
     return RID_ECUDA;
   }
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
@@ -607,18 +606,18 @@ rid_status rid_tc_plan_init(rid_plan_s* p) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, sketch_tc_kernel);
     if (e == cudaSuccess && fa.numRegs != TC_LAUNCH_REGS) {
-      rid_tc_plan_free(p);
+      rid_tc_plan_free_fp64(p);
       return RID_EUNSUPPORTED;
     }
   }
   if (e != cudaSuccess) {
-    rid_tc_plan_free(p);
+    rid_tc_plan_free_fp64(p);
     return RID_ECUDA;
   }
   return RID_OK;
 }
 
-void rid_tc_plan_free(rid_plan_s* p) {
+void rid_tc_plan_free_fp64(rid_plan_s* p) {
   TcState* st = (TcState*)p->tc_state;
   if (!st) return;
   cudaStreamSynchronize(p->stream);
@@ -628,7 +627,7 @@ void rid_tc_plan_free(rid_plan_s* p) {
   p->tc_bytes = 0;
 }
 
-cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
+cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
   const TcState* st = (const TcState*)p->tc_state;
   if (!st) return cudaErrorNotSupported;
   const double2* A = (const double2*)A_;
@@ -677,7 +676,7 @@ cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A_, int64_t lda, doub
   return e;
 }
 
-int rid_tc_error_word(const rid_plan_s* p) {
+int rid_tc_error_word_fp64(const rid_plan_s* p) {
   const TcState* st = (const TcState*)p->tc_state;
   if (!st) return 0;
   int h = 0;

@@ -1,0 +1,79 @@
+"""Mixed-precision sketch (complex64 A, BF16x3 splits, FP32 accumulation on the
+tensor cores) against the FP64 oracle run on the same A (upcast exactly).
+
+Stated accuracy: the sketch is FP32-grade, |Y - Y_FP64| <= 2^-16 ||Omega_i|| ||A_j||
+per entry (three BF16 terms carry about 24 bits of every value; the FP32 sums
+over the K range add the rest); the ID keeps the FP64 oracle's J whenever the
+spectral gap exceeds that noise, and T within 1e-3 of the oracle.  The QR,
+solve and error estimate after the sketch are FP64.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import U64, to_dev_colmajor, to_host
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(2048, 1024, 32, 42), (1000, 777, 17, 27), (4096, 333, 5, 15), (300, 200, 100, 110)]
+
+
+@pytest.fixture(scope="module")
+def rid():
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    return rid
+
+
+def c64_lowrank(m, n, k, eps=1e-5, seed=0):
+    return np.asfortranarray(synth.lowrank_plus_noise(m, n, k, eps, seed=seed + m + n).astype(np.complex64))
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=str)
+def test_mixed_sketch_accuracy(rid, shape):
+    m, n, k, l = shape
+    A = c64_lowrank(m, n, k)
+    Oo = oracle.gaussian_test_matrix(l, m, 3)
+    with rid.Plan(m, n, k, l, seed=3, dtype=torch.complex64, mode="bf16") as plan:
+        plan.set_omega(torch.from_numpy(Oo).cuda())
+        Y = to_host(plan.sketch(to_dev_colmajor(A, torch.complex64)))
+        plan.sync_status()
+    Yo = oracle.randomize(Oo, A.astype(np.complex128))
+    scale = np.outer(np.linalg.norm(Oo, axis=1), np.linalg.norm(A.astype(np.complex128), axis=0))
+    rel = np.abs(Y - Yo) / scale
+    print(f"mixed sketch {shape}: max |dY| / (||Omega_i|| ||A_j||) = {rel.max():.2e}")
+    assert rel.max() <= 2.0 ** -16
+
+
+@pytest.mark.parametrize("shape", SHAPES[:3], ids=str)
+def test_mixed_whole_id_against_fp64_oracle(rid, shape):
+    m, n, k, l = shape
+    A = c64_lowrank(m, n, k)
+    out = oracle.rid(A.astype(np.complex128), k, l, seed=11)
+    res = rid.decompose(to_dev_colmajor(A, torch.complex64), k, l, seed=11, mode="bf16", nprobe=8, probe_seed=2)
+    perm, T = to_host(res["perm"]), to_host(res["T"])
+    assert np.array_equal(perm[:k], out["J"])
+    dT = np.abs(T - out["T"]).max() / np.abs(out["T"]).max()
+    print(f"mixed ID {shape}: max |dT| / max |T| = {dT:.2e}")
+    assert dT <= 1e-3
+
+
+def test_mixed_error_estimate_is_fp64(rid):
+    """The error pass on complex64 A computes in FP64: same as the oracle on the
+    upcast A within the FP64 rounding bound."""
+    m, n, k, l = 1500, 600, 12, 20
+    A = c64_lowrank(m, n, k, eps=1e-4)
+    A128 = A.astype(np.complex128)
+    out = oracle.rid(A128, k, l, seed=4)
+    omega = oracle.probe_matrix(n, 8, 9)
+    est_o, up_o, _ = oracle.error_estimate(A128, out["perm"], out["T"], omega)
+    with rid.Plan(m, n, k, l, seed=4, dtype=torch.complex64, mode="bf16") as plan:
+        est, up = plan.error(to_dev_colmajor(A, torch.complex64), torch.from_numpy(out["perm"].astype(np.int32)).cuda(),
+                             to_dev_colmajor(out["T"]), 8, 9)
+    w_abs = np.abs(omega)
+    w_abs[out["perm"][:k]] = np.abs(out["T"]) @ np.abs(omega[out["perm"][k:]])
+    bound = 4 * (n + k) * U64 * np.linalg.norm(np.abs(A128) @ w_abs, axis=0)
+    assert abs(est - est_o) <= np.max(bound / np.linalg.norm(omega, axis=0)) + 1e-13 * est_o

@@ -236,3 +236,53 @@ def test_results_are_deterministic(rid, mode):
     r2 = rid.decompose(A, k, l, seed=2, mode=mode)
     assert torch.equal(r1["perm"], r2["perm"]) and torch.equal(r1["T"], r2["T"])
     assert r1["est"] == r2["est"]
+
+
+# --- the paper's randomization: Omega = S F D (Sec. 2) ---------------------------
+def srft_matrix(l, m, seed):
+    """Rows s_q of F D built from the oracle's SRFT parameters (definition)."""
+    phi, s = oracle.srft_parameters(l, m, seed)
+    jk = np.outer(s, np.arange(m)) % m
+    return np.exp(-2j * np.pi * (jk / m)) * np.exp(2j * np.pi * phi)[None, :]
+
+
+@pytest.mark.parametrize("shape", [(2048, 1024, 32, 40), (1000, 777, 17, 25), (4096, 333, 1, 3)], ids=str)
+def test_srft_omega_matches_oracle(rid, shape):
+    m, n, k, l = shape
+    with rid.Plan(m, n, k, l, seed=1) as plan:
+        plan.use_srft(99)
+        Om = to_host(plan.omega())
+    Oo = srft_matrix(l, m, 99)
+    assert np.abs(np.abs(Om) - 1).max() < 1e-14
+    assert np.abs(Om - Oo).max() <= 1e-13
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("shape", [(2048, 1024, 32, 40), (1000, 777, 17, 25)], ids=str)
+def test_srft_sketch_matches_oracle(rid, shape, mode):
+    m, n, k, l = shape
+    A = lowrank(m, n, k)
+    with rid.Plan(m, n, k, l, seed=1, mode=mode) as plan:
+        plan.use_srft(7)
+        Y = to_host(plan.sketch(to_dev_colmajor(A)))
+        plan.sync_status()
+    Yo = oracle.srft_randomize(A, l, 7)
+    Oo = srft_matrix(l, m, 7)
+    tol = dot_bound(Oo, A) + 1e-13 * (np.abs(Oo) @ np.abs(A))
+    if mode != "fp64":
+        tol = tol + emulation_bound(Oo, A)
+    assert np.all(np.abs(Y - Yo) <= tol)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_srft_whole_id_matches_oracle(rid, mode):
+    m, n, k, l = 2048, 1024, 32, 64
+    A = lowrank(m, n, k)
+    Oo = srft_matrix(l, m, 5)
+    out = oracle.rid(A, k, l, seed=0, Omega=Oo)
+    with rid.Plan(m, n, k, l, seed=0, mode=mode) as plan:
+        plan.use_srft(5)
+        res = rid.decompose(to_dev_colmajor(A), k, l, plan=plan)
+    perm, T = to_host(res["perm"]), to_host(res["T"])
+    assert np.array_equal(perm[:k], out["J"])
+    assert np.abs(T - out["T"]).max() <= 1e-10 * np.abs(out["T"]).max()
