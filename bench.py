@@ -188,7 +188,7 @@ def run_reference(args, cfg, world, rank):
     for _ in range(args.steps):
         oracle_slab_step(cfg, Omega, A_slab, probes)
     dt = (time.perf_counter() - t0) / args.steps
-    bytes_per_step = 16 * cfg.m * ns
+    bytes_per_step = cfg.a_bytes * ns / cfg.n
     value = bytes_per_step / dt / 1e9
     sample = f"oracle ID of the column slab A[:, :{ns}] (m={cfg.m}, k={cfg.k}, l={cfg.l}); Omega drawn untimed"
     line = {
@@ -203,8 +203,10 @@ def run_reference(args, cfg, world, rank):
 
 
 def workload_config(cfg, args):
-    return {"workload": f"{cfg.name}: complex128 A = U V^H + tail (sigma_j = 1 for j <= {cfg.rank}, "
-                        f"tail ~{cfg.eps:g}), m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
+    kind = (f"A = U V^H + tail (sigma_j = 1 for j <= {cfg.rank}, tail ~{cfg.eps:g})" if cfg.kind == "spectrum"
+            else f"A = X Y + {cfg.eps:g} N (rank {cfg.rank})")
+    ctype = "complex64" if cfg.dtype == "c64" else "complex128"
+    return {"workload": f"{cfg.name}: {ctype} {kind}, m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
                         f"{cfg.a_bytes / 2**30:.0f} GiB",
             "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode,
             "l2": "inputs larger than L2 (A is %.0f GiB, L2 129 MB)" % (cfg.a_bytes / 2**30)}
@@ -225,7 +227,8 @@ def run_ours(args, cfg, world, rank, local):
     m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
     A = synth.device.device_matrix(cfg, device=dev)
     stream = torch.cuda.current_stream(dev)
-    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, mode=args.mode, stream=stream)
+    a_dtype = torch.complex64 if cfg.dtype == "c64" else torch.complex128
+    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, dtype=a_dtype, mode=args.mode, stream=stream)
     plan.enable_timing()
     Y = rid.colmajor_empty(l, n, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
@@ -287,18 +290,21 @@ def run_ours(args, cfg, world, rank, local):
                 "per_launch": "8 l m n flops (complex product)"}
         tc_flops = None
     else:
-        # the emulation's own work: 28 BF16 slice-pair products of the real
-        # (2l x 2m) x (2m x n) problem, 2 flops per multiply-add
-        tc_flops = 28 * 2.0 * (2 * l) * (2 * m) * n
+        # the emulation's own work: BF16 slice-pair products of the real
+        # (2l x 2m) x (2m x n) problem, 2 flops per multiply-add (28 pairs for the
+        # FP64-grade digits, 6 for the BF16x3 splits of the mixed mode)
+        pairs = 28 if args.mode == "fp64_emulated" else 6
+        tc_flops = pairs * 2.0 * (2 * l) * (2 * m) * n
         achieved = tc_flops / t_prod / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
-                "frac": achieved / bf16_sust, "traffic": TC_TRAFFIC.get("bytes_per_launch") if tc_source_unchanged() else None,
-                "kernel": "sketch_tc_kernel",
+                "frac": achieved / bf16_sust,
+                "traffic": TC_TRAFFIC.get("bytes_per_launch") if args.mode == "fp64_emulated" and tc_source_unchanged() else None,
+                "kernel": "sketch_tc_kernel" if args.mode == "fp64_emulated" else "sketch_mixed_kernel",
                 "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
-                "per_launch": "28 slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
+                "per_launch": f"{pairs} slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
     # whole-ID roofline: sum over steps of max(bytes / HBM, flops / the peak of the pipe used)
     p64 = FP64_PEAK_TFLOPS * 1e12
-    a_b = 16.0 * m * n
+    a_b = float(cfg.a_bytes)
     sketch_roof = (max(a_b / (hbm * 1e9), sketch_flops / p64) if tc_flops is None
                    else max(a_b / (hbm * 1e9), tc_flops / (bf16_sust * 1e12)))
     t_roof = (sketch_roof +
@@ -310,7 +316,8 @@ def run_ours(args, cfg, world, rank, local):
     line = {
         "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, generated on the device)",
+        "vs_baseline": None, "dtype": "bf16" if args.mode == "bf16" else "f64",
+        "data": "synthetic (seeded, generated on the device)",
         "config": workload_config(cfg, args),
         "roofline": roof,
         "id_roofline_frac": id_frac,
@@ -323,6 +330,8 @@ def run_ours(args, cfg, world, rank, local):
 
     if args.e2e_steps > 0:
         line["e2e"] = run_e2e(args, cfg, plan, A, Y, perm, T, stream, world)
+    if args.mode == "bf16":
+        line["vs_fp64_path"] = compare_with_fp64(args, cfg, A, perm, T, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, cfg, A)
     plan.close()
@@ -360,6 +369,47 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
             "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": args.e2e_steps}
 
 
+def compare_with_fp64(args, cfg, A, perm, T, stream, rank):
+    """The plain FP64 GPU path (FP64-emulated sketch, FP64 QR / solve / error) on
+    the same inputs upcast to complex128: its throughput and how far the mixed
+    path's ID lies from it."""
+    import torch
+    import paper_1205_3830_gb300 as rid
+    m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
+    A128 = A.t().to(torch.complex128).t()
+    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, mode="fp64_emulated", stream=stream)
+    Y = rid.colmajor_empty(l, n, device=A.device)
+    perm2 = torch.empty(n, dtype=torch.int32, device=A.device)
+    T2 = rid.colmajor_empty(k, n - k, device=A.device)
+
+    def step():
+        plan.sketch(A128, Y)
+        plan.select(Y, perm2)
+        plan.solve(Y, T2)
+        return plan.error(A128, perm2, T2, args.nprobe, 1)
+
+    step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = 2
+    for _ in range(reps):
+        est, upper = step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    same_J = bool(torch.equal(torch.sort(perm[:k]).values, torch.sort(perm2[:k]).values))
+    same_perm = bool(torch.equal(perm[:k], perm2[:k]))
+    dT = None
+    if same_perm and n > k:
+        dT = float((T - T2).abs().max() / T2.abs().max())
+    plan.close()
+    del A128
+    return {"fp64_path_value": cfg.a_bytes / 1e9 / (ms / 1e3), "fp64_path_ms_per_step": ms, "unit": "GB/s",
+            "same_J": same_J, "same_pivot_order": same_perm, "max_dT_rel": dT, "fp64_path_error_estimate": est,
+            "stated_accuracy": "mixed sketch (BF16x3, FP32 sums) vs FP64-emulated sketch, same Omega and A"}
+
+
 def cpu_baseline(args, cfg, A):
     import numpy as np
     ns = args.ref_cols
@@ -368,7 +418,7 @@ def cpu_baseline(args, cfg, A):
     t0 = time.perf_counter()
     oracle_slab_step(cfg, Omega, A_slab, probes)
     dt = time.perf_counter() - t0
-    return {"value": 16 * cfg.m * ns / dt / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
+    return {"value": cfg.a_bytes * ns / cfg.n / dt / 1e9, "unit": "GB/s", "cores": cpu_cores(), "kind": "oracle",
             "sample": f"oracle ID of the column slab A[:, :{ns}] (m={cfg.m}, k={cfg.k}, l={cfg.l}), "
                       f"{dt:.1f} s; Omega drawn untimed"}
 
@@ -380,7 +430,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--config", default="large_tall")
-    ap.add_argument("--mode", default="fp64_emulated", choices=("fp64", "fp64_emulated"))
+    ap.add_argument("--mode", default="fp64_emulated", choices=("fp64", "fp64_emulated", "bf16"))
     ap.add_argument("--nprobe", type=int, default=8)
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)

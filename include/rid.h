@@ -33,6 +33,7 @@
 #ifndef RID_H
 #define RID_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -182,6 +183,40 @@ RID_API rid_status rid_plan_timing(rid_plan_t plan, int32_t enable, double out[3
  *   first call before any stream capture. */
 RID_API rid_status rid_select_noalloc(void* Y, int64_t ldy, int32_t l, int64_t n, int32_t k,
                                       int32_t* perm, int32_t* status, void* stream);
+
+/* ---- Batched IDs -------------------------------------------------------------------
+ * Many independent complex128 IDs of uneven sizes (e.g. the blocks of a
+ * hierarchical-matrix compressor) in one persistent launch.  Each problem is
+ * the whole four-step ID of Sec. 2 / Sec. 3.3 with the plan's conventions:
+ * Omega from `seed` exactly as rid_plan_create draws it, Householder QR with
+ * column pivoting, back substitution, probe error estimate; FP64 arithmetic. */
+typedef struct {
+  int64_t m, n;          /* A is m x n */
+  int32_t k, l;          /* 1 <= k <= min(m, n), k <= l <= 128, k <= 64, n <= 4096 */
+  const void* A;         /* device, complex128, column-major, lda >= m */
+  int64_t lda;
+  void* Y;               /* device, l x n complex128 (ldy >= l): the sketch, then R (like rid_select) */
+  int64_t ldy;
+  int32_t* perm;         /* device, int32[n]: J = perm[0..k-1] */
+  void* T;               /* device, k x (n-k) complex128 (ldt >= k); NULL allowed when n == k */
+  int64_t ldt;
+  uint64_t seed;         /* Omega of this problem */
+} rid_batch_item;
+
+/* Device workspace bytes rid_batch_run needs for `count` problems. */
+RID_API rid_status rid_batch_workspace(int32_t count, size_t* bytes);
+
+/* Run `count` IDs (items: HOST array) on `stream`.  err_out (device,
+ * double[2 count]) receives each problem's (est, upper) as rid_error returns
+ * them; status_out (device, int32[count]) RID_OK or RID_ERANK per problem
+ * (est = upper = -1 then).  tile = 16 or 32: the sketch's column tile (pick
+ * with an autotuner; results do not depend on it).  workspace: device,
+ * >= rid_batch_workspace bytes.  Returns RID_EINVAL / RID_EUNSUPPORTED for
+ * sizes beyond the limits above before anything is launched; synchronizes the
+ * stream once to stage the descriptors, then runs asynchronously. */
+RID_API rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t nprobe, uint64_t probe_seed,
+                                 int32_t tile, double* err_out, int32_t* status_out, void* workspace,
+                                 size_t ws_bytes, void* stream);
 
 /* Static, human-readable name of a status code. */
 RID_API const char* rid_status_string(rid_status status);

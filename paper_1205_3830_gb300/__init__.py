@@ -23,7 +23,7 @@ import torch
 from . import _native
 from ._native import RIDError, check
 
-__all__ = ["Plan", "RIDError", "colmajor_empty", "as_colmajor", "decompose", "MODES"]
+__all__ = ["Plan", "RIDError", "colmajor_empty", "as_colmajor", "decompose", "MODES", "Batch", "batch_decompose"]
 
 MODES = {
     "fp64": _native.RID_FP64_NATIVE,
@@ -188,6 +188,91 @@ class Plan:
     def sync_status(self):
         """Synchronize the plan's stream and raise RIDError on a device-side error."""
         check(self._lib.rid_sync_status(self._h), "rid_sync_status")
+
+
+class Batch:
+    """Many independent complex128 IDs run together by rid_batch_run.
+
+    problems: list of (A, k, l, seed) with A a column-major complex128 device
+    tensor.  Outputs (Y holding R, perm, T) are allocated here; run() launches
+    all problems in one persistent kernel on the current stream.
+    """
+
+    _tile_cache = {}
+
+    def __init__(self, problems, nprobe=8, probe_seed=1, device=None):
+        self._lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.nprobe, self.probe_seed = int(nprobe), int(probe_seed)
+        self.Y, self.perm, self.T, self.A = [], [], [], []
+        items = (_native.BatchItem * len(problems))()
+        for i, (A, k, l, seed) in enumerate(problems):
+            assert A.is_cuda and A.dtype == torch.complex128 and A.stride(0) == 1
+            m, n = A.shape
+            Y = colmajor_empty(l, n, device=self.device)
+            perm = torch.empty(n, dtype=torch.int32, device=self.device)
+            T = colmajor_empty(k, n - k, device=self.device)
+            self.A.append(A), self.Y.append(Y), self.perm.append(perm), self.T.append(T)
+            it = items[i]
+            it.m, it.n, it.k, it.l = m, n, int(k), int(l)
+            it.A, it.lda = A.data_ptr(), _ld(A)
+            it.Y, it.ldy = Y.data_ptr(), _ld(Y)
+            it.perm = perm.data_ptr()
+            it.T, it.ldt = (T.data_ptr() if T.numel() else 0), max(_ld(T), int(k))
+            it.seed = int(seed) & (2 ** 64 - 1)
+        self.items = items
+        self.count = len(problems)
+        need = ctypes.c_size_t()
+        check(self._lib.rid_batch_workspace(self.count, ctypes.byref(need)), "rid_batch_workspace")
+        self.ws = torch.empty(max(1, need.value), dtype=torch.uint8, device=self.device)
+        self.err = torch.empty(2 * max(1, self.count), dtype=torch.float64, device=self.device)
+        self.status = torch.empty(max(1, self.count), dtype=torch.int32, device=self.device)
+        self.signature = (self.count, sum(int(p[0].shape[0]) * int(p[0].shape[1]) for p in problems) // max(1, self.count))
+
+    def run(self, tile=None, stream=None):
+        tile = tile or self._tile_cache.get(self.signature, 32)
+        stream = stream or torch.cuda.current_stream(self.device)
+        check(self._lib.rid_batch_run(ctypes.byref(self.items), self.count, self.nprobe,
+                                      self.probe_seed & (2 ** 64 - 1), int(tile), ctypes.c_void_p(self.err.data_ptr()),
+                                      ctypes.c_void_p(self.status.data_ptr()), ctypes.c_void_p(self.ws.data_ptr()),
+                                      self.ws.numel(), ctypes.c_void_p(stream.cuda_stream)), "rid_batch_run")
+        return self
+
+    def autotune(self, tiles=(16, 32), reps=2):
+        """Time each sketch tile on this batch and remember the fastest for
+        batches of the same signature (results do not depend on the tile)."""
+        best, best_ms = None, float("inf")
+        for t in tiles:
+            self.run(tile=t)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                self.run(tile=t)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            if ms < best_ms:
+                best, best_ms = t, ms
+        self._tile_cache[self.signature] = best
+        return best, best_ms
+
+    def results(self):
+        """List of dicts (J, perm, T, est, upper, status) after run()."""
+        torch.cuda.synchronize()
+        err = self.err.cpu().numpy()
+        status = self.status.cpu().numpy()
+        out = []
+        for i in range(self.count):
+            k = int(self.items[i].k)
+            out.append({"perm": self.perm[i], "J": self.perm[i][:k], "T": self.T[i], "Y": self.Y[i],
+                        "est": float(err[2 * i]), "upper": float(err[2 * i + 1]), "status": int(status[i])})
+        return out
+
+
+def batch_decompose(problems, nprobe=8, probe_seed=1, tile=None):
+    """Run a list of (A, k, l, seed) problems as one batch; returns Batch.results()."""
+    return Batch(problems, nprobe, probe_seed).run(tile).results()
 
 
 def decompose(A, k, l, seed=0, mode="fp64", nprobe=8, probe_seed=1, plan=None):

@@ -32,9 +32,19 @@ SIGNATURES = {
     "rid_sync_status": (ctypes.c_int, [_c_plan]),
     "rid_plan_stats": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64)]),
     "rid_plan_timing": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(ctypes.c_double)]),
+    "rid_batch_workspace": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_size_t)]),
+    "rid_batch_run": (ctypes.c_int, [ctypes.c_void_p, _i32, _i32, _u64, _i32, _p, _p, _p, ctypes.c_size_t, _p]),
     "rid_select_noalloc": (ctypes.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p]),
     "rid_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
+
+
+
+class BatchItem(ctypes.Structure):
+    """Mirror of rid_batch_item (include/rid.h)."""
+    _fields_ = [("m", _i64), ("n", _i64), ("k", _i32), ("l", _i32), ("A", _p), ("lda", _i64), ("Y", _p),
+                ("ldy", _i64), ("perm", _p), ("T", _p), ("ldt", _i64), ("seed", _u64)]
+
 
 _lib = None
 

@@ -1,0 +1,517 @@
+// Batched randomized IDs: many independent problems of uneven sizes in one
+// persistent launch.  A CTA takes whole problems from a work queue (one atomic
+// counter; problems are queued largest first) and runs every step of the ID for
+// its problem with CTA-wide synchronisation only, so no CTA ever waits on
+// another:
+//   sketch   Y = Omega A        (Sec. 2; Omega drawn on the fly from the
+//                                problem's seed, the same Philox counters as a
+//                                plan with that seed)
+//   select   k Householder steps with column pivoting on Y (Sec. 2)
+//   solve    R1 T = R2 by back substitution (Sec. 2)
+//   error    probe estimate of ||A - A(:, J) P||_2 (Sec. 3.3)
+// All arithmetic is FP64; sums run in a fixed order, so a problem's result
+// does not depend on which CTA ran it or what ran beside it.
+#include <climits>
+
+#include "rid_internal.cuh"
+
+namespace {
+
+constexpr int BT_THREADS = 256;
+constexpr int BT_WARPS = BT_THREADS / 32;
+constexpr int BT_KC = 32;                  // rows of A per sketch chunk
+constexpr int BT_MAX_L = 128;
+constexpr int BT_MAX_K = 64;
+constexpr int BT_MAX_N = 4096;
+constexpr int BT_NR = 32;                  // right-hand sides per solve block
+
+struct BatchItemDev {
+  int64_t m, n;
+  int32_t k, l;
+  const double2* A;
+  int64_t lda;
+  double2* Y;
+  int64_t ldy;
+  int32_t* perm;
+  double2* T;
+  int64_t ldt;
+  uint64_t seed;
+};
+
+struct BatchArgs {
+  const BatchItemDev* items;
+  const int32_t* order;       // queue order (largest first)
+  int count;
+  unsigned* next;             // work-queue counter
+  int nprobe;
+  uint64_t probe_seed;
+  double* err_out;            // 2 per problem
+  int32_t* status_out;        // per problem
+  int ct;                     // sketch column tile: 16 or 32 (tuned)
+};
+
+__device__ __forceinline__ double warp_sum(double x) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+  return x;
+}
+
+// Block sum in a fixed order; valid in all threads.
+__device__ double block_sum(double x, double* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  x = warp_sum(x);
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  double s = 0.0;
+  for (int w = 0; w < BT_WARPS; ++w) s += red[w];
+  return s;
+}
+
+// ---- step 1: Y = Omega A, column tiles of ct, K chunks of BT_KC rows ------------------
+template <int CT>
+__device__ void batch_sketch(const BatchItemDev& it, double2* smem) {
+  const int l = it.l;
+  const int64_t m = it.m, n = it.n;
+  double2* As = smem;                                  // CT x (BT_KC + 1)
+  double2* Os = smem + CT * (BT_KC + 1);               // l x (BT_KC + 1)
+  constexpr int MAXE = (BT_MAX_L * CT + BT_THREADS - 1) / BT_THREADS;
+  for (int64_t c0 = 0; c0 < n; c0 += CT) {
+    double2 acc[MAXE];
+#pragma unroll
+    for (int u = 0; u < MAXE; ++u) acc[u] = make_double2(0.0, 0.0);
+    for (int64_t r0 = 0; r0 < m; r0 += BT_KC) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < CT * BT_KC; e += BT_THREADS) {
+        const int c = e / BT_KC, rr = e % BT_KC;
+        const int64_t gc = c0 + c, gr = r0 + rr;
+        As[c * (BT_KC + 1) + rr] = (gc < n && gr < m) ? it.A[gc * it.lda + gr] : make_double2(0.0, 0.0);
+      }
+      for (int e = threadIdx.x; e < l * BT_KC; e += BT_THREADS) {
+        const int i = e / BT_KC, rr = e % BT_KC;
+        const int64_t gr = r0 + rr;
+        Os[i * (BT_KC + 1) + rr] =
+            gr < m ? philox_complex_normal((uint64_t)i, (uint64_t)gr, it.seed, RID_STREAM_OMEGA) : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < MAXE; ++u) {
+        const int e = threadIdx.x + u * BT_THREADS;
+        if (e < l * CT) {
+          const int i = e / CT, c = e % CT;
+          const double2* o = Os + i * (BT_KC + 1);
+          const double2* a = As + c * (BT_KC + 1);
+          double2 s = acc[u];
+#pragma unroll 8
+          for (int rr = 0; rr < BT_KC; ++rr) s = cfma(o[rr], a[rr], s);
+          acc[u] = s;
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < MAXE; ++u) {
+      const int e = threadIdx.x + u * BT_THREADS;
+      if (e < l * CT) {
+        const int i = e / CT, c = e % CT;
+        if (c0 + c < n) it.Y[i + (c0 + c) * it.ldy] = acc[u];
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---- step 2: pivoted Householder QR on Y (k steps) ---------------------------------
+// Returns RID_OK or RID_ERANK.
+__device__ int batch_select(const BatchItemDev& it, double2* tau, double* nu, double* red, double2* v) {
+  const int l = it.l, k = it.k;
+  const int64_t n = it.n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __shared__ double s_best_v;
+  __shared__ int s_best_i;
+  __shared__ double2 s_scale;
+  for (int64_t c = threadIdx.x; c < n; c += BT_THREADS) it.perm[c] = (int32_t)c;
+  // nu_c = |Y(j:, c)|^2 for the current step j, recomputed after every update
+  for (int64_t c = warp; c < n; c += BT_WARPS) {
+    double s = 0.0;
+    for (int i = lane; i < l; i += 32) s += cabs2(it.Y[i + c * it.ldy]);
+    s = warp_sum(s);
+    if (lane == 0) nu[c] = s;
+  }
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    // pivot: first maximum of nu over columns j..n-1
+    if (warp == 0) {
+      double bv = -1.0;
+      int bi = INT_MAX;
+      for (int64_t c = j + lane; c < n; c += 32) {
+        const double x = nu[c];
+        if (x > bv) {
+          bv = x;
+          bi = (int)c;
+        }
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, bv, off);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+        if (ov > bv || (ov == bv && oi < bi)) {
+          bv = ov;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_best_v = bv;
+        s_best_i = bi;
+      }
+    }
+    __syncthreads();
+    if (!(s_best_v > 0.0)) return RID_ERANK;
+    const int p = s_best_i;
+    double2* colj = it.Y + (int64_t)j * it.ldy;
+    if (p != j) {
+      double2* colp = it.Y + (int64_t)p * it.ldy;
+      for (int i = threadIdx.x; i < l; i += BT_THREADS) {
+        const double2 t = colj[i];
+        colj[i] = colp[i];
+        colp[i] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int32_t t = it.perm[j];
+        it.perm[j] = it.perm[p];
+        it.perm[p] = t;
+        nu[p] = nu[j];
+      }
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < l; i += BT_THREADS) part += cabs2(colj[i]);
+    const double xnorm2 = block_sum(part, red);
+    if (threadIdx.x == 0) {
+      const double2 alpha = colj[j];
+      double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
+      if (!(xnorm2 == 0.0 && alpha.y == 0.0)) {
+        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
+        const double beta = alpha.x >= 0.0 ? -nrm : nrm;
+        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+        scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+        colj[j] = make_double2(beta, 0.0);
+      }
+      tau[j] = t;
+      s_scale = scale;
+    }
+    __syncthreads();
+    const double2 scale = s_scale;
+    for (int i = j + 1 + threadIdx.x; i < l; i += BT_THREADS)
+      if (scale.x != 0.0 || scale.y != 0.0) colj[i] = cmul(colj[i], scale);
+    __syncthreads();
+    // v = (1, Y(j+1:, j)); apply H^H to columns j+1..n-1, then their new norms
+    for (int i = threadIdx.x; i < l - j; i += BT_THREADS) v[i] = i == 0 ? make_double2(1.0, 0.0) : colj[j + i];
+    __syncthreads();
+    const double2 ctau = make_double2(tau[j].x, -tau[j].y);
+    for (int64_t c = j + 1 + warp; c < n; c += BT_WARPS) {
+      double2* col = it.Y + c * it.ldy + j;
+      double2 w = make_double2(0.0, 0.0);
+      for (int i = lane; i < l - j; i += 32) w = cfma_conj(v[i], col[i], w);
+      w.x = warp_sum(w.x);
+      w.y = warp_sum(w.y);
+      const double2 s = cmul(ctau, w);
+      double nn = 0.0;
+      for (int i = lane; i < l - j; i += 32) {
+        const double2 vs = cmul(v[i], s);
+        double2 x = col[i];
+        x.x -= vs.x;
+        x.y -= vs.y;
+        col[i] = x;
+        if (i > 0) nn += cabs2(x);
+      }
+      nn = warp_sum(nn);
+      if (lane == 0) nu[c] = nn;
+    }
+    __syncthreads();
+  }
+  return RID_OK;
+}
+
+// ---- step 3: T = R1^-1 R2 -------------------------------------------------------------
+__device__ void batch_solve(const BatchItemDev& it, double2* rhs, double2* rcol) {
+  const int k = it.k;
+  const int64_t ncols = it.n - k;
+  for (int64_t c0 = 0; c0 < ncols; c0 += BT_NR) {
+    const int nvalid = (int)min((int64_t)BT_NR, ncols - c0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * BT_NR; e += BT_THREADS) {
+      const int c = e / k, i = e % k;
+      rhs[i * BT_NR + c] = c < nvalid ? it.Y[i + (k + c0 + c) * it.ldy] : make_double2(0.0, 0.0);
+    }
+    for (int j = k - 1; j >= 0; --j) {
+      __syncthreads();
+      if (threadIdx.x < BT_NR) rhs[j * BT_NR + threadIdx.x] = cdiv(rhs[j * BT_NR + threadIdx.x], it.Y[j + (int64_t)j * it.ldy]);
+      for (int i = threadIdx.x; i < j; i += BT_THREADS) rcol[i] = it.Y[i + (int64_t)j * it.ldy];
+      __syncthreads();
+      for (int e = threadIdx.x; e < j * BT_NR; e += BT_THREADS) {
+        const int i = e / BT_NR, c = e % BT_NR;
+        const double2 r = rcol[i], t = rhs[j * BT_NR + c];
+        double2 x = rhs[e];
+        x.x = fma(-r.x, t.x, x.x);
+        x.x = fma(r.y, t.y, x.x);
+        x.y = fma(-r.x, t.y, x.y);
+        x.y = fma(-r.y, t.x, x.y);
+        rhs[e] = x;
+      }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < k * BT_NR; e += BT_THREADS) {
+      const int c = e / k, i = e % k;
+      if (c < nvalid) it.T[i + (c0 + c) * it.ldt] = rhs[i * BT_NR + c];
+    }
+  }
+  __syncthreads();
+}
+
+// ---- step 4: error estimate ------------------------------------------------------------
+__device__ void batch_error(const BatchItemDev& it, int r, uint64_t probe_seed, double2* wj, int* inv, double2* wc,
+                            double* red, double* out) {
+  const int k = it.k;
+  const int64_t m = it.m, n = it.n, ncols = n - k;
+  // inverse permutation: position of each column of A, and w~(J) = -T w(Jc)
+  for (int64_t c = threadIdx.x; c < n; c += BT_THREADS) inv[it.perm[c]] = (int)c;
+  for (int e = threadIdx.x; e < k * RID_MAX_PROBES; e += BT_THREADS) wj[e] = make_double2(0.0, 0.0);
+  __syncthreads();
+  {
+    // each thread owns up to 4 (i, q) pairs of the k x r product; the probes of
+    // 32 columns of Jc at a time are drawn once into shared memory
+    constexpr int OWN = (BT_MAX_K * RID_MAX_PROBES + BT_THREADS - 1) / BT_THREADS;
+    double2 s[OWN];
+#pragma unroll
+    for (int u = 0; u < OWN; ++u) s[u] = make_double2(0.0, 0.0);
+    for (int64_t t0 = 0; t0 < ncols; t0 += 32) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * r; e += BT_THREADS) {
+        const int tt = e / r, q = e % r;
+        const int64_t t = t0 + tt;
+        wc[tt * RID_MAX_PROBES + q] =
+            t < ncols ? philox_complex_normal((uint64_t)it.perm[k + t], (uint64_t)q, probe_seed, RID_STREAM_PROBES)
+                      : make_double2(0.0, 0.0);
+      }
+      __syncthreads();
+      const int tn = (int)min((int64_t)32, ncols - t0);
+#pragma unroll
+      for (int u = 0; u < OWN; ++u) {
+        const int e = threadIdx.x + u * BT_THREADS;
+        if (e < k * r) {
+          const int i = e / r, q = e % r;
+          for (int tt = 0; tt < tn; ++tt) s[u] = cfma(it.T[i + (t0 + tt) * it.ldt], wc[tt * RID_MAX_PROBES + q], s[u]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < OWN; ++u) {
+      const int e = threadIdx.x + u * BT_THREADS;
+      if (e < k * r) wj[(e / r) * RID_MAX_PROBES + (e % r)] = make_double2(-s[u].x, -s[u].y);
+    }
+  }
+  __syncthreads();
+  double e2[RID_MAX_PROBES];
+#pragma unroll
+  for (int q = 0; q < RID_MAX_PROBES; ++q) e2[q] = 0.0;
+  for (int64_t r0 = 0; r0 < m; r0 += BT_THREADS) {
+    const int64_t row = r0 + threadIdx.x;
+    double2 acc[RID_MAX_PROBES];
+#pragma unroll
+    for (int q = 0; q < RID_MAX_PROBES; ++q) acc[q] = make_double2(0.0, 0.0);
+    for (int64_t c0 = 0; c0 < n; c0 += 32) {
+      __syncthreads();
+      for (int e = threadIdx.x; e < 32 * r; e += BT_THREADS) {
+        const int cc = e / r, q = e % r;
+        const int64_t c = c0 + cc;
+        double2 w = make_double2(0.0, 0.0);
+        if (c < n) {
+          const int pos = inv[c];
+          w = pos < k ? wj[pos * RID_MAX_PROBES + q]
+                      : philox_complex_normal((uint64_t)c, (uint64_t)q, probe_seed, RID_STREAM_PROBES);
+        }
+        wc[cc * RID_MAX_PROBES + q] = w;
+      }
+      __syncthreads();
+      if (row < m) {
+        const int cn = (int)min((int64_t)32, n - c0);
+        for (int cc = 0; cc < cn; ++cc) {
+          const double2 a = it.A[row + (c0 + cc) * it.lda];
+#pragma unroll
+          for (int q = 0; q < RID_MAX_PROBES; ++q)
+            if (q < r) acc[q] = cfma(a, wc[cc * RID_MAX_PROBES + q], acc[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < RID_MAX_PROBES; ++q) e2[q] += cabs2(acc[q]);
+  }
+  double est = 0.0, emax = 0.0;
+  for (int q = 0; q < r; ++q) {
+    const double en2 = block_sum(e2[q], red);
+    double w2 = 0.0;
+    for (int64_t c = threadIdx.x; c < n; c += BT_THREADS)
+      w2 += cabs2(philox_complex_normal((uint64_t)c, (uint64_t)q, probe_seed, RID_STREAM_PROBES));
+    w2 = block_sum(w2, red);
+    const double en = sqrt(en2);
+    est = fmax(est, en / sqrt(w2));
+    emax = fmax(emax, en);
+  }
+  if (threadIdx.x == 0) {
+    out[0] = est;
+    out[1] = 10.0 * sqrt(0.63661977236758134308 /* 2 / pi */) * emax;
+  }
+  __syncthreads();
+}
+
+template <int CT>
+__global__ void __launch_bounds__(BT_THREADS) batch_kernel(BatchArgs a) {
+  extern __shared__ double2 smem[];
+  __shared__ double red[BT_WARPS];
+  __shared__ int s_task;
+  __shared__ double2 tau[BT_MAX_K];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(a.next, 1u);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= a.count) break;
+    const BatchItemDev it = a.items[a.order[t]];
+    const int pid = a.order[t];
+    batch_sketch<CT>(it, smem);
+    // scratch of the later steps shares the sketch's shared memory
+    double* nu = (double*)smem;                                   // n doubles
+    double2* v = (double2*)(nu + BT_MAX_N);                        // l entries
+    const int st = batch_select(it, tau, nu, red, v);
+    if (st != RID_OK) {
+      if (threadIdx.x == 0) {
+        a.status_out[pid] = st;
+        a.err_out[2 * pid] = -1.0;
+        a.err_out[2 * pid + 1] = -1.0;
+      }
+      continue;
+    }
+    batch_solve(it, smem, smem + BT_MAX_K * BT_NR);
+    double2* wj = smem;                                            // k x 16
+    int* inv = (int*)(smem + BT_MAX_K * RID_MAX_PROBES);           // n ints
+    double2* wc = (double2*)(inv + BT_MAX_N);                      // 32 x 16
+    batch_error(it, a.nprobe, a.probe_seed, wj, inv, wc, red, a.err_out + 2 * pid);
+    if (threadIdx.x == 0) a.status_out[pid] = RID_OK;
+  }
+}
+
+size_t batch_smem_bytes(int ct) {
+  const size_t sketch = (size_t)(ct + BT_MAX_L) * (BT_KC + 1) * sizeof(double2);
+  const size_t select = BT_MAX_N * sizeof(double) + BT_MAX_L * sizeof(double2);
+  const size_t solve = (size_t)(BT_MAX_K * BT_NR + BT_MAX_K) * sizeof(double2);
+  const size_t error = BT_MAX_K * RID_MAX_PROBES * sizeof(double2) + BT_MAX_N * sizeof(int) +
+                       32 * RID_MAX_PROBES * sizeof(double2);
+  size_t s = sketch;
+  if (select > s) s = select;
+  if (solve > s) s = solve;
+  if (error > s) s = error;
+  return s;
+}
+
+}  // namespace
+
+extern "C" {
+
+rid_status rid_batch_workspace(int32_t count, size_t* bytes) {
+  if (count < 0 || !bytes) return RID_EINVAL;
+  *bytes = (size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)) + 256;
+  return RID_OK;
+}
+
+rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t nprobe, uint64_t probe_seed,
+                         int32_t tile, double* err_out, int32_t* status_out, void* workspace, size_t ws_bytes,
+                         void* stream) {
+  if (count < 0 || (count > 0 && (!items || !err_out || !status_out || !workspace))) return RID_EINVAL;
+  if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  if (tile != 16 && tile != 32) return RID_EINVAL;
+  size_t need = 0;
+  rid_batch_workspace(count, &need);
+  if (ws_bytes < need) return RID_EINVAL;
+  if (count == 0) return RID_OK;
+  // host-side checks, the queue order (largest first) and the device descriptors
+  BatchItemDev* dev = (BatchItemDev*)malloc(sizeof(BatchItemDev) * (size_t)count);
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
+  double* cost = (double*)malloc(sizeof(double) * (size_t)count);
+  if (!dev || !order || !cost) {
+    free(dev);
+    free(order);
+    free(cost);
+    return RID_ENOMEM;
+  }
+  rid_status st = RID_OK;
+  for (int32_t i = 0; i < count && st == RID_OK; ++i) {
+    const rid_batch_item& x = items[i];
+    if (x.m < 1 || x.n < 1 || x.k < 1 || x.l < x.k || x.k > x.m || x.k > x.n || x.lda < x.m || x.ldy < x.l ||
+        x.ldt < x.k || !x.A || !x.Y || !x.perm || (x.n > x.k && !x.T))
+      st = RID_EINVAL;
+    else if (x.l > BT_MAX_L || x.k > BT_MAX_K || x.n > BT_MAX_N)
+      st = RID_EUNSUPPORTED;
+    dev[i] = BatchItemDev{x.m, x.n, x.k, x.l, (const double2*)x.A, x.lda, (double2*)x.Y, x.ldy, x.perm,
+                          (double2*)x.T, x.ldt, x.seed};
+    order[i] = i;
+    cost[i] = 8.0 * x.l * (double)x.m * (double)x.n + 8.0 * nprobe * (double)x.m * (double)x.n;
+  }
+  if (st != RID_OK) {
+    free(dev);
+    free(order);
+    free(cost);
+    return st;
+  }
+  // largest first: a simple insertion-free sort by cost
+  {
+    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
+    // bottom-up merge sort on order[] by descending cost
+    for (int32_t w = 1; w < count; w *= 2) {
+      for (int32_t lo = 0; lo < count; lo += 2 * w) {
+        int32_t mid = lo + w < count ? lo + w : count, hi = lo + 2 * w < count ? lo + 2 * w : count;
+        int32_t a = lo, b = mid, o = lo;
+        while (a < mid && b < hi) tmp[o++] = cost[order[a]] >= cost[order[b]] ? order[a++] : order[b++];
+        while (a < mid) tmp[o++] = order[a++];
+        while (b < hi) tmp[o++] = order[b++];
+      }
+      for (int32_t i = 0; i < count; ++i) order[i] = tmp[i];
+    }
+    free(tmp);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  char* ws = (char*)workspace;
+  BatchItemDev* d_items = (BatchItemDev*)ws;
+  int32_t* d_order = (int32_t*)(ws + (size_t)count * sizeof(BatchItemDev));
+  unsigned* d_next = (unsigned*)(ws + (size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)));
+  cudaError_t e = cudaMemcpyAsync(d_items, dev, sizeof(BatchItemDev) * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(unsigned), s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);      // the host arrays are pageable
+  free(dev);
+  free(order);
+  free(cost);
+  if (e != cudaSuccess) return RID_ECUDA;
+  int dev_id = 0, sms = 0;
+  cudaGetDevice(&dev_id);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+  const size_t smem = batch_smem_bytes(tile);
+  BatchArgs args{d_items, d_order, count, d_next, nprobe, probe_seed, err_out, status_out, tile};
+  // persistent grid: as many CTAs as can be resident at once
+  int per_sm = 1;
+  if (tile == 16) {
+    cudaFuncSetAttribute(batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16>, BT_THREADS, smem);
+  } else {
+    cudaFuncSetAttribute(batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32>, BT_THREADS, smem);
+  }
+  if (per_sm < 1) per_sm = 1;
+  const int grid = sms * per_sm < count ? sms * per_sm : count;
+  if (tile == 16)
+    batch_kernel<16><<<grid, BT_THREADS, smem, s>>>(args);
+  else
+    batch_kernel<32><<<grid, BT_THREADS, smem, s>>>(args);
+  return cudaGetLastError() == cudaSuccess ? RID_OK : RID_ECUDA;
+}
+
+}  // extern "C"

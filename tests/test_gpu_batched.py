@@ -1,0 +1,99 @@
+"""Batched IDs (one persistent launch for many uneven problems) against the
+CPU oracle and against the single-problem plan path.
+
+Same tolerances as the plan path: J exactly, T within 1e-10 max|T| of the
+oracle; against the plan path (same Omega, same FP64 algorithm, different
+summation blocking in the sketch) T within 1e-12, and the plan path's error
+pass on the batch's own (perm, T) gives its estimates within the FP64
+rounding bound of E w~ (the estimate is a cancellation).  Results do not depend on the sketch tile or on which other
+problems share the batch (bit for bit).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import U64, to_dev_colmajor, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rid():
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    return rid
+
+
+def make_problems(count, seed, m_range=(64, 420), n_range=(64, 420), k_range=(4, 24)):
+    shapes = synth.batched_shapes(count, seed, m_range=m_range, n_range=n_range, k_range=k_range)
+    probs = []
+    for i, (m, n, k, l) in enumerate(shapes):
+        A = synth.lowrank_plus_noise(m, n, k, 1e-10, seed=seed * 1000 + i)
+        probs.append((A, k, l, 7000 + i))
+    return probs
+
+
+def test_batch_matches_oracle_and_plan_path(rid):
+    probs = make_problems(24, seed=3)
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    res = rid.batch_decompose(dev, nprobe=8, probe_seed=5)
+    for (A, k, l, s), (Ad, _, _, _), r in zip(probs, dev, res):
+        assert r["status"] == 0
+        out = oracle.rid(A, k, l, seed=s)
+        perm, T = to_host(r["perm"]), to_host(r["T"])
+        assert np.array_equal(perm[:k], out["J"])
+        if T.size:
+            assert np.abs(T - out["T"]).max() <= 1e-10 * np.abs(out["T"]).max()
+        one = rid.decompose(Ad, k, l, seed=s, mode="fp64", nprobe=8, probe_seed=5)
+        assert torch.equal(one["perm"], r["perm"])
+        if T.size:
+            T1 = to_host(one["T"])
+            assert np.abs(T - T1).max() <= 1e-12 * np.abs(T1).max()
+        # the estimate cancels terms of size |A| |T| |w| down to ~1e-10: compare
+        # the batch's estimate with the plan path's error pass on the same (perm, T)
+        with rid.Plan(A.shape[0], A.shape[1], k, l, seed=s) as plan:
+            est, up = plan.error(Ad, r["perm"], r["T"] if T.size else torch.empty((k, 0), dtype=torch.complex128).cuda(),
+                                 8, 5)
+        # rounding bound of two FP64 evaluations of E w~ (the estimate cancels
+        # terms of size |A| |w~| down to ~1e-8 of that)
+        n = A.shape[1]
+        omega = oracle.probe_matrix(n, 8, 5)
+        w_abs = np.abs(omega)
+        if T.size:
+            w_abs[perm[:k]] = np.abs(T) @ np.abs(omega[perm[k:]])
+        bound_q = 2 * 4 * (n + k) * U64 * np.linalg.norm(np.abs(A) @ w_abs, axis=0)
+        assert abs(r["est"] - est) <= np.max(bound_q / np.linalg.norm(omega, axis=0)) + 1e-14 * est
+        assert abs(r["upper"] - up) <= 10 * np.sqrt(2 / np.pi) * np.max(bound_q) + 1e-14 * up
+
+
+def test_batch_is_independent_of_tile_and_company(rid):
+    probs = make_problems(12, seed=4)
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    b = rid.Batch(dev, nprobe=4, probe_seed=1)
+    r16 = [dict(x, T=x["T"].clone(), perm=x["perm"].clone()) for x in b.run(tile=16).results()]
+    r32 = b.run(tile=32).results()
+    for a, c in zip(r16, r32):
+        assert torch.equal(a["perm"], c["perm"]) and torch.equal(a["T"], c["T"]) and a["est"] == c["est"]
+    alone = rid.batch_decompose([dev[5]], nprobe=4, probe_seed=1)[0]
+    assert torch.equal(alone["perm"], r32[5]["perm"]) and torch.equal(alone["T"], r32[5]["T"])
+    assert alone["est"] == r32[5]["est"]
+
+
+def test_batch_reports_rank_deficiency_per_problem(rid):
+    probs = make_problems(5, seed=6)
+    A0 = np.zeros((100, 80), dtype=np.complex128)
+    A0[:, 3] = 1.0                       # rank 1
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs] + [(to_dev_colmajor(A0), 4, 8, 1)]
+    res = rid.batch_decompose(dev)
+    assert [r["status"] for r in res[:5]] == [0] * 5
+    assert res[5]["status"] == 4 and res[5]["est"] == -1.0
+
+
+def test_batch_autotune_picks_a_tile(rid):
+    probs = make_problems(16, seed=8)
+    b = rid.Batch([(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs])
+    tile, ms = b.autotune()
+    assert tile in (16, 32) and ms > 0
