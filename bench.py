@@ -423,6 +423,137 @@ def cpu_baseline(args, cfg, A):
                       f"{dt:.1f} s; Omega drawn untimed"}
 
 
+# ---------------------------------------------------------------------------
+# Batched and served forms
+# ---------------------------------------------------------------------------
+def device_lowrank(m, n, rank, eps, gen, device):
+    import torch
+    X = torch.randn((m, rank), generator=gen, dtype=torch.complex128, device=device)
+    Yf = torch.randn((rank, n), generator=gen, dtype=torch.complex128, device=device)
+    A = torch.randn((n, m), generator=gen, dtype=torch.complex128, device=device).t().mul_(eps)
+    return A.addmm_(X, Yf)
+
+
+def run_batched(args, world, rank, local):
+    """4096 independent complex128 IDs (m, n ~ U[64, 1024], k ~ U[4, 64],
+    l = k + 8, A = X Y + 1e-10 N) per step, in one persistent launch."""
+    import torch
+    import synth
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    shapes = synth.batched_shapes(args.count, synth.MASTER_SEED + 4 + rank)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.MASTER_SEED + 4 + rank)
+    problems = [(device_lowrank(m, n, k, 1e-10, gen, dev), k, l, 1000 + i) for i, (m, n, k, l) in enumerate(shapes)]
+    batch = rid.Batch(problems, nprobe=args.nprobe, probe_seed=1)
+    tile, _ = batch.autotune()
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        batch.run(tile)
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        batch.run(tile)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world) / args.steps
+    res = batch.results()
+    a_bytes = sum(16.0 * m * n for (m, n, k, l) in shapes)
+    flops = sum(8.0 * l * m * n + 8.0 * m * n * args.nprobe + 16.0 * n * (l * k - k * k / 2) + 4.0 * k * k * (n - k)
+                for (m, n, k, l) in shapes)
+    achieved = flops / (ms / 1e3) / 1e12
+    # the plain FP64 GPU path on the same inputs: one plan per problem, in turn
+    sub = min(64, len(problems))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for (A, k, l, sd) in problems[:sub]:
+        rid.decompose(A, k, l, seed=sd, mode="fp64", nprobe=args.nprobe, probe_seed=1)
+    torch.cuda.synchronize()
+    plan_ids_s = sub / (time.perf_counter() - t0)
+    line = {
+        "metric": METRIC, "value": world * a_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, generated on the device)",
+        "config": {"workload": f"batched: {len(shapes)} complex128 IDs, m, n ~ U[64, 1024], k ~ U[4, 64], l = k + 8, "
+                               f"A = X Y + 1e-10 N ({a_bytes / 2**30:.1f} GiB in all)",
+                   "count": len(shapes), "nprobe": args.nprobe, "tile": tile,
+                   "l2": "inputs larger than L2 (%.1f GiB)" % (a_bytes / 2**30)},
+        "ids_per_s": world * len(shapes) / (ms / 1e3),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "batch_kernel",
+                     "per_launch": "sum over problems of 8lmn + 8mnr + QR + solve flops"},
+        "gpu_launches": args.steps,
+        "ranks_ok": int(sum(1 for r in res if r["status"] == 0)),
+        "vs_fp64_plan_path": {"ids_per_s": plan_ids_s, "problems_timed": sub,
+                              "accuracy": "same J, T within 1e-12 (tests/test_gpu_batched.py)"},
+        "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_serving(args, world, rank, local):
+    """Poisson stream of complex128 ID requests (m, n log-uniform in [256, 16384],
+    k log-uniform in [8, 256], l = k + 10, A = X Y + 1e-10 N) at a sweep of
+    rates; continuous batching admitted by HBM footprint; p50 / p99 latency."""
+    import torch
+    import synth
+    from paper_1205_3830_gb300 import build
+    build.build()
+    from paper_1205_3830_gb300 import serve
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.MASTER_SEED + 5 + rank)
+    rates = [float(x) for x in args.rates.split(",")]
+    specs = synth.serving_requests(args.requests, 1.0, synth.MASTER_SEED + 5 + rank)   # shapes; times rescaled per rate
+    mats = [device_lowrank(m, n, k, 1e-10, gen, dev) for (_, m, n, k, l) in specs]
+    gaps = [specs[0][0]] + [specs[i][0] - specs[i - 1][0] for i in range(1, len(specs))]
+    a_bytes = sum(16.0 * m * n for (_, m, n, k, l) in specs)
+    # warm-up: every kernel once
+    serve.run_one(mats[0], specs[0][3], specs[0][4], 1, args.nprobe, 1, args.mode)
+    sweep = []
+    for rate in rates:
+        srv = serve.Server(slots=args.slots, mode=args.mode)
+        t0 = time.perf_counter()
+        due = 0.0
+        for i, (_, m, n, k, l) in enumerate(specs):
+            due += gaps[i] / rate
+            wait = t0 + due - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+            srv.submit(i, mats[i], k, l, 2000 + i, args.nprobe, 1)
+        done = srv.drain()
+        wall = time.perf_counter() - t0
+        srv.close()
+        errs = sum(1 for r in done if r.error is not None)
+        st = serve.latency_stats(done)
+        sweep.append({"offered_per_s": rate, "served_per_s": len(done) / wall, "gb_per_s": a_bytes / 1e9 / wall,
+                      "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"), "peak_concurrent": srv.peak_running,
+                      "peak_hbm_gb": srv.peak_used / 1e9, "errors": errs})
+    best = max(sweep, key=lambda x: x["served_per_s"])
+    line = {
+        "metric": METRIC, "value": best["served_per_s"], "unit": "IDs/s", "n_gpus": world, "steps": len(rates),
+        "warmup": 1, "ms_per_step": 1e3 / best["served_per_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.mode != "bf16" else "bf16",
+        "data": "synthetic (seeded, generated on the device)",
+        "config": {"workload": f"serving: {len(specs)} complex128 ID requests, Poisson arrivals, m, n log-uniform "
+                               f"[256, 16384], k log-uniform [8, 256], l = k + 10",
+                   "mode": args.mode, "slots": args.slots, "rates": rates},
+        "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "sweep": sweep,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,15 +566,29 @@ def main():
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--count", type=int, default=4096, help="problems per batch (--config batched)")
+    ap.add_argument("--requests", type=int, default=64, help="requests per rate (--config serving)")
+    ap.add_argument("--rates", default="5,20,80,320", help="offered request rates per second (--config serving)")
+    ap.add_argument("--slots", type=int, default=8, help="concurrent requests (--config serving)")
     ap.add_argument("--m", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()
     import dataclasses
     import synth
+    world, rank, local = init_dist()
+    if args.config in ("batched", "serving"):
+        if args.impl == "reference":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the CPU oracle is timed on the single-ID workloads only"}), flush=True)
+        elif args.config == "batched":
+            run_batched(args, world, rank, local)
+        else:
+            run_serving(args, world, rank, local)
+        return
     cfg = synth.CONFIGS[args.config]
     if args.m or args.n:
         cfg = dataclasses.replace(cfg, m=args.m or cfg.m, n=args.n or cfg.n)
-    world, rank, local = init_dist()
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
     else:

@@ -85,6 +85,13 @@ typedef enum {
 RID_API rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
                            rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream);
 
+/* Device bytes rid_plan_create would allocate for these arguments (Omega, its
+ * split forms and every workspace), computed without allocating anything:
+ * what a server admitting requests by HBM footprint needs.  Same argument
+ * checks and return codes as rid_plan_create. */
+RID_API rid_status rid_plan_footprint(int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype, rid_mode mode,
+                                      size_t* bytes);
+
 /* Free the plan's device memory (synchronizes its stream first).  NULL is a no-op. */
 RID_API rid_status rid_plan_destroy(rid_plan_t plan);
 

@@ -21,6 +21,8 @@ SIGNATURES = {
     "rid_plan_create": (ctypes.c_int, [ctypes.POINTER(_c_plan), _i64, _i64, _i32, _i32, ctypes.c_int,
                                        ctypes.c_int, _u64, _p]),
     "rid_plan_destroy": (ctypes.c_int, [_c_plan]),
+    "rid_plan_footprint": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
+                                          ctypes.POINTER(ctypes.c_size_t)]),
     "rid_plan_omega": (ctypes.c_int, [_c_plan, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
     "rid_plan_set_omega": (ctypes.c_int, [_c_plan, _p, _i64]),
     "rid_plan_use_srft": (ctypes.c_int, [_c_plan, _u64]),

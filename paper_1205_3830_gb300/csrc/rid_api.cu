@@ -13,6 +13,8 @@ void rid_tc_plan_free_fp64(rid_plan_s* p);
 cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
 int rid_tc_error_word_fp64(const rid_plan_s* p);
 rid_status rid_mx_plan_init(rid_plan_s* p);
+rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run);
+rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run);
 void rid_mx_plan_free(rid_plan_s* p);
 cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
 int rid_mx_error_word(const rid_plan_s* p);
@@ -134,6 +136,44 @@ const char* rid_status_string(rid_status s) {
     case RID_EUNSUPPORTED: return "RID_EUNSUPPORTED: dtype/mode not available";
   }
   return "RID_?: unknown status";
+}
+
+static rid_status check_plan_args(int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype, rid_mode mode) {
+  if (m < 1 || n < 1 || k < 1 || l < k || k > m || k > n) return RID_EINVAL;
+  if (n > 0x7fffffffLL || m > ((int64_t)1 << 40)) return RID_EINVAL;
+  if (l > 512) return RID_EUNSUPPORTED;
+  if (dtype != RID_C128 && dtype != RID_C64) return RID_EINVAL;
+  if (mode < RID_FP64_NATIVE || mode > RID_MIXED_3XTF32) return RID_EINVAL;
+  if (dtype == RID_C128 && (mode == RID_MIXED_BF16 || mode == RID_MIXED_3XTF32)) return RID_EUNSUPPORTED;
+  if (dtype == RID_C64 && (mode == RID_FP64_NATIVE || mode == RID_FP64_EMULATED)) return RID_EUNSUPPORTED;
+  int nr = 0;
+  if (rid_solve_smem_bytes(k, &nr) > 200 * 1024) return RID_EUNSUPPORTED;
+  return RID_OK;
+}
+
+rid_status rid_plan_footprint(int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype, rid_mode mode,
+                              size_t* bytes) {
+  if (!bytes) return RID_EINVAL;
+  const rid_status s = check_plan_args(m, n, k, l, dtype, mode);
+  if (s != RID_OK) return s;
+  rid_plan_s p{};
+  p.m = m; p.n = n; p.k = k; p.l = l;
+  p.dtype = dtype; p.mode = mode;
+  if (cudaGetDevice(&p.device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess)
+    return RID_ECUDA;
+  p.ldo = (m + 15) / 16 * 16;
+  choose_launch_shapes(&p);
+  size_t total = plan_layout(&p).total;
+  if (mode == RID_FP64_EMULATED || mode == RID_MIXED_BF16) {
+    const rid_status t = mode == RID_FP64_EMULATED ? rid_tc_plan_setup_fp64(&p, 1) : rid_mx_plan_setup(&p, 1);
+    if (t != RID_OK) return t;
+    total += p.tc_bytes;
+  } else if (mode != RID_FP64_NATIVE) {
+    return RID_EUNSUPPORTED;
+  }
+  *bytes = total;
+  return RID_OK;
 }
 
 rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,

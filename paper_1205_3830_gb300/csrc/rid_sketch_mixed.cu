@@ -283,7 +283,7 @@ void rid_mx_plan_free(rid_plan_s* p) {
   p->tc_bytes = 0;
 }
 
-rid_status rid_mx_plan_init(rid_plan_s* p) {
+rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run) {
   if (p->mode != RID_MIXED_BF16 || p->dtype != RID_C64) return RID_EUNSUPPORTED;
   MxState* st = (MxState*)calloc(1, sizeof(MxState));
   if (!st) return RID_ENOMEM;
@@ -308,6 +308,11 @@ rid_status rid_mx_plan_init(rid_plan_s* p) {
   const size_t part_bytes = (size_t)st->ksplit * p->n * st->l2p * 4;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   const size_t total = al(om_bytes) + al(a_bytes) + al(part_bytes) + al(4);
+  if (dry_run) {
+    p->tc_bytes = total;
+    free(st);
+    return RID_OK;
+  }
   char* base = nullptr;
   if (cudaMalloc((void**)&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -383,3 +388,5 @@ int rid_mx_error_word(const rid_plan_s* p) {
   cudaStreamSynchronize(p->stream);
   return h;
 }
+
+rid_status rid_mx_plan_init(rid_plan_s* p) { return rid_mx_plan_setup(p, 0); }

@@ -507,7 +507,9 @@ int choose_ksplit(int units, int NC, int sms) {
 
 void rid_tc_plan_free_fp64(rid_plan_s* p);
 
-rid_status rid_tc_plan_init_fp64(rid_plan_s* p) {
+// dry_run: compute p->tc_bytes (the device bytes the state needs) and return
+// without allocating or launching anything.
+rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
   TcState* st = (TcState*)calloc(1, sizeof(TcState));
   if (!st) return RID_ENOMEM;
@@ -560,6 +562,11 @@ rid_status rid_tc_plan_init_fp64(rid_plan_s* p) {
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   const size_t total = al(om_bytes) + al(a_bytes) + al(aexp_bytes) + al((size_t)p->n * 4) +
                        al((size_t)st->l2 * 4) + al(part_bytes) + al(4);
+  if (dry_run) {
+    p->tc_bytes = total;
+    free(st);
+    return RID_OK;
+  }
   char* base = nullptr;
   if (cudaMalloc((void**)&base, total) != cudaSuccess) {
     cudaGetLastError();
@@ -684,3 +691,5 @@ int rid_tc_error_word_fp64(const rid_plan_s* p) {
   cudaStreamSynchronize(p->stream);
   return h;
 }
+
+rid_status rid_tc_plan_init_fp64(rid_plan_s* p) { return rid_tc_plan_setup_fp64(p, 0); }

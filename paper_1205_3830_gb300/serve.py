@@ -1,0 +1,167 @@
+"""Serving randomized IDs with continuous batching.
+
+Requests (a device-resident complex matrix A, rank k, l, a seed) arrive at
+any time.  A request is admitted when a slot is free and its device
+footprint (rid_plan_footprint: Omega, its split forms and all workspace, plus
+the outputs Y, perm, T) fits in the HBM budget next to the requests already
+running; otherwise it waits, first come first served.  Each slot is a worker
+thread with its own CUDA stream, so admitted requests run concurrently on the
+device; a request's whole ID runs on its slot's stream, its memory is freed
+when it completes and the next request is admitted at once.
+
+Latency is measured from submit() to the moment the result (J, T, the error
+estimate) is available on the host side of the worker.
+"""
+from __future__ import annotations
+
+import collections
+import ctypes
+import threading
+import time
+
+import torch
+
+from . import Plan, _native, colmajor_empty, MODES, _DTYPES
+from ._native import check
+
+
+def footprint(m, n, k, l, dtype=torch.complex128, mode="fp64_emulated"):
+    """Device bytes one request of this shape holds while it runs."""
+    lib = _native.load()
+    b = ctypes.c_size_t()
+    check(lib.rid_plan_footprint(int(m), int(n), int(k), int(l), _DTYPES[dtype], MODES[mode], ctypes.byref(b)),
+          "rid_plan_footprint")
+    outputs = 16 * l * n + 4 * n + 16 * k * max(0, n - k)
+    return int(b.value) + outputs
+
+
+class Request:
+    __slots__ = ("rid", "A", "k", "l", "seed", "nprobe", "probe_seed", "bytes", "t_submit", "t_admit", "t_done",
+                 "result", "error")
+
+    def __init__(self, rid, A, k, l, seed, nprobe, probe_seed, nbytes):
+        self.rid, self.A, self.k, self.l, self.seed = rid, A, int(k), int(l), int(seed)
+        self.nprobe, self.probe_seed, self.bytes = nprobe, probe_seed, nbytes
+        self.t_submit = time.perf_counter()
+        self.t_admit = self.t_done = None
+        self.result = self.error = None
+
+    @property
+    def latency(self):
+        return None if self.t_done is None else self.t_done - self.t_submit
+
+
+class Server:
+    """slots concurrent IDs, admitted by an HBM budget (bytes)."""
+
+    def __init__(self, slots=8, hbm_budget=None, mode="fp64_emulated", device=None):
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            hbm_budget = int(0.8 * free)
+        self.budget = int(hbm_budget)
+        self.mode = mode
+        self.used = 0
+        self.peak_used = 0
+        self.running = 0
+        self.peak_running = 0
+        self.queue = collections.deque()
+        self.done = []
+        self.cv = threading.Condition()
+        self.stop = False
+        self.workers = [threading.Thread(target=self._worker, args=(i,), daemon=True) for i in range(slots)]
+        for w in self.workers:
+            w.start()
+
+    # -- client side ---------------------------------------------------------------
+    def submit(self, rid, A, k, l, seed, nprobe=8, probe_seed=1):
+        m, n = A.shape
+        nbytes = footprint(m, n, k, l, A.dtype, self.mode)
+        if nbytes > self.budget:
+            raise ValueError(f"request {rid} needs {nbytes} bytes, above the server's budget {self.budget}")
+        req = Request(rid, A, k, l, seed, nprobe, probe_seed, nbytes)
+        with self.cv:
+            self.queue.append(req)
+            self.cv.notify_all()
+        return req
+
+    def drain(self, timeout=None):
+        """Wait until every submitted request is done; returns them in completion order."""
+        t_end = None if timeout is None else time.perf_counter() + timeout
+        with self.cv:
+            while self.queue or self.running:
+                left = None if t_end is None else t_end - time.perf_counter()
+                if left is not None and left <= 0:
+                    raise TimeoutError("requests still running")
+                self.cv.wait(timeout=left)
+            return list(self.done)
+
+    def close(self):
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
+        for w in self.workers:
+            w.join()
+
+    # -- workers -----------------------------------------------------------------------
+    def _admit(self):
+        """Pop the head request once it fits (first come, first served)."""
+        with self.cv:
+            while True:
+                if self.stop and not self.queue:
+                    return None
+                if self.queue and self.used + self.queue[0].bytes <= self.budget:
+                    req = self.queue.popleft()
+                    self.used += req.bytes
+                    self.running += 1
+                    self.peak_used = max(self.peak_used, self.used)
+                    self.peak_running = max(self.peak_running, self.running)
+                    req.t_admit = time.perf_counter()
+                    return req
+                self.cv.wait()
+
+    def _worker(self, slot):
+        torch.cuda.set_device(self.device)
+        stream = torch.cuda.Stream(self.device)
+        while True:
+            req = self._admit()
+            if req is None:
+                return
+            try:
+                with torch.cuda.stream(stream):
+                    req.result = run_one(req.A, req.k, req.l, req.seed, req.nprobe, req.probe_seed, self.mode, stream)
+            except Exception as exc:        # reported with the request, the server keeps running
+                req.error = exc
+            req.t_done = time.perf_counter()
+            with self.cv:
+                self.used -= req.bytes
+                self.running -= 1
+                self.done.append(req)
+                self.cv.notify_all()
+
+
+def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None):
+    """One whole ID on `stream`; returns host copies of J, T and the estimate."""
+    m, n = A.shape
+    stream = stream or torch.cuda.current_stream(A.device)
+    with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream) as plan:
+        Y = colmajor_empty(l, n, device=A.device)
+        perm = torch.empty(n, dtype=torch.int32, device=A.device)
+        T = colmajor_empty(k, n - k, device=A.device)
+        plan.sketch(A, Y)
+        plan.select(Y, perm)
+        plan.solve(Y, T)
+        est, upper = plan.error(A, perm, T, nprobe, probe_seed)     # synchronizes the stream
+        plan.sync_status()
+        return {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper}
+
+
+def latency_stats(reqs):
+    lat = sorted(r.latency for r in reqs if r.latency is not None)
+    if not lat:
+        return {}
+
+    def pct(p):
+        return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
+
+    return {"p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "max_ms": 1e3 * lat[-1], "count": len(lat)}
