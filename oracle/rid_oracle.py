@@ -56,12 +56,16 @@ __all__ = [
     "STREAM_OMEGA",
     "STREAM_PROBES",
     "STREAM_SRFT",
+    "STREAM_LPROBES",
+    "left_probe_matrix",
+    "error_estimate_left",
 ]
 
 # Philox counter "stream" word for each random object of the method.
 STREAM_OMEGA = 3   # the l x m Gaussian test matrix Omega
 STREAM_PROBES = 4  # the n x r Gaussian probes of the error estimate
 STREAM_SRFT = 5    # the SRFT's random phases D and row samples S
+STREAM_LPROBES = 6 # the r x m Gaussian row probes of the row-probe error estimate
 
 
 class RankDeficient(ArithmeticError):
@@ -154,6 +158,11 @@ def gaussian_test_matrix(l, m, seed):
 def probe_matrix(n, r, seed):
     """The n x r complex Gaussian probes of the error estimate (row = column of A)."""
     return complex_gaussian(n, r, seed, STREAM_PROBES)
+
+
+def left_probe_matrix(r, m, seed):
+    """The r x m complex Gaussian row probes of the row-probe error estimate."""
+    return complex_gaussian(r, m, seed, STREAM_LPROBES)
 
 
 # ---------------------------------------------------------------------------
@@ -282,6 +291,30 @@ def error_estimate(A, perm, T, omega):
     est = float(np.max(e_norm / w_norm))
     upper = float(10.0 * math.sqrt(2.0 / math.pi) * np.max(e_norm))
     return est, upper, Ew
+
+
+def error_estimate_left(A, perm, T, G):
+    """Row-probe estimate of ||A - B P||_2 with B = A(:, J).
+
+    E = A - A(:, J) P is formed densely from its definition and Z = G E for the
+    r x m row probes G.  Returns (est, upper, Z): est = max_q ||Z_q|| / ||G_q||
+    (never above ||E||_2) and upper = 10 sqrt(2/pi) max_q ||Z_q||.  This is the
+    probe bound of Halko, Martinsson & Tropp (SIAM Review 2011, Lemma 4.1)
+    applied to E^T, whose 2-norm is that of E; it needs G independent of E,
+    which holds because E depends on A and Omega only.
+    """
+    A = np.asarray(A, dtype=np.complex128)
+    G = np.asarray(G, dtype=np.complex128)
+    n = A.shape[1]
+    k = T.shape[0]
+    P = interpolation_matrix(perm, T, n)
+    E = A - A[:, np.asarray(perm)[:k]] @ P
+    Z = G @ E
+    z_norm = np.sqrt(np.sum(Z.real ** 2 + Z.imag ** 2, axis=1))
+    g_norm = np.sqrt(np.sum(G.real ** 2 + G.imag ** 2, axis=1))
+    est = float(np.max(z_norm / g_norm))
+    upper = float(10.0 * math.sqrt(2.0 / math.pi) * np.max(z_norm))
+    return est, upper, Z
 
 
 def exact_error(A, perm, T):

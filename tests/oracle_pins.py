@@ -245,6 +245,45 @@ def pin_error_estimate(o):
         assert np.abs(direct).max() > 1e3 * 1e-13 * scale     # the check has teeth
 
 
+def pin_error_estimate_left(o):
+    """Row probes.  A residual built to be sigma u v^H on the columns Jc (and 0
+    on J) gives ||g E|| = sigma |sum_i g_i u_i| for every row probe g, a closed
+    form that fixes the probe orientation, the conjugation and the norms; on an
+    ID of a noisy low-rank matrix, est <= ||E||_2 <= upper."""
+    rng = np.random.default_rng(41)
+    m, n, k, r = 60, 25, 4, 5
+    perm = rng.permutation(n)
+    J, Jc = perm[:k], perm[k:]
+    AJ = synth.cgauss(rng, (m, k))
+    T = synth.cgauss(rng, (k, n - k))
+    u = synth.cgauss(rng, (m,))
+    u /= np.linalg.norm(u)
+    v = synth.cgauss(rng, (n - k,))
+    v /= np.linalg.norm(v)
+    sigma = 3e-7
+    A = np.zeros((m, n), dtype=np.complex128)
+    A[:, J] = AJ
+    A[:, Jc] = AJ @ T + sigma * np.outer(u, v.conj())
+    G = o.left_probe_matrix(r, m, 7)
+    assert G.shape == (r, m)
+    est, upper, Z = o.error_estimate_left(A, perm, T, G)
+    gu = np.array([abs(sum(G[q, i] * u[i] for i in range(m))) for q in range(r)])
+    gn = np.array([math.sqrt(sum(abs(G[q, i]) ** 2 for i in range(m))) for q in range(r)])
+    # rounding of A_Jc - A_J T (entries O(k)) leaves ~1e-15 k on a residual of 3e-7
+    assert abs(est - sigma * np.max(gu / gn)) <= 1e-6 * sigma * np.max(gu / gn)
+    assert abs(upper - 10.0 * math.sqrt(2.0 / math.pi) * sigma * np.max(gu)) <= 1e-6 * upper
+    assert np.all(Z[:, J] == 0)
+    # bounds on a real ID
+    m, n, k = 90, 70, 5
+    A = synth.lowrank_plus_noise(m, n, k, 1e-6, seed=22)
+    out = o.rid(A, k, k + 6, seed=5)
+    exact = o.exact_error(A, out["perm"], out["T"])
+    for ps in (1, 2, 3):
+        est, upper, _ = o.error_estimate_left(A, out["perm"], out["T"], o.left_probe_matrix(6, m, ps))
+        assert 0.05 * exact <= est <= exact * (1 + 1e-9)
+        assert exact <= upper
+
+
 # --- the paper's SRFT ---------------------------------------------------------
 def pin_srft(o):
     """S F D A equals rows s of numpy's FFT (along columns) of D A."""
@@ -261,5 +300,5 @@ def pin_srft(o):
 ALL_PINS = [
     pin_philox_kat, pin_uniform53, pin_gaussian_distribution, pin_randomize_exact,
     pin_qr_lapack, pin_qr_pivot_rule, pin_rank_deficient, pin_factor_r, pin_exact_rank,
-    pin_spectrum_bound, pin_brute_force, pin_error_estimate, pin_srft,
+    pin_spectrum_bound, pin_brute_force, pin_error_estimate, pin_error_estimate_left, pin_srft,
 ]

@@ -39,6 +39,11 @@ MUTATIONS = [
     ("probe_sign", "w[J, :] = -(T @ omega[Jc, :])", "w[J, :] = (T @ omega[Jc, :])", [pins.pin_error_estimate]),
     ("upper_constant", "upper = float(10.0 * math.sqrt(2.0 / math.pi) * np.max(e_norm))",
      "upper = float(0.1 * math.sqrt(2.0 / math.pi) * np.max(e_norm))", [pins.pin_error_estimate]),
+    ("left_probe_conjugated", "Z = G @ E", "Z = G.conj() @ E", [pins.pin_error_estimate_left]),
+    ("left_probe_wrong_norm", "g_norm = np.sqrt(np.sum(G.real ** 2 + G.imag ** 2, axis=1))",
+     "g_norm = np.sqrt(np.sum(G.real ** 2, axis=1))", [pins.pin_error_estimate_left]),
+    ("left_probe_P_not_applied", "E = A - A[:, np.asarray(perm)[:k]] @ P", "E = A - A[:, np.asarray(perm)[:k]] @ P.conj()",
+     [pins.pin_error_estimate_left]),
     ("srft_phase_sign", "DA = np.exp(2j * np.pi * phi)[:, None] * A", "DA = np.exp(-2j * np.pi * phi)[:, None] * A",
      [pins.pin_srft]),
     ("srft_dft_sign", "F_rows = np.exp(-2j * np.pi * (jk / m))", "F_rows = np.exp(2j * np.pi * (jk / m))",
