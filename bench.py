@@ -208,7 +208,7 @@ def workload_config(cfg, args):
     ctype = "complex64" if cfg.dtype == "c64" else "complex128"
     return {"workload": f"{cfg.name}: {ctype} {kind}, m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
                         f"{cfg.a_bytes / 2**30:.0f} GiB",
-            "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode,
+            "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode, "estimator": args.estimator,
             "l2": "inputs larger than L2 (A is %.0f GiB, L2 129 MB)" % (cfg.a_bytes / 2**30)}
 
 
@@ -230,6 +230,9 @@ def run_ours(args, cfg, world, rank, local):
     a_dtype = torch.complex64 if cfg.dtype == "c64" else torch.complex128
     plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, dtype=a_dtype, mode=args.mode, stream=stream)
     plan.enable_timing()
+    rows = args.estimator == "rows"
+    if rows:
+        plan.set_probes(args.nprobe, 1)       # the error's products ride along in the sketch
     Y = rid.colmajor_empty(l, n, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     T = rid.colmajor_empty(k, n - k, device=dev)
@@ -242,7 +245,7 @@ def run_ours(args, cfg, world, rank, local):
         if ev: ev[2].record(stream)
         plan.solve(Y, T)
         if ev: ev[3].record(stream)
-        res = plan.error(A, perm, T, args.nprobe, 1)
+        res = plan.error_sketched(perm, T) if rows else plan.error(A, perm, T, args.nprobe, 1)
         if ev: ev[4].record(stream)
         return res
 
@@ -271,14 +274,24 @@ def run_ours(args, cfg, world, rank, local):
            for i, name in enumerate(("sketch", "select", "solve", "error"))}
     st = plan.stats()
     launches = args.steps * (st["sketch_launches"] + st["select_launches"] + st["solve_launches"] +
-                             st["error_launches"])
+                             (2 if rows else st["error_launches"]))
+    # the column-probe estimator (a second pass over A), timed once for context
+    col_ms = None
+    if rows:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.error(A, perm, T, args.nprobe, 1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        col_ms = e0.elapsed_time(e1)
     value = world * cfg.a_bytes / 1e9 / (ms_step / 1e3)
 
     # roofline of the dominant kernel (the sketch's product) and of the whole ID
     peaks = measured_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     bf16_sust = float(peaks.get("bf16_tflops_sustained", 1724.5))
-    sketch_flops = 8.0 * l * m * n                       # complex l x m x n product
+    ls = l + (args.nprobe if rows else 0)               # rows of the product: Omega, then the row probes
+    sketch_flops = 8.0 * ls * m * n                      # complex ls x m x n product
     k_ms = [statistics.mean(t[i] for t in kernel_ms) for i in range(3)]
     t_prod = k_ms[1] / 1e3
     fp64_equiv = {"achieved": sketch_flops / t_prod / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s"}
@@ -287,30 +300,32 @@ def run_ours(args, cfg, world, rank, local):
         roof = {"bound": "alu", "achieved": fp64_equiv["achieved"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": fp64_equiv["frac"], "traffic": None, "kernel": "sketch_fp64_kernel",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flops x 2.07 GHz (a DFMA probe measured 1.20)",
-                "per_launch": "8 l m n flops (complex product)"}
+                "per_launch": "8 (l + r) m n flops (complex product, r row probes)" if rows else "8 l m n flops"}
         tc_flops = None
     else:
         # the emulation's own work: BF16 slice-pair products of the real
         # (2l x 2m) x (2m x n) problem, 2 flops per multiply-add (28 pairs for the
         # FP64-grade digits, 6 for the BF16x3 splits of the mixed mode)
         pairs = 28 if args.mode == "fp64_emulated" else 6
-        tc_flops = pairs * 2.0 * (2 * l) * (2 * m) * n
+        tc_flops = pairs * 2.0 * (2 * ls) * (2 * m) * n
         achieved = tc_flops / t_prod / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sust,
                 "traffic": TC_TRAFFIC.get("bytes_per_launch") if args.mode == "fp64_emulated" and tc_source_unchanged() else None,
                 "kernel": "sketch_tc_kernel" if args.mode == "fp64_emulated" else "sketch_mixed_kernel",
                 "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
-                "per_launch": f"{pairs} slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
+                "per_launch": f"{pairs} slice pairs x 2 x (2 ls)(2m)n flops, ls = l + r row probes" if rows else
+                              f"{pairs} slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
     # whole-ID roofline: sum over steps of max(bytes / HBM, flops / the peak of the pipe used)
     p64 = FP64_PEAK_TFLOPS * 1e12
     a_b = float(cfg.a_bytes)
     sketch_roof = (max(a_b / (hbm * 1e9), sketch_flops / p64) if tc_flops is None
                    else max(a_b / (hbm * 1e9), tc_flops / (bf16_sust * 1e12)))
+    err_roof = (max(16.0 * k * (n - k) / (hbm * 1e9), 8.0 * k * (n - k) * args.nprobe / p64) if rows
+                else max(a_b / (hbm * 1e9), 8.0 * m * n * args.nprobe / p64))
     t_roof = (sketch_roof +
               max(2 * 16.0 * l * n * k / (hbm * 1e9), 16.0 * n * (l * k - k * k / 2) / p64) +
-              4.0 * k * k * (n - k) / p64 +
-              max(a_b / (hbm * 1e9), 8.0 * m * n * args.nprobe / p64))
+              4.0 * k * k * (n - k) / p64 + err_roof)
     id_frac = t_roof / (ms_step / 1e3)
 
     line = {
@@ -324,7 +339,10 @@ def run_ours(args, cfg, world, rank, local):
         "step_ms": per,
         "sketch_kernel_ms": {"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2]},
         "gpu_launches": launches,
-        "error_estimate": {"est": est, "upper": upper},
+        "error_estimate": {"est": est, "upper": upper,
+                           "estimator": ("row probes multiplied in the sketch's pass over A" if rows
+                                         else "column probes, a second pass over A"),
+                           "column_probe_pass_ms": col_ms},
         "clocks": clocks,
     }
 
@@ -356,7 +374,10 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
         plan.sketch(A, Y)
         plan.select(Y, perm)
         plan.solve(Y, T)
-        plan.error(A, perm, T, args.nprobe, 1)
+        if args.estimator == "rows":
+            plan.error_sketched(perm, T)
+        else:
+            plan.error(A, perm, T, args.nprobe, 1)
         perm_h.copy_(perm, non_blocking=True)
         T_h.copy_(T, non_blocking=True)
     stop.record(stream)
@@ -563,6 +584,9 @@ def main():
     ap.add_argument("--config", default="large_tall")
     ap.add_argument("--mode", default="fp64_emulated", choices=("fp64", "fp64_emulated", "bf16"))
     ap.add_argument("--nprobe", type=int, default=8)
+    ap.add_argument("--estimator", choices=("rows", "columns"), default=None,
+                    help="error estimate from row probes multiplied in the sketch (default for the FP64 modes) "
+                         "or from column probes in a second pass over A (default for bf16)")
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -573,6 +597,10 @@ def main():
     ap.add_argument("--m", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()
+    if args.estimator is None:
+        args.estimator = "columns" if args.mode == "bf16" else "rows"
+    if args.estimator == "rows" and args.mode == "bf16":
+        ap.error("row probes need an FP64-grade sketch (--mode fp64 or fp64_emulated)")
     import dataclasses
     import synth
     world, rank, local = init_dist()

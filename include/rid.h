@@ -11,7 +11,9 @@
  *                                     the paper's "faster randomization")
  *   rid_select  Y Pi ~= Q [R1 | R2]   truncated QR with column pivoting (Sec. 2)
  *   rid_solve   R1 T = R2             the factorization of R (Sec. 2, Sec. 3.2)
- *   rid_error   ||A - B P||_2         error of the ID (Sec. 3.3, Table 5)
+ *   rid_error   ||A - B P||_2         error of the ID (Sec. 3.3, Table 5); or
+ *               rid_error_sketched    the same from row probes that rid_sketch
+ *                                     multiplied in its pass over A
  *
  * Conventions shared by every call:
  *   - Matrices are complex, interleaved (re, im), COLUMN-MAJOR with a leading
@@ -153,6 +155,35 @@ RID_API rid_status rid_solve(rid_plan_t plan, const void* Y, int64_t ldy, void* 
 RID_API rid_status rid_error(rid_plan_t plan, const void* A, int64_t lda, const int32_t* perm,
                      const void* T, int64_t ldt, int32_t nprobe, uint64_t probe_seed,
                      double out[2]);
+
+/* Row probes for the error of the ID (Sec. 3.3), computed in the sketch's
+ * own pass over A.  Appends nprobe rows g_q to Omega: an nprobe x m complex
+ * Gaussian G, entry (q, i) from the Philox block at counter (i lo, i hi, q, 6)
+ * with key = probe_seed and Box-Muller as for Omega, independent of Omega.
+ * Every later rid_sketch also computes X = G A (nprobe x n, plan memory) in
+ * the same pass as Y = Omega A; Y is unchanged.  nprobe = 0 removes them.
+ *   1 <= nprobe <= 16 and l + nprobe <= 512 (RID_EINVAL / RID_EUNSUPPORTED).
+ *   Modes RID_FP64_NATIVE and RID_FP64_EMULATED only (RID_EUNSUPPORTED
+ *   otherwise: an FP32-grade X cannot resolve an FP64-grade residual).
+ *   Allocates (l + nprobe) x m complex128 for Omega and G plus small buffers
+ *   (RID_ENOMEM if that fails; the plan is then unchanged) and synchronizes
+ *   the stream.  rid_plan_omega still returns the l rows of the test matrix. */
+RID_API rid_status rid_plan_set_probes(rid_plan_t plan, int32_t nprobe, uint64_t probe_seed);
+
+/* Error of the ID from the row probes of the last rid_sketch, without reading
+ * A.  E = A - A(:, J) P has E(:, J) = 0 and E(:, perm[k+i]) =
+ * A(:, perm[k+i]) - A(:, J) T(:, i), so
+ *   (g_q E)(perm[k+i]) = X(q, perm[k+i]) - sum_a X(q, perm[a]) T(a, i).
+ *   out (HOST, double[2]): out[0] = max_q ||g_q E|| / ||g_q|| (never above
+ *   ||E||_2); out[1] = 10 sqrt(2/pi) max_q ||g_q E||, an upper bound on
+ *   ||E||_2 with probability >= 1 - 10^-r (Halko, Martinsson & Tropp 2011,
+ *   Lemma 4.1, applied to E^T, whose 2-norm is that of E).
+ *   perm, T: the outputs of rid_select and rid_solve for the Y of that
+ *   rid_sketch (T may be null when n == k).  RID_EINVAL if no row probes are
+ *   set or no rid_sketch ran since they were set.  Synchronizes the stream;
+ *   returns RID_ERANK if the last rid_select found a rank-deficient sketch. */
+RID_API rid_status rid_error_sketched(rid_plan_t plan, const int32_t* perm, const void* T, int64_t ldt,
+                                      double out[2]);
 
 /* Synchronize the plan's stream and return the device status word
  * (RID_OK or RID_ERANK), or RID_ECUDA if the stream reported an error. */

@@ -72,6 +72,7 @@ class Plan:
         self.seed = int(seed)
         self.dtype = dtype
         self.mode = mode
+        self.nrow = 0
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         if stream is None:
@@ -165,6 +166,22 @@ class Plan:
                                   ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(ptr),
                                   max(_ld(T), self.k), int(nprobe), int(probe_seed) & (2 ** 64 - 1),
                                   out), "rid_error")
+        return float(out[0]), float(out[1])
+
+    def set_probes(self, nprobe=8, probe_seed=1):
+        """Row probes G (nprobe x m) multiplied by every later sketch in its pass
+        over A, for error_sketched(); nprobe = 0 removes them (synchronizes)."""
+        check(self._lib.rid_plan_set_probes(self._h, int(nprobe), int(probe_seed) & (2 ** 64 - 1)),
+              "rid_plan_set_probes")
+        self.nrow = int(nprobe)
+
+    def error_sketched(self, perm, T):
+        """(est, upper) of ||A - A(:, J) P||_2 from the row probes of the last
+        sketch: no pass over A (synchronizes)."""
+        out = (ctypes.c_double * 2)()
+        ptr = T.data_ptr() if T.numel() else 0
+        check(self._lib.rid_error_sketched(self._h, ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(ptr),
+                                           max(_ld(T), self.k), out), "rid_error_sketched")
         return float(out[0]), float(out[1])
 
     def stats(self):

@@ -2,6 +2,8 @@
 // kernels.  Every entry point validates its arguments on the host before it
 // launches anything.
 #include <stdlib.h>
+
+#include <algorithm>
 #include <string.h>
 
 #include "rid_internal.cuh"
@@ -163,6 +165,7 @@ rid_status rid_plan_footprint(int64_t m, int64_t n, int32_t k, int32_t l, rid_dt
       cudaDeviceGetAttribute(&p.num_sms, cudaDevAttrMultiProcessorCount, p.device) != cudaSuccess)
     return RID_ECUDA;
   p.ldo = (m + 15) / 16 * 16;
+  p.ls = l;
   choose_launch_shapes(&p);
   size_t total = plan_layout(&p).total;
   if (mode == RID_FP64_EMULATED || mode == RID_MIXED_BF16) {
@@ -199,6 +202,7 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
   if (e != cudaSuccess) { free(p); return RID_ECUDA; }
   p->ldo = (m + 15) / 16 * 16;     // 256-byte aligned rows of Omega
+  p->ls = l;
   choose_launch_shapes(p);
 
   const Layout L = plan_layout(p);
@@ -206,6 +210,7 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   e = cudaMalloc((void**)&base, L.total);
   if (e != cudaSuccess) { free(p); cudaGetLastError(); return RID_ENOMEM; }
   p->ws_bytes = L.total;
+  p->ws_base = base;
   p->omega = (double2*)(base + L.omega);
   p->status = (int*)(base + L.status);
   p->sk_partial = (double2*)(base + L.sk_partial);
@@ -249,7 +254,8 @@ rid_status rid_plan_destroy(rid_plan_t p) {
   if (p->timing)
     for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
   rid_tc_plan_free(p);
-  cudaFree((void*)p->omega);   // the omega piece is the start of the single allocation
+  if (p->probe_base) cudaFree(p->probe_base);
+  cudaFree(p->ws_base);
   free(p);
   return RID_OK;
 }
@@ -289,6 +295,71 @@ rid_status rid_plan_use_srft(rid_plan_t p, uint64_t srft_seed) {
   return from_cuda(e);
 }
 
+rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
+  if (!p || nprobe < 0 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  if (nprobe > 0 && p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED) return RID_EUNSUPPORTED;
+  if (p->l + nprobe > 512) return RID_EUNSUPPORTED;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  const int32_t ls = p->l + nprobe;
+  char* base = nullptr;
+  size_t total = 0, o_x = 0, o_norm = 0, o_part = 0, o_sk = 0;
+  const int lp_grid = (int)std::min<int64_t>(std::max<int64_t>((p->n - p->k + 7) / 8, 1), 2 * (int64_t)p->num_sms);
+  if (nprobe > 0) {
+    // Omega with the probe rows below it, X = G A, ||g_q||^2, partial sums,
+    // and (native FP64, split K) partials with ls rows
+    auto take = [&](size_t bytes) { size_t at = total; total += align256(bytes); return at; };
+    take((size_t)ls * p->ldo * sizeof(double2));
+    o_x = take((size_t)nprobe * p->n * sizeof(double2));
+    o_norm = take((size_t)nprobe * sizeof(double));
+    o_part = take((size_t)lp_grid * RID_MAX_PROBES * sizeof(double));
+    o_sk = take(p->mode == RID_FP64_NATIVE && p->split_k > 1 ? (size_t)p->split_k * ls * p->n * sizeof(double2) : 0);
+    if (cudaMalloc((void**)&base, total) != cudaSuccess) {
+      cudaGetLastError();
+      return RID_ENOMEM;
+    }
+    // the l rows of the test matrix, then G (Philox stream 6, key probe_seed)
+    e = cudaMemcpyAsync(base, p->omega, (size_t)p->l * p->ldo * sizeof(double2), cudaMemcpyDeviceToDevice,
+                        p->stream);
+    if (e == cudaSuccess)
+      e = rid_launch_gaussian((double2*)base + (int64_t)p->l * p->ldo, nprobe, p->m, p->ldo, 1, probe_seed,
+                              RID_STREAM_LPROBES, p->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e != cudaSuccess) {
+      cudaFree(base);
+      return from_cuda(e);
+    }
+  }
+  // switch the plan over (the old Omega is no longer read)
+  rid_tc_plan_free(p);
+  if (nprobe > 0) {
+    if (p->probe_base) cudaFree(p->probe_base);
+    p->probe_base = base;
+    p->probe_bytes = total;
+    p->omega = (double2*)base;
+    p->xrow = (double2*)(base + o_x);
+    p->grow_norm2 = (double*)(base + o_norm);
+    p->lp_part = (double*)(base + o_part);
+    p->lp_grid = lp_grid;
+    if (p->mode == RID_FP64_NATIVE && p->split_k > 1) p->sk_partial = (double2*)(base + o_sk);
+  }
+  // nprobe == 0 keeps the current Omega allocation; only its first l rows are read
+  p->ls = ls;
+  p->nrow = nprobe;
+  p->x_valid = 0;
+  if (nprobe > 0) {
+    e = rid_launch_row_probe_norms(p);
+    if (e != cudaSuccess) return from_cuda(e);
+  }
+  if (p->mode != RID_FP64_NATIVE) {
+    const rid_status s = rid_tc_plan_init(p);
+    if (s != RID_OK) return s;
+  }
+  return from_cuda(cudaStreamSynchronize(p->stream));
+}
+
 rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t ldy) {
   if (!p || !A || !Y || lda < p->m || ldy < p->l) return RID_EINVAL;
   if (!aligned16(Y) || ((uintptr_t)A & (p->dtype == RID_C128 ? 15u : 7u))) return RID_EINVAL;
@@ -299,6 +370,7 @@ rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t
     e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy);
   else
     e = rid_tc_sketch(p, A, lda, (double2*)Y, ldy);
+  if (e == cudaSuccess && p->nrow > 0) p->x_valid = 1;
   return from_cuda(e);
 }
 
@@ -342,6 +414,28 @@ rid_status rid_error(rid_plan_t p, const void* A, int64_t lda, const int32_t* pe
   return status == RID_OK ? RID_OK : (rid_status)status;
 }
 
+rid_status rid_error_sketched(rid_plan_t p, const int32_t* perm, const void* T, int64_t ldt, double out[2]) {
+  if (!p || !perm || !out || ldt < p->k) return RID_EINVAL;
+  if (p->n > p->k && !T) return RID_EINVAL;
+  if (p->nrow < 1 || !p->x_valid) return RID_EINVAL;
+  if (((uintptr_t)perm & 3u) || (T && !aligned16(T))) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = rid_launch_error_sketched(p, perm, (const double2*)T, ldt);
+  if (e != cudaSuccess) return from_cuda(e);
+  double host[2];
+  int status = 0;
+  e = cudaMemcpyAsync(host, p->err_out, sizeof(host), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&status, p->status, sizeof(int), cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  out[0] = host[0];
+  out[1] = host[1];
+  if (p->mode != RID_FP64_NATIVE && rid_tc_error_word(p) != 0) return RID_ETIMEOUT;
+  return status == RID_OK ? RID_OK : (rid_status)status;
+}
+
 rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   if (!p || !out) return RID_EINVAL;
   out[0] = p->mode == RID_FP64_NATIVE ? (p->split_k > 1 ? 2 : 1) : p->tc_sketch_launches;
@@ -349,7 +443,7 @@ rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   out[2] = p->n > p->k ? 1 : 0;
   out[3] = p->n > p->k ? 6 : 5;
   out[4] = p->split_k;
-  out[5] = (int64_t)(p->ws_bytes + p->tc_bytes);
+  out[5] = (int64_t)(p->ws_bytes + p->tc_bytes + p->probe_bytes);
   out[6] = p->mode;
   out[7] = p->dtype;
   return RID_OK;

@@ -243,3 +243,122 @@ cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
                                                          p->err_out);
   return cudaGetLastError();
 }
+
+// ---------------------------------------------------------------------------
+// Row probes fused into the sketch.  G (rows l..ls-1 of Omega) is drawn
+// independently of Omega, so Lemma 4.1 of Halko, Martinsson & Tropp (2011)
+// holds for E^T and the row probes g_q:  ||E||_2 <= 10 sqrt(2/pi) max ||g_q E||
+// with probability >= 1 - 10^-r.  The sketch wrote X = G A next to Y; since
+// E(:, J) = 0 and E(:, perm[k+i]) = A(:, perm[k+i]) - A_J T(:, i),
+//   (g_q E)(perm[k+i]) = X(q, perm[k+i]) - sum_a X(q, perm[a]) T(a, i),
+// which needs k (n-k) products per probe and no access to A.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int LP_THREADS = 256;
+constexpr int LP_WARPS = LP_THREADS / 32;
+
+// ||g_q||^2 over the m entries of row l + q of Omega, one CTA per probe.
+__global__ void __launch_bounds__(EW_THREADS)
+row_probe_norm_kernel(const double2* __restrict__ G, int64_t ldo, int64_t m, double* __restrict__ out) {
+  __shared__ double red[EW_THREADS / 32];
+  const double2* g = G + (int64_t)blockIdx.x * ldo;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < m; i += EW_THREADS) s += cabs2(g[i]);
+  s = block_sum_256(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+// One warp per column i of T: lanes split the k-long dot products X_q(J) T(:, i)
+// (X_q(J) staged q-major in shared memory), a fixed-order shuffle tree sums
+// them, lane 0 forms |Z_q(i)|^2.  part[b][q] = the CTA's sum over its columns.
+__global__ void __launch_bounds__(LP_THREADS)
+row_probe_resid_kernel(const double2* __restrict__ X, int r, const int32_t* __restrict__ perm,
+                       const double2* __restrict__ T, int64_t ldt, int k, int64_t ncols,
+                       double* __restrict__ part) {
+  extern __shared__ double2 xj[];                 // xj[q * k + a] = X(q, perm[a])
+  __shared__ double wsum[LP_WARPS][RM];
+  for (int e = threadIdx.x; e < k * r; e += LP_THREADS) {
+    const int q = e / k, a = e - q * k;
+    xj[e] = X[q + (int64_t)perm[a] * r];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double sq[RM];
+#pragma unroll
+  for (int q = 0; q < RM; ++q) sq[q] = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * LP_WARPS + warp; i < ncols; i += (int64_t)gridDim.x * LP_WARPS) {
+    double2 acc[RM];
+#pragma unroll
+    for (int q = 0; q < RM; ++q) acc[q] = make_double2(0.0, 0.0);
+    const double2* Ti = T + i * ldt;
+    for (int a = lane; a < k; a += 32) {
+      const double2 t = Ti[a];
+#pragma unroll
+      for (int q = 0; q < RM; ++q)
+        if (q < r) acc[q] = cfma(xj[q * k + a], t, acc[q]);
+    }
+    const int64_t col = perm[k + i];
+#pragma unroll
+    for (int q = 0; q < RM; ++q) {
+      if (q < r) {
+        double2 v = acc[q];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+          v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+          v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+        }
+        if (lane == 0) {
+          const double2 x = X[q + col * r];
+          sq[q] += cabs2(make_double2(x.x - v.x, x.y - v.y));
+        }
+      }
+    }
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < RM; ++q) wsum[warp][q] = sq[q];
+  __syncthreads();
+  if (threadIdx.x < r) {
+    double s = 0.0;
+    for (int w = 0; w < LP_WARPS; ++w) s += wsum[w][threadIdx.x];
+    part[(int64_t)blockIdx.x * RM + threadIdx.x] = s;
+  }
+}
+
+__global__ void row_probe_finalize_kernel(const double* __restrict__ part, int blocks, int r,
+                                          const double* __restrict__ g_norm2, double* __restrict__ out) {
+  if (threadIdx.x != 0) return;
+  double est = 0.0, zmax = 0.0;
+  for (int q = 0; q < r; ++q) {
+    double s = 0.0;
+    for (int b = 0; b < blocks; ++b) s += part[(int64_t)b * RM + q];
+    const double zn = sqrt(s);
+    const double ratio = zn / sqrt(g_norm2[q]);
+    if (ratio > est) est = ratio;
+    if (zn > zmax) zmax = zn;
+  }
+  out[0] = est;
+  out[1] = 10.0 * sqrt(0.63661977236758134308 /* 2 / pi */) * zmax;
+}
+
+}  // namespace
+
+cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p) {
+  row_probe_norm_kernel<<<p->nrow, EW_THREADS, 0, p->stream>>>(p->omega + (int64_t)p->l * p->ldo, p->ldo, p->m,
+                                                              p->grow_norm2);
+  return cudaGetLastError();
+}
+
+cudaError_t rid_launch_error_sketched(const rid_plan_s* p, const int32_t* perm, const double2* T, int64_t ldt) {
+  const int64_t ncols = p->n - p->k;
+  const size_t smem = (size_t)p->k * p->nrow * sizeof(double2);   // <= 512 * 16 * 16 = 128 KiB
+  cudaError_t e = cudaFuncSetAttribute(row_probe_resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  row_probe_resid_kernel<<<p->lp_grid, LP_THREADS, smem, p->stream>>>(p->xrow, p->nrow, perm, T, ldt, p->k, ncols,
+                                                                      p->lp_part);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  row_probe_finalize_kernel<<<1, 32, 0, p->stream>>>(p->lp_part, p->lp_grid, p->nrow, p->grow_norm2, p->err_out);
+  return cudaGetLastError();
+}

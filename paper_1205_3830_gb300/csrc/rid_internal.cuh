@@ -19,11 +19,13 @@ struct rid_plan_s {
   int device;
   int num_sms;
 
-  double2* omega;          // l x m complex128, row-major, row stride ldo
+  double2* omega;          // ls x m complex128, row-major, row stride ldo: the l rows of
+                           // the test matrix, then the row probes G (rows l..ls-1)
   int64_t ldo;
+  int32_t ls;              // rows the sketch computes: l + nrow
   int* status;             // device status word (RID_OK / RID_ERANK)
 
-  // sketch (native FP64): split-K partial sums, split_k x l x n (ld = l)
+  // sketch (native FP64): split-K partial sums, split_k x ls x n (ld = ls)
   int split_k;
   int64_t k_per_split;
   double2* sk_partial;
@@ -46,7 +48,18 @@ struct rid_plan_s {
   double* norm_part;       // err_row_blocks x RID_MAX_PROBES
   double* err_out;         // 2 doubles (device)
 
-  size_t ws_bytes;         // bytes of the plan's single workspace allocation
+  size_t ws_bytes;         // bytes of the plan's workspace allocation
+  void* ws_base;           // that allocation (Omega starts it until row probes are set)
+
+  // row probes fused into the sketch (rid_plan_set_probes)
+  int32_t nrow;            // row probes (0: none)
+  int x_valid;             // a rid_sketch has written X since the probes were set
+  double2* xrow;           // X = G A: nrow x n, column-major, ld nrow
+  double* grow_norm2;      // ||g_q||^2, nrow
+  double* lp_part;         // lp_grid x RID_MAX_PROBES partial sums of |g_q E|^2
+  int lp_grid;
+  void* probe_base;        // allocation of Omega + G, X, norms, partials (null: none)
+  size_t probe_bytes;
 
   // optional per-kernel timing of rid_sketch (CUDA events on the plan's stream)
   int timing;
@@ -62,6 +75,7 @@ struct rid_plan_s {
 #define RID_STREAM_OMEGA 3u
 #define RID_STREAM_PROBES 4u
 #define RID_STREAM_SRFT 5u
+#define RID_STREAM_LPROBES 6u
 
 // ---------------------------------------------------------------------------
 // Launchers (each returns cudaGetLastError() of its launches).
@@ -86,6 +100,11 @@ size_t rid_solve_smem_bytes(int k, int* nr_out);
 cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
                              const int32_t* perm, const double2* T, int64_t ldt, int nprobe,
                              uint64_t probe_seed);
+
+// ||g_q||^2 of the row probes (rows l..ls-1 of Omega), once per rid_plan_set_probes.
+cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p);
+// est / upper from X of the last sketch, perm and T, into p->err_out.
+cudaError_t rid_launch_error_sketched(const rid_plan_s* p, const int32_t* perm, const double2* T, int64_t ldt);
 
 // ---------------------------------------------------------------------------
 // Device helpers shared by the kernels.

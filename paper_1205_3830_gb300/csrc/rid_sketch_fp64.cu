@@ -7,7 +7,8 @@
 // shared memory.  The FP64 pipe of GB300 (about 2 DFMA per clock per SM)
 // bounds this kernel; every other resource is far from its limit.
 // Split-K partials are summed by a second kernel in a fixed order, so the
-// result does not depend on scheduling.
+// result does not depend on scheduling.  With row probes set, Omega has
+// ls = l + r rows: rows below l go to Y, the r probe rows to X = G A.
 #include "rid_internal.cuh"
 
 namespace {
@@ -19,7 +20,8 @@ constexpr int BK = 16;   // reduction chunk (complex elements)
 __global__ void __launch_bounds__(256)
 sketch_fp64_kernel(const double2* __restrict__ Om, int64_t ldo, const double2* __restrict__ A,
                    int64_t lda, double2* __restrict__ out, int64_t ldout, int64_t out_split_stride,
-                   int64_t l, int64_t m, int64_t n, int64_t k_per_split) {
+                   int64_t l, int64_t m, int64_t n, int64_t k_per_split, int64_t ly,
+                   double2* __restrict__ X, int64_t ldx) {
   __shared__ double2 Os[BL][BK + 1];
   __shared__ double2 As[BN][BK + 1];
   const int tid = threadIdx.x;
@@ -64,14 +66,17 @@ sketch_fp64_kernel(const double2* __restrict__ Om, int64_t ldo, const double2* _
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
       const int64_t gi = i0 + ty + 16 * a, gj = j0 + tx + 16 * b;
-      if (gi < l && gj < n) dst[gi + gj * ldout] = acc[a][b];
+      if (gi < l && gj < n) {
+        if (gi < ly) dst[gi + gj * ldout] = acc[a][b];
+        else X[(gi - ly) + gj * ldx] = acc[a][b];
+      }
     }
 }
 
-// Y(i, j) = sum_{s = 0..S-1} partial_s(i, j), in that order.
+// Y(i, j) = sum_{s = 0..S-1} partial_s(i, j), in that order (rows i >= ly: X).
 __global__ void splitk_reduce_kernel(const double2* __restrict__ part, int64_t split_stride,
                                      int splits, double2* __restrict__ Y, int64_t ldy, int64_t l,
-                                     int64_t n) {
+                                     int64_t n, int64_t ly, double2* __restrict__ X, int64_t ldx) {
   const int64_t total = l * n;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
@@ -82,7 +87,8 @@ __global__ void splitk_reduce_kernel(const double2* __restrict__ part, int64_t s
       s.x += v.x;
       s.y += v.y;
     }
-    Y[i + j * ldy] = s;
+    if (i < ly) Y[i + j * ldy] = s;
+    else X[(i - ly) + j * ldx] = s;
   }
 }
 
@@ -90,31 +96,32 @@ __global__ void splitk_reduce_kernel(const double2* __restrict__ part, int64_t s
 
 cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_t lda, double2* Y,
                                    int64_t ldy) {
-  const dim3 grid((unsigned)((p->l + BL - 1) / BL), (unsigned)((p->n + BN - 1) / BN),
+  const int64_t ls = p->ls, ly = p->l, ldx = p->nrow > 0 ? p->nrow : 1;
+  const dim3 grid((unsigned)((ls + BL - 1) / BL), (unsigned)((p->n + BN - 1) / BN),
                   (unsigned)p->split_k);
   if (p->timing) {
     cudaEventRecord(p->ev[0], p->stream);
     cudaEventRecord(p->ev[1], p->stream);
   }
   if (p->split_k == 1) {
-    sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, Y, ldy, 0, p->l,
-                                                    p->m, p->n, p->k_per_split);
+    sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, Y, ldy, 0, ls,
+                                                    p->m, p->n, p->k_per_split, ly, p->xrow, ldx);
     if (p->timing) {
       cudaEventRecord(p->ev[2], p->stream);
       cudaEventRecord(p->ev[3], p->stream);
     }
     return cudaGetLastError();
   }
-  const int64_t stride = (int64_t)p->l * p->n;
-  sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, p->sk_partial, p->l,
-                                                  stride, p->l, p->m, p->n, p->k_per_split);
+  const int64_t stride = ls * p->n;
+  sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, p->sk_partial, ls,
+                                                  stride, ls, p->m, p->n, p->k_per_split, ls, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t blocks = (stride + 255) / 256;
   if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
   if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->sk_partial, stride,
-                                                                p->split_k, Y, ldy, p->l, p->n);
+                                                                p->split_k, Y, ldy, ls, p->n, ly, p->xrow, ldx);
   if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return cudaGetLastError();
 }

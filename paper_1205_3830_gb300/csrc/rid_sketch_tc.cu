@@ -437,10 +437,12 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
   }
 }
 
-// Y(i, j) = 2^(E_om + E_A - 16) sum_split partial, rows 2i / 2i+1 -> Re / Im.
+// Y(i, j) = 2^(E_om + E_A - 16) sum_split partial, rows 2i / 2i+1 -> Re / Im;
+// rows i >= ly (the row probes) go to X.
 __global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit, int64_t n, int l, int l2p,
                                  const int* __restrict__ om_exp, const int* __restrict__ a_exp_max,
-                                 double2* __restrict__ Y, int64_t ldy) {
+                                 double2* __restrict__ Y, int64_t ldy, int ly, double2* __restrict__ X,
+                                 int64_t ldx) {
   const int64_t total = n * l;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / l;
@@ -452,8 +454,10 @@ __global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit,
       im += (double)p[1].x + (double)p[1].y;
     }
     const int ea = a_exp_max[j];
-    Y[i + j * ldy] = make_double2(ea == TC_EXP_ZERO ? 0.0 : ldexp(re, om_exp[2 * i] + ea - 16),
-                                  ea == TC_EXP_ZERO ? 0.0 : ldexp(im, om_exp[2 * i + 1] + ea - 16));
+    const double2 v = make_double2(ea == TC_EXP_ZERO ? 0.0 : ldexp(re, om_exp[2 * i] + ea - 16),
+                                   ea == TC_EXP_ZERO ? 0.0 : ldexp(im, om_exp[2 * i + 1] + ea - 16));
+    if (i < ly) Y[i + j * ldy] = v;
+    else X[(i - ly) + j * ldx] = v;
   }
 }
 
@@ -516,7 +520,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   st->S = TC_S;
   st->NC = (int)((2 * p->m + TC_KC - 1) / TC_KC);
   st->KP = (int64_t)st->NC * TC_KC;
-  st->l2 = 2 * p->l;
+  st->l2 = 2 * p->ls;         // the test matrix and the row probes
   st->ntiles = (st->l2 + 127) / 128;
   st->tile_w = ((st->l2 + st->ntiles - 1) / st->ntiles + 15) / 16 * 16;
   st->l2p = st->ntiles * st->tile_w;
@@ -593,13 +597,13 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   }
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
   if (e == cudaSuccess) {
-    omega_exp_kernel<<<p->l, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, st->om_exp);
+    omega_exp_kernel<<<p->ls, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, st->om_exp);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    int64_t blocks = ((int64_t)p->l * (st->KP / 2) + 255) / 256;
+    int64_t blocks = ((int64_t)p->ls * (st->KP / 2) + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, p->l, st->KP,
+    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, p->ls, st->KP,
                                                                  st->om_exp, st->om_slices);
     e = cudaGetLastError();
   }
@@ -672,11 +676,12 @@ cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda,
   }
   if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   {
-    const int64_t total = p->n * (int64_t)p->l;
+    const int64_t total = p->n * (int64_t)p->ls;
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->l, st->l2p,
-                                                               st->om_exp, st->a_exp_max, Y, ldy);
+    tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->ls, st->l2p,
+                                                               st->om_exp, st->a_exp_max, Y, ldy, p->l, p->xrow,
+                                                               p->nrow > 0 ? p->nrow : 1);
     e = cudaGetLastError();
   }
   if (p->timing) cudaEventRecord(p->ev[3], p->stream);

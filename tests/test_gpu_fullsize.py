@@ -35,6 +35,7 @@ def run_case(rid, cfg, mode):
     m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
     A = synth.device.device_matrix(cfg)
     with rid.Plan(m, n, k, l, seed=cfg.seed, mode=mode) as plan:
+        plan.set_probes(8, 7)                 # row probes ride along in the sketch
         Y = plan.sketch(A)
         Y_h = Y.cpu().numpy()
         perm = plan.select(Y)
@@ -65,6 +66,28 @@ def run_case(rid, cfg, mode):
         assert abs(up - up_o) <= 10 * math.sqrt(2 / math.pi) * np.max(bound_q) + 1e-12 * up_o
         # sigma_{k+1} <~ 1e-12: the ID error obeys 10 sqrt(1 + k (n - k)) sigma_{k+1}
         assert est <= 10 * math.sqrt(1 + k * (n - k)) * 1.1 * cfg.eps
+        # the row-probe estimate on the same (perm, T).  A dense E does not fit
+        # on the host at this size; E(:, J) = 0 exactly, so the host forms
+        # Z = X(Jc) - X(J) T from X = G A in FP64 (library products).
+        est_s, up_s = plan.error_sketched(torch.from_numpy(perm_o.astype(np.int32)).cuda(), to_dev_colmajor(To))
+        G = oracle.left_probe_matrix(8, m, 7)
+        X = G @ A_h
+        J, Jc = perm_o[:k], perm_o[k:]
+        Z = X[:, Jc] - X[:, J] @ To
+        gn = np.linalg.norm(G, axis=1)
+        zn = np.linalg.norm(Z, axis=1)
+        est_h, up_h = np.max(zn / gn), 10 * math.sqrt(2 / math.pi) * np.max(zn)
+        absG = np.abs(G)
+        dX = 2 * 4 * (2 * m * U64) * (absG @ np.abs(A_h))          # both sides' products
+        if mode != "fp64":
+            dX = dX + 2.0 ** -46 * (2 * m) * np.outer(absG.max(axis=1), np.abs(A_h).max(axis=0))
+        absT = np.abs(To)
+        dZ = dX[:, Jc] + dX[:, J] @ absT + 2 * 4 * (2 * k * U64) * (np.abs(X[:, J]) @ absT)
+        B = np.linalg.norm(dZ, axis=1)
+        assert abs(est_s - est_h) <= np.max(B / gn) + 1e-12 * est_h
+        assert abs(up_s - up_h) <= 10 * math.sqrt(2 / math.pi) * np.max(B) + 1e-12 * up_h
+        # both estimators bound the same ||E||_2 from below and above
+        assert est_s <= up * (1 + 1e-9) and est <= up_s * (1 + 1e-9)
 
 
 @pytest.mark.parametrize("mode", ["fp64", "fp64_emulated"])

@@ -1,0 +1,182 @@
+"""Row probes fused into the sketch (rid_plan_set_probes / rid_error_sketched)
+against the oracle's row-probe estimate (oracle.error_estimate_left), which
+forms E = A - A(:, J) P densely from its definition.
+
+Tolerance: the CUDA path computes Z_q = X_q(Jc) - X_q(J) T from X = G A, the
+oracle Z_q = G_q (A - A_J P).  With dX the sketch bound on X (the dot-product
+bound, plus 2^-46 (2m) max|g_q| max|A_j| for the emulated product) the two
+differ by at most
+  dZ = dX(Jc) + dX(J) |T| + 4 gamma_k |X_J| |T|            (CUDA path)
+     + 4 (gamma_m + gamma_k) |G| (|A| + |A_J| |P|)(Jc)      (oracle)
+per entry, so |est - est_o| <= max_q ||dZ_q|| / ||g_q||; the two generators
+of G agree to 1e-14 relative, which moves the estimate by 1e-13 ||E||_F at
+most.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import U64, dot_bound, to_dev_colmajor, to_host
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [
+    (2048, 1024, 32, 40),
+    (1000, 777, 17, 25),
+    (50, 300, 40, 60),
+    (4096, 333, 1, 3),
+    (300, 64, 64, 70),
+    (513, 129, 9, 9),
+]
+MODES = ["fp64", "fp64_emulated"]
+
+
+@pytest.fixture(scope="module")
+def rid():
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    return rid
+
+
+def lowrank(m, n, k, eps=1e-6, seed=0):
+    return synth.lowrank_plus_noise(m, n, k, eps, seed=seed + 3 * m + 5 * n + k)
+
+
+def run_with_probes(rid, A, k, l, seed, mode, nprobe, probe_seed, perm=None, T=None):
+    m, n = A.shape
+    with rid.Plan(m, n, k, l, seed=seed, mode=mode) as plan:
+        plan.set_probes(nprobe, probe_seed)
+        Ad = to_dev_colmajor(A)
+        Y = plan.sketch(Ad)
+        if perm is None:
+            perm_d = plan.select(Y)
+            T_d = plan.solve(Y)
+        else:
+            perm_d = torch.from_numpy(perm.astype(np.int32)).cuda()
+            T_d = to_dev_colmajor(T) if T.size else torch.empty((k, 0), dtype=torch.complex128).cuda()
+        est, up = plan.error_sketched(perm_d, T_d)
+        return est, up, to_host(perm_d), to_host(T_d)
+
+
+def tolerances(A, perm, T, G, mode):
+    """(tol_est, tol_upper): the bound of the module docstring."""
+    m, n = A.shape
+    k = T.shape[0]
+    J, Jc = perm[:k], perm[k:]
+    gk = 2 * k * U64 / (1 - 2 * k * U64)
+    gm = 2 * m * U64 / (1 - 2 * m * U64)
+    X = G @ A
+    dX = dot_bound(G, A)
+    if mode == "fp64_emulated":
+        dX = dX + 2.0 ** -46 * (2 * m) * np.outer(np.abs(G).max(axis=1), np.abs(A).max(axis=0))
+    P = oracle.interpolation_matrix(perm, T, n)
+    absT = np.abs(T)
+    dZ = dX[:, Jc] + dX[:, J] @ absT + 4 * gk * (np.abs(X[:, J]) @ absT)
+    dZ = dZ + 4 * (gm + gk) * (np.abs(G) @ (np.abs(A) + np.abs(A[:, J]) @ np.abs(P)))[:, Jc]
+    B = np.linalg.norm(dZ, axis=1)
+    gn = np.linalg.norm(G, axis=1)
+    EF = np.linalg.norm(A - A[:, J] @ P)
+    tol_est = np.max(B / gn) + 1e-13 * EF
+    tol_up = 10 * math.sqrt(2 / math.pi) * (np.max(B) + 1e-13 * EF * np.max(gn))
+    return tol_est, tol_up
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("nprobe", [1, 8, 16])
+@pytest.mark.parametrize("shape", SHAPES, ids=str)
+def test_row_probe_estimate_matches_oracle(rid, shape, nprobe, mode):
+    m, n, k, l = shape
+    A = lowrank(m, n, k)
+    out = oracle.rid(A, k, l, seed=9)
+    perm, T = out["perm"], out["T"]
+    est, up, _, _ = run_with_probes(rid, A, k, l, 9, mode, nprobe, 41, perm, T)
+    G = oracle.left_probe_matrix(nprobe, m, 41)
+    est_o, up_o, _ = oracle.error_estimate_left(A, perm, T, G)
+    tol_est, tol_up = tolerances(A, perm, T, G, mode)
+    assert abs(est - est_o) <= tol_est + 1e-14 * est_o
+    assert abs(up - up_o) <= tol_up + 1e-14 * up_o
+    if n > k:
+        assert est_o > 100 * tol_est          # the comparison has teeth
+    else:
+        assert est == 0.0 and up == 0.0       # A = B P exactly when every column is in J
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_row_probes_leave_the_sketch_unchanged(rid, mode):
+    m, n, k, l = 3000, 700, 20, 30
+    A = to_dev_colmajor(lowrank(m, n, k))
+    with rid.Plan(m, n, k, l, seed=4, mode=mode) as plan:
+        Y0 = plan.sketch(A).clone()
+        plan.set_probes(8, 2)
+        Y1 = plan.sketch(A).clone()
+        plan.set_probes(0)
+        Y2 = plan.sketch(A).clone()
+    assert torch.equal(Y0, Y1) and torch.equal(Y0, Y2)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_row_probe_estimate_brackets_the_true_error(rid, mode):
+    m, n, k, l = 1500, 600, 25, 35
+    A = lowrank(m, n, k, eps=1e-8)
+    est, up, perm, T = run_with_probes(rid, A, k, l, 3, mode, 8, 5)
+    err = oracle.exact_error(A, perm, T)
+    # est <= ||E||_2 always.  From below: ||g E|| >= sigma_1 |<g, u_1>| with
+    # |<g, u_1>|^2 ~ Exp(1), so the best of 8 probes has ||g E|| >= 0.1 ||E||_2
+    # except with probability (1 - e^-0.01)^8 < 1e-15, and ||g||^2 <= 2m (a
+    # chi-square tail far smaller still): est >= 0.1 ||E||_2 / sqrt(2m).
+    # (Row probes are normalised by ||g|| ~ sqrt(m), so for tall A with a flat
+    # residual spectrum est sits near ||E||_F / sqrt(m).)
+    assert 0.1 * err / math.sqrt(2 * m) <= est <= err * (1 + 1e-6)
+    assert err <= up
+
+
+def test_row_probes_with_srft(rid):
+    m, n, k, l = 1024, 300, 12, 24
+    A = lowrank(m, n, k)
+    Ad = to_dev_colmajor(A)
+    with rid.Plan(m, n, k, l, seed=1, mode="fp64_emulated") as plan:
+        plan.set_probes(6, 8)
+        plan.use_srft(4)                      # replaces the l test rows, keeps the probes
+        Y = plan.sketch(Ad)
+        perm = plan.select(Y)
+        T = plan.solve(Y)
+        est, up = plan.error_sketched(perm, T)
+    perm_h, T_h = to_host(perm), to_host(T)
+    G = oracle.left_probe_matrix(6, m, 8)
+    est_o, up_o, _ = oracle.error_estimate_left(A, perm_h, T_h, G)
+    tol_est, tol_up = tolerances(A, perm_h, T_h, G, "fp64_emulated")
+    assert abs(est - est_o) <= tol_est + 1e-14 * est_o
+    assert abs(up - up_o) <= tol_up + 1e-14 * up_o
+
+
+def test_row_probe_argument_errors(rid):
+    from paper_1205_3830_gb300._native import RIDError
+    m, n, k, l = 256, 100, 5, 10
+    A = to_dev_colmajor(lowrank(m, n, k))
+    with rid.Plan(m, n, k, l, seed=1, mode="fp64_emulated") as plan:
+        Y = plan.sketch(A)
+        perm = plan.select(Y)
+        T = plan.solve(Y)
+        with pytest.raises(RIDError, match="EINVAL"):
+            plan.error_sketched(perm, T)              # no probes set
+        plan.set_probes(4, 1)
+        with pytest.raises(RIDError, match="EINVAL"):
+            plan.error_sketched(perm, T)              # set, but no sketch since
+        with pytest.raises(RIDError, match="EINVAL"):
+            plan.set_probes(17, 1)
+        plan.sketch(A)
+        plan.error_sketched(perm, T)
+        plan.set_probes(0)
+        with pytest.raises(RIDError, match="EINVAL"):
+            plan.error_sketched(perm, T)
+    with rid.Plan(m, n, k, 500, seed=1, mode="fp64") as plan:
+        with pytest.raises(RIDError, match="EUNSUPPORTED"):
+            plan.set_probes(13, 1)                   # l + nprobe > 512
+    with rid.Plan(m, n, k, l, seed=1, dtype=torch.complex64, mode="bf16") as plan:
+        with pytest.raises(RIDError, match="EUNSUPPORTED"):
+            plan.set_probes(4, 1)
