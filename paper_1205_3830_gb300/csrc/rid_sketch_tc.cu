@@ -27,10 +27,14 @@
 // chunk needs them, so flushing overlaps the next chunk's products.
 //
 // Tiles.  M = 128 columns of A (TMEM lanes), N <= 128 rows of Omega' (TMEM
-// columns; N = 128 runs at the full tensor rate), K in 16-element stages with
-// the 32-byte swizzle: one stage holds S A-slice tiles and S Omega-slice
-// tiles (4 KB each).  A K-split over CTAs balances the waves; partial sums are
-// reduced in a fixed order, so results are deterministic.
+// columns; the 2l rows are split evenly into N-tiles, a multiple of 16 each),
+// K in 32-element stages of 64-byte rows with the 64-byte swizzle: one stage
+// holds S A-slice tiles and S Omega-slice tiles.  The N-tiles of one column
+// block form a cluster: each A tile is loaded once and multicast to them, and
+// a stage is released by a multicast commit.  A K-split over CTAs balances
+// the waves; partial sums are reduced in a fixed order, so results are
+// deterministic.  Row probes (rows l.. of Omega) are sliced and multiplied
+// like the test matrix's rows and reduced into X instead of Y.
 #include <climits>
 #include <cudaTypedefs.h>
 
