@@ -69,8 +69,8 @@ rid_status from_cuda(cudaError_t e) {
 
 // Workspace layout of a plan: one allocation, carved into 256-byte aligned pieces.
 struct Layout {
-  size_t omega, status, sk_partial, qr_val, qr_idx, qr_counter, tau, probes, wtilde, wj_part,
-      ew_part, norm_part, err_out, total;
+  size_t omega, status, sk_partial, qr_val, qr_idx, qr_counter, tau, sel_cand, sel_val, sel_idx, sel_bar,
+      probes, wtilde, wj_part, ew_part, norm_part, err_out, total;
 };
 
 Layout plan_layout(const rid_plan_s* p) {
@@ -84,6 +84,10 @@ Layout plan_layout(const rid_plan_s* p) {
   L.qr_idx = take((size_t)p->qr_grid * sizeof(int));
   L.qr_counter = take(sizeof(unsigned));
   L.tau = take((size_t)p->k * sizeof(double2));
+  L.sel_cand = take((size_t)2 * p->sel_grid * p->l * sizeof(double2));
+  L.sel_val = take((size_t)2 * p->sel_grid * sizeof(double));
+  L.sel_idx = take((size_t)2 * p->sel_grid * sizeof(int));
+  L.sel_bar = take(2 * sizeof(unsigned));
   L.probes = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
   L.wtilde = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
   L.wj_part = take((size_t)p->err_wj_grid * p->k * RID_MAX_PROBES * sizeof(double2));
@@ -111,6 +115,7 @@ void choose_launch_shapes(rid_plan_s* p) {
   int64_t g = (p->n + 7) / 8;
   if (g > 4 * sms) g = 4 * sms;
   p->qr_grid = (int)(g < 1 ? 1 : g);
+  p->sel_grid = rid_select_coop_grid(p->device, p->num_sms, p->n, p->l);
   // error
   const int64_t ncols = p->n - p->k;
   int64_t wg = (ncols + 63) / 64;
@@ -218,6 +223,10 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   p->qr_idx = (int*)(base + L.qr_idx);
   p->qr_counter = (unsigned*)(base + L.qr_counter);
   p->tau = (double2*)(base + L.tau);
+  p->sel_cand = (double2*)(base + L.sel_cand);
+  p->sel_val = (double*)(base + L.sel_val);
+  p->sel_idx = (int*)(base + L.sel_idx);
+  p->sel_bar = (unsigned*)(base + L.sel_bar);
   p->probes = (double2*)(base + L.probes);
   p->wtilde = (double2*)(base + L.wtilde);
   p->wj_part = (double2*)(base + L.wj_part);

@@ -36,6 +36,12 @@ struct rid_plan_s {
   int* qr_idx;
   unsigned* qr_counter;
   double2* tau;            // k
+  // select in one cooperative launch (sel_grid CTAs; 0: one launch per step)
+  int sel_grid;
+  double2* sel_cand;       // 2 x sel_grid x l posted columns
+  double* sel_val;         // 2 x sel_grid
+  int* sel_idx;            // 2 x sel_grid
+  unsigned* sel_bar;       // grid barrier: arrivals, generation
 
   // error: probes, modified probes, partial sums, result
   int err_wj_grid;         // CTAs over the columns of T
@@ -92,6 +98,8 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
                                    int64_t ldy);
 
 cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm);
+// CTAs of the cooperative select for n columns on this device (0: not available).
+int rid_select_coop_grid(int device, int num_sms, int64_t n, int l);
 
 cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy, double2* T,
                              int64_t ldt);

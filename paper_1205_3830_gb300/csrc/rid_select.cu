@@ -79,6 +79,84 @@ __device__ double block_sum(double x) {
   return result;
 }
 
+// Reflector scalars in LAPACK zlarfg convention from alpha = Y(j, j) and
+// xnorm2 = sum_{i>j} |Y(i, j)|^2: beta = -sign(Re alpha) ||(alpha, x)||,
+// tau = (beta - alpha) / beta, scale = 1 / (alpha - beta) for v = x * scale.
+// The norm is formed with explicit fma so that every kernel rounds it alike.
+// Returns false when H = I (x = 0 and alpha real): tau = 0, nothing scaled.
+__device__ __forceinline__ bool zlarfg_scalars(double2 alpha, double xnorm2, double2& tau, double2& scale,
+                                               double& beta) {
+  tau = make_double2(0.0, 0.0);
+  scale = make_double2(0.0, 0.0);
+  beta = alpha.x;
+  if (xnorm2 == 0.0 && alpha.y == 0.0) return false;
+  const double nrm = sqrt(fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xnorm2)));
+  beta = alpha.x >= 0.0 ? -nrm : nrm;
+  tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
+  scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
+  return true;
+}
+
+// H^H applied to one column, held in registers: x = in[0..rows),
+// out = x - v (conj(tau) v^H x), and the returned sum_{i>0} |out_i|^2 (valid
+// in lane 0 when norm is set).  R = ceil(rows / 32) register chunks per lane;
+// v is zero beyond rows, so only the stores are predicated.  Both select paths
+// call this, so they round alike.
+template <int R>
+__device__ __forceinline__ double reflect_column(const double2* __restrict__ in, double2* __restrict__ out,
+                                                 const double2* __restrict__ v, double2 ctau, int rows, int lane,
+                                                 bool norm) {
+  double2 x[R];
+  double2 w0 = make_double2(0.0, 0.0), w1 = make_double2(0.0, 0.0);   // two chains for the FP64 pipe
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    x[u] = (i < rows) ? __ldcg(in + i) : make_double2(0.0, 0.0);
+    if (u & 1) w1 = cfma_conj(v[i], x[u], w1);
+    else w0 = cfma_conj(v[i], x[u], w0);
+  }
+  double2 w = make_double2(w0.x + w1.x, w0.y + w1.y);
+  w.x = warp_sum(w.x);
+  w.y = warp_sum(w.y);
+  const double2 s = cmul(ctau, w);                // conj(tau) (v^H x)
+  double nu0 = 0.0, nu1 = 0.0;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    const double2 vi = v[i];
+    x[u].x = fma(-vi.x, s.x, x[u].x);
+    x[u].x = fma(vi.y, s.y, x[u].x);
+    x[u].y = fma(-vi.x, s.y, x[u].y);
+    x[u].y = fma(-vi.y, s.x, x[u].y);
+    if (i < rows) out[i] = x[u];
+    if (u > 0 || lane > 0) {
+      nu0 = fma(x[u].x, x[u].x, nu0);
+      nu1 = fma(x[u].y, x[u].y, nu1);
+    }
+  }
+  return norm ? warp_sum(nu0 + nu1) : 0.0;
+}
+
+// RMAX: the largest chunk count a kernel instantiation handles (8: l <= 256,
+// two CTAs of 128 registers per SM; 16: l <= 512, one CTA per SM).
+template <int RMAX>
+__device__ __forceinline__ double reflect_any(const double2* in, double2* out, const double2* v, double2 ctau,
+                                              int rows, int lane, bool norm) {
+  switch ((rows + 31) >> 5) {
+#define RID_REFLECT_CASE(R) \
+    case R: if (R <= RMAX) return reflect_column<(R <= RMAX ? R : 1)>(in, out, v, ctau, rows, lane, norm); break;
+    RID_REFLECT_CASE(1) RID_REFLECT_CASE(2) RID_REFLECT_CASE(3) RID_REFLECT_CASE(4)
+    RID_REFLECT_CASE(5) RID_REFLECT_CASE(6) RID_REFLECT_CASE(7) RID_REFLECT_CASE(8)
+    RID_REFLECT_CASE(9) RID_REFLECT_CASE(10) RID_REFLECT_CASE(11) RID_REFLECT_CASE(12)
+    RID_REFLECT_CASE(13) RID_REFLECT_CASE(14) RID_REFLECT_CASE(15) RID_REFLECT_CASE(16)
+#undef RID_REFLECT_CASE
+    default: break;
+  }
+  return 0.0;
+}
+
+constexpr int rid_min_blocks(int rmax) { return rmax <= 8 ? 2 : 1; }
+
 struct SelectArgs {
   double2* Y;
   int64_t ldy;
@@ -142,16 +220,9 @@ __device__ void pivot_and_reflect(const SelectArgs& a, int j) {
   for (int i = j + 1 + threadIdx.x; i < a.l; i += blockDim.x) part += cabs2(__ldcg(colj + i));
   const double xnorm2 = block_sum(part);
   if (threadIdx.x == 0) {
-    const double2 alpha = __ldcg(colj + j);
-    double2 tau = make_double2(0.0, 0.0);
-    double2 scale = make_double2(0.0, 0.0);
-    if (!(xnorm2 == 0.0 && alpha.y == 0.0)) {
-      const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
-      const double beta = alpha.x >= 0.0 ? -nrm : nrm;
-      tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-      scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
-      colj[j] = make_double2(beta, 0.0);
-    }
+    double2 tau, scale;
+    double beta;
+    if (zlarfg_scalars(__ldcg(colj + j), xnorm2, tau, scale, beta)) colj[j] = make_double2(beta, 0.0);
     a.tau[j] = tau;
     s_scale = scale;
   }
@@ -181,13 +252,15 @@ __global__ void __launch_bounds__(QR_THREADS) select_init_kernel(SelectArgs a) {
 }
 
 // Step j: apply H_j^H to columns j+1..n-1, new norms, then pivot j+1.
-__global__ void __launch_bounds__(QR_THREADS) select_step_kernel(SelectArgs a, int j) {
+template <int RMAX>
+__global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_step_kernel(SelectArgs a, int j) {
   __shared__ double2 v[32 * QR_PER_LANE];
   if (*(volatile int*)a.status != RID_OK) return;
   const int lane = threadIdx.x & 31;
   const int rows = a.l - j;                         // rows j..l-1 of the reflector
-  for (int i = threadIdx.x; i < rows; i += blockDim.x)
-    v[i] = (i == 0) ? make_double2(1.0, 0.0) : a.Y[(int64_t)j * a.ldy + j + i];
+  const int padded = (rows + 31) & ~31;
+  for (int i = threadIdx.x; i < padded; i += blockDim.x)
+    v[i] = (i == 0) ? make_double2(1.0, 0.0) : (i < rows ? a.Y[(int64_t)j * a.ldy + j + i] : make_double2(0.0, 0.0));
   const double2 t = a.tau[j];
   const double2 ctau = make_double2(t.x, -t.y);
   __syncthreads();
@@ -197,51 +270,243 @@ __global__ void __launch_bounds__(QR_THREADS) select_step_kernel(SelectArgs a, i
   ArgMax best{-1.0, INT_MAX};
   for (int64_t c = j + 1 + gwarp; c < a.n; c += nwarps) {
     double2* col = a.Y + c * a.ldy + j;
-    double2 x[QR_PER_LANE];
-    double2 w = make_double2(0.0, 0.0);
-#pragma unroll
-    for (int u = 0; u < QR_PER_LANE; ++u) {
-      const int i = lane + 32 * u;
-      x[u] = (i < rows) ? col[i] : make_double2(0.0, 0.0);
-      if (i < rows) w = cfma_conj(v[i], x[u], w);
-    }
-    w.x = warp_sum(w.x);
-    w.y = warp_sum(w.y);
-    const double2 s = cmul(ctau, w);                // conj(tau) (v^H y)
-    double nu = 0.0;
-#pragma unroll
-    for (int u = 0; u < QR_PER_LANE; ++u) {
-      const int i = lane + 32 * u;
-      if (i < rows) {
-        const double2 vs = cmul(v[i], s);
-        x[u].x -= vs.x;
-        x[u].y -= vs.y;
-        col[i] = x[u];
-        if (i > 0) nu += cabs2(x[u]);
-      }
-    }
-    nu = warp_sum(nu);
+    const double nu = reflect_any<RMAX>(col, col, v, ctau, rows, lane, true);
     best = better(best, ArgMax{nu, (int)c});
   }
   if (j + 1 >= a.k) return;                         // last step: no further pivot
   if (post_and_check_last(a, best)) pivot_and_reflect(a, j + 1);
 }
 
+// ---------------------------------------------------------------------------
+// All k steps in one cooperative launch (the plan path).
+//
+// The grid stays resident (a cooperative launch guarantees it) and steps
+// through the factorization with one grid barrier per step:
+//   - every CTA reduces the posted (norm, position) pairs to the pivot p_j and
+//     forms reflector j itself from the winner's posted copy of the column
+//     (same data, same code, same block size: bitwise the same result in
+//     every CTA, so nothing is broadcast);
+//   - warps apply H_j^H to the trailing positions c > j; position p_j takes
+//     the column that sat at j (the swap), the pivot's slot is never read, and
+//     column j of R is written one step later, once nobody reads slot j;
+//   - each CTA posts its best (norm, position) and a copy of that column into
+//     the buffer of parity j + 1, so the next step reads posted copies while
+//     the slots themselves are rewritten.
+// Data written by other CTAs is read with L2 loads (ld.global.cg).  Every
+// barrier wait has a clock budget; on expiry the status word becomes
+// RID_ETIMEOUT and the CTA returns.
+// ---------------------------------------------------------------------------
+constexpr long long SEL_WAIT_BUDGET = 4000000000ll;   // clock cycles (~2 s)
+
+struct CoopArgs {
+  double2* Y;
+  int64_t ldy;
+  int l, k;
+  int64_t n;
+  int32_t* perm;
+  double2* tau;
+  int* status;
+  double2* cand;           // [2][G][l] posted columns
+  double* val;             // [2][G] posted norms
+  int* idx;                // [2][G] posted positions
+  unsigned* bar;           // [0] arrivals, [1] generation
+};
+
+__device__ bool grid_sync(const CoopArgs& a) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = a.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(a.bar, 1u) == gridDim.x - 1) {
+      a.bar[0] = 0u;                      // every CTA has arrived: reset, then release
+      __threadfence();
+      atomicAdd(a.bar + 1, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*gen == g) {
+        if (clock64() - t0 > SEL_WAIT_BUDGET) {
+          atomicExch(a.status, (int)RID_ETIMEOUT);
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// The CTA's best pair and a copy of that column, into buffer `buf`.
+__device__ void post_candidate(const CoopArgs& a, ArgMax best, int buf) {
+  const ArgMax r = block_argmax(best);
+  const int64_t slot = (int64_t)buf * gridDim.x + blockIdx.x;
+  if (r.i != INT_MAX) {
+    const double2* col = a.Y + (int64_t)r.i * a.ldy;
+    double2* dst = a.cand + slot * a.l;
+    for (int i = threadIdx.x; i < a.l; i += QR_THREADS) dst[i] = __ldcg(col + i);
+  }
+  if (threadIdx.x == 0) {
+    a.val[slot] = r.v;
+    a.idx[slot] = r.i;
+  }
+  __threadfence();
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_kernel(CoopArgs a) {
+  __shared__ double2 v[32 * QR_PER_LANE];    // reflector j: v[0] = 1, v[i] = row j + i
+  __shared__ double2 rc[32 * QR_PER_LANE];   // column j of R with reflector j below it
+  __shared__ double2 s_tau, s_scale;
+  __shared__ int s_b;
+  const int lane = threadIdx.x & 31;
+  const int G = gridDim.x;
+  const int l = a.l;
+  const int64_t gwarp = ((int64_t)blockIdx.x * QR_THREADS + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t)G * QR_WARPS;
+
+  // full column norms, the first posting
+  for (int64_t c = (int64_t)blockIdx.x * QR_THREADS + threadIdx.x; c < a.n; c += (int64_t)G * QR_THREADS)
+    a.perm[c] = (int32_t)c;
+  {
+    ArgMax best{-1.0, INT_MAX};
+    for (int64_t c = gwarp; c < a.n; c += nwarps) {
+      const double2* col = a.Y + c * a.ldy;
+      double sq = 0.0;
+      for (int i = lane; i < l; i += 32) sq += cabs2(__ldcg(col + i));
+      sq = warp_sum(sq);
+      best = better(best, ArgMax{sq, (int)c});
+    }
+    post_candidate(a, best, 0);
+  }
+  if (!grid_sync(a)) return;
+
+  for (int j = 0; j < a.k; ++j) {
+    const int buf = j & 1;
+    // pivot j: the best posted pair (ties to the lowest position)
+    ArgMax w{-1.0, INT_MAX};
+    int wb = -1;
+    for (int b = threadIdx.x; b < G; b += QR_THREADS) {
+      const ArgMax o{__ldcg(a.val + (int64_t)buf * G + b), __ldcg(a.idx + (int64_t)buf * G + b)};
+      const ArgMax nb = better(w, o);
+      if (nb.i != w.i) {
+        w = nb;
+        wb = b;
+      }
+    }
+    const ArgMax r = block_argmax(w);
+    if (wb >= 0 && w.i == r.i) s_b = wb;
+    // column j - 1 of R, held since the last step, into its slot
+    if (j > 0 && blockIdx.x == (j - 1) % G)
+      for (int i = threadIdx.x; i < l; i += QR_THREADS) a.Y[(int64_t)(j - 1) * a.ldy + i] = rc[i];
+    __syncthreads();
+    if (!(r.v > 0.0)) {                                  // rank(Y) = j < k (Sec. 2)
+      if (blockIdx.x == 0 && threadIdx.x == 0) *a.status = RID_ERANK;
+      return;
+    }
+    const int p = r.i;
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p != j) {
+      const int32_t t = a.perm[j];
+      a.perm[j] = a.perm[p];
+      a.perm[p] = t;
+    }
+    // reflector j from the posted copy of the pivot column (zlarfg convention)
+    const double2* pc = a.cand + ((int64_t)buf * G + s_b) * l;
+    for (int i = threadIdx.x; i < l; i += QR_THREADS) rc[i] = __ldcg(pc + i);
+    __syncthreads();
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) part += cabs2(rc[i]);
+    const double xnorm2 = block_sum(part);
+    if (threadIdx.x == 0) {
+      double2 tau, scale;
+      double beta;
+      if (zlarfg_scalars(rc[j], xnorm2, tau, scale, beta)) rc[j] = make_double2(beta, 0.0);
+      if (blockIdx.x == 0) a.tau[j] = tau;
+      s_tau = tau;
+      s_scale = scale;
+    }
+    __syncthreads();
+    const double2 scale = s_scale;
+    if (scale.x != 0.0 || scale.y != 0.0)
+      for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) rc[i] = cmul(rc[i], scale);
+    __syncthreads();
+    const int rows = l - j;
+    const int padded = (rows + 31) & ~31;
+    for (int i = threadIdx.x; i < padded; i += QR_THREADS)
+      v[i] = (i == 0) ? make_double2(1.0, 0.0) : (i < rows ? rc[j + i] : make_double2(0.0, 0.0));
+    __syncthreads();
+
+    // H_j^H on positions c > j; position p takes the column that sat at j
+    const double2 ctau = make_double2(s_tau.x, -s_tau.y);
+    const bool more = j + 1 < a.k;
+    ArgMax best{-1.0, INT_MAX};
+    for (int64_t c = j + 1 + gwarp; c < a.n; c += nwarps) {
+      const int64_t src = (c == p) ? j : c;
+      const double2* in = a.Y + src * a.ldy;
+      double2* out = a.Y + c * a.ldy;
+      if (src != c)
+        for (int i = lane; i < j; i += 32) out[i] = __ldcg(in + i);     // the rows above j move along
+      const double nu = reflect_any<RMAX>(in + j, out + j, v, ctau, rows, lane, more);
+      if (more) best = better(best, ArgMax{nu, (int)c});
+    }
+    if (more) post_candidate(a, best, (j + 1) & 1);
+    if (!grid_sync(a)) return;       // after the last step too: slot k-1 may still be read
+  }
+  // column k - 1 of R
+  if (blockIdx.x == (a.k - 1) % G)
+    for (int i = threadIdx.x; i < l; i += QR_THREADS) a.Y[(int64_t)(a.k - 1) * a.ldy + i] = rc[i];
+}
+
 }  // namespace
+
+// CTAs of the cooperative select for n columns (0: use one launch per step).
+int rid_select_coop_grid(int device, int num_sms, int64_t n, int l) {
+  int coop = 0, per_sm = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return 0;
+  }
+  const cudaError_t e = l <= 256
+      ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_coop_kernel<8>, QR_THREADS, 0)
+      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_coop_kernel<16>, QR_THREADS, 0);
+  if (e != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  int64_t g = (int64_t)per_sm * num_sms;
+  const int64_t by_work = (n + 2 * QR_WARPS - 1) / (2 * QR_WARPS);     // at least two columns a warp
+  if (g > by_work) g = by_work;
+  return (int)(g < 1 ? 1 : g);
+}
 
 cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm) {
   if (p->l > 32 * QR_PER_LANE) return cudaErrorInvalidValue;
-  SelectArgs a{Y, ldy, p->l, p->k, p->n, perm, p->qr_val, p->qr_idx, p->qr_counter, p->tau,
-               p->status};
   cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) return e;
+  if (p->sel_grid > 0) {
+    CoopArgs c{Y, ldy, p->l, p->k, p->n, perm, p->tau, p->status, p->sel_cand, p->sel_val, p->sel_idx,
+               p->sel_bar};
+    e = cudaMemsetAsync(p->sel_bar, 0, 2 * sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&c};
+    const void* fn = p->l <= 256 ? (const void*)select_coop_kernel<8> : (const void*)select_coop_kernel<16>;
+    return cudaLaunchCooperativeKernel(fn, dim3(p->sel_grid), dim3(QR_THREADS), args, 0, p->stream);
+  }
+  SelectArgs a{Y, ldy, p->l, p->k, p->n, perm, p->qr_val, p->qr_idx, p->qr_counter, p->tau,
+               p->status};
   e = cudaMemsetAsync(p->qr_counter, 0, sizeof(unsigned), p->stream);
   if (e != cudaSuccess) return e;
   select_init_kernel<<<p->qr_grid, QR_THREADS, 0, p->stream>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (int j = 0; j < p->k; ++j) {
-    select_step_kernel<<<p->qr_grid, QR_THREADS, 0, p->stream>>>(a, j);
+    if (p->l <= 256) select_step_kernel<8><<<p->qr_grid, QR_THREADS, 0, p->stream>>>(a, j);
+    else select_step_kernel<16><<<p->qr_grid, QR_THREADS, 0, p->stream>>>(a, j);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -327,7 +592,8 @@ extern "C" RID_API rid_status rid_select_noalloc(void* Y, int64_t ldy, int32_t l
   select_init_kernel<<<(unsigned)grid, QR_THREADS, 0, s>>>(a);
   if (cudaGetLastError() != cudaSuccess) return RID_ECUDA;
   for (int j = 0; j < k; ++j) {
-    select_step_kernel<<<(unsigned)grid, QR_THREADS, 0, s>>>(a, j);
+    if (l <= 256) select_step_kernel<8><<<(unsigned)grid, QR_THREADS, 0, s>>>(a, j);
+    else select_step_kernel<16><<<(unsigned)grid, QR_THREADS, 0, s>>>(a, j);
     if (cudaGetLastError() != cudaSuccess) return RID_ECUDA;
   }
   return RID_OK;

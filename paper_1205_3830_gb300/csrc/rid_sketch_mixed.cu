@@ -78,21 +78,42 @@ __global__ void mx_omega_slice_kernel(const double2* __restrict__ om, int64_t ld
   }
 }
 
-// A' columns (complex64 A read as 2m floats), split into 3 terms; zero padding to KP.
-__global__ void mx_a_slice_kernel(const float2* __restrict__ A, int64_t lda, int64_t m, int64_t n, int64_t KP,
-                                  uint16_t* __restrict__ slices) {
-  const int64_t per_col = KP / 2;
+// hi / mid / lo BF16 terms of an FP32 value: every step is exact in FP32
+// (x - hi keeps the 16 bits below hi, minus mid the last 8), so this equals
+// split3((double)x) bit for bit at FP32 speed.
+__device__ __forceinline__ void split3f(float x, uint16_t (&t)[MX_S]) {
+  const uint16_t h = bf16_rn(x);
+  const float r1 = x - __uint_as_float((uint32_t)h << 16);
+  const uint16_t m = bf16_rn(r1);
+  const float r2 = r1 - __uint_as_float((uint32_t)m << 16);
+  t[0] = h;
+  t[1] = m;
+  t[2] = bf16_rn(r2);
+}
+
+// A' columns (complex64 A read as 2m floats), split into 3 terms; zero padding
+// to KP.  A thread takes two consecutive complex entries: two 8-byte loads and
+// one 8-byte store per term.
+__global__ void __launch_bounds__(256) mx_a_slice_kernel(const float2* __restrict__ A, int64_t lda, int64_t m,
+                                                         int64_t n, int64_t KP, uint16_t* __restrict__ slices) {
+  const int64_t per_col = KP / 4;                      // pairs of complex entries per column
   const int64_t total = n * per_col;
   const int64_t slice_stride = n * KP;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / per_col, r = e - j * per_col;
-    const float2 x = r < m ? __ldg(A + j * lda + r) : make_float2(0.f, 0.f);
-    uint16_t re[MX_S], im[MX_S];
-    split3((double)x.x, re);
-    split3((double)x.y, im);
+    const int64_t j = e / per_col, r = 2 * (e - j * per_col);
+    const float2* col = A + j * lda;
+    const float2 x0 = r < m ? __ldcs(col + r) : make_float2(0.f, 0.f);
+    const float2 x1 = r + 1 < m ? __ldcs(col + r + 1) : make_float2(0.f, 0.f);
+    uint16_t re0[MX_S], im0[MX_S], re1[MX_S], im1[MX_S];
+    split3f(x0.x, re0);
+    split3f(x0.y, im0);
+    split3f(x1.x, re1);
+    split3f(x1.y, im1);
 #pragma unroll
-    for (int s = 0; s < MX_S; ++s)
-      *(uint32_t*)(slices + s * slice_stride + j * KP + 2 * r) = (uint32_t)re[s] | ((uint32_t)im[s] << 16);
+    for (int s = 0; s < MX_S; ++s) {
+      const uint2 w = make_uint2((uint32_t)re0[s] | ((uint32_t)im0[s] << 16), (uint32_t)re1[s] | ((uint32_t)im1[s] << 16));
+      *(uint2*)(slices + s * slice_stride + j * KP + 2 * r) = w;
+    }
   }
 }
 
@@ -355,7 +376,7 @@ cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A_, int64_t lda, doub
   if (p->timing) cudaEventRecord(p->ev[0], p->stream);
   cudaError_t e;
   {
-    const int64_t total = p->n * (st->KP / 2);
+    const int64_t total = p->n * (st->KP / 4);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
     mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, p->n, st->KP, st->a_slices);

@@ -64,6 +64,27 @@ def test_select_noalloc_matches_plan_select_twice(lib):
         assert np.abs(R[:k] - R_ref[:k]).max() <= 1e-12 * np.abs(R_ref[:k]).max()
 
 
+@pytest.mark.parametrize("shape", [(2048, 8192, 200, 208), (300, 64, 64, 70), (4096, 333, 1, 3),
+                                   (700, 2500, 40, 512), (513, 129, 9, 9)], ids=str)
+def test_select_noalloc_and_plan_select_agree_bit_for_bit(lib, shape):
+    """The plan runs all k steps in one cooperative launch, the allocation-free
+    entry one launch per step; both take the same arithmetic in the same order."""
+    import paper_1205_3830_gb300 as rid
+    m, n, k, l = shape
+    Yo = oracle.randomize(oracle.gaussian_test_matrix(l, m, 3), synth.lowrank_plus_noise(m, n, min(k, 60), 1e-10, seed=4))
+    with rid.Plan(m, n, k, l, seed=3) as plan:
+        Y_ref = colmajor(Yo)
+        perm_ref = plan.select(Y_ref)
+        plan.sync_status()
+    Y = colmajor(Yo)
+    st, perm, status = select_noalloc(lib, Y, l, n, k)
+    assert st == 0
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0
+    assert torch.equal(perm, perm_ref)
+    assert torch.equal(Y, Y_ref)          # R, the reflectors below it and the trailing rows
+
+
 def test_select_noalloc_reports_rank_deficiency(lib):
     m, n, k, l = 64, 40, 5, 8
     A = np.zeros((m, n), dtype=np.complex128)
