@@ -173,7 +173,59 @@ __global__ void omega_slice_kernel(const double2* __restrict__ om, int64_t ldo, 
 }
 
 // ---- A' slices (every call) -------------------------------------------------------
-// One warp per (column j, chunk c): 128 complex rows = 256 real values.
+// The same digits as digits_of, computed for the hot path with few integer
+// operations.  q' = q + B with B = sum_{s=1..6} 128 * 256^(6-s) holds the
+// balanced digits as plain bytes (byte 6-s of q' is d_s + 128 for s >= 1, and
+// q' >> 48 = d_0), so no carries are propagated.  A digit u becomes its BF16
+// value with one FFMA: the float with exponent field 150 - 8s and low bits u is
+// 2^(-8s) (2^23 + u), so sgn * that - sgn * 2^(-8s) (2^23 + bias) = sgn d 2^(-8s)
+// exactly (and +0 for a zero digit, as the integer conversion gives).
+__device__ __forceinline__ unsigned long long digit_bytes(double x, int e, float& sgn) {
+  const long long b = __double_as_longlong(x);
+  sgn = b < 0 ? -1.0f : 1.0f;
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long q = 0;
+  if (ex != 0 && e != TC_EXP_ZERO) {
+    const unsigned long long mant = (unsigned long long)(b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = (ex - 1075) + 8 * TC_S - e;
+    if (sh >= 0) {
+      q = mant << sh;
+    } else if (sh > -62) {
+      q = (mant + (1ull << (-sh - 1))) >> (-sh);
+    }
+  }
+  return q + 0x0000808080808080ull;
+}
+
+template <int S>
+__device__ __forceinline__ float digit_value(uint32_t u, float sgn) {
+  constexpr uint32_t kExp = (uint32_t)(150 - 8 * S) << 23;
+  // 2^(-8S) (2^23 + 128) for S >= 1 (the bias), 2^23 for the leading digit
+  const float c = S == 0 ? 8388608.0f : __uint_as_float(kExp | 128u);
+  return __fmaf_rn(sgn, __uint_as_float(kExp | u), __fmul_rn(-sgn, c));
+}
+
+// The TC_S packed words (re digit | im digit << 16) of one complex entry.
+__device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S]) {
+  static_assert(TC_S == 7, "digit byte layout assumes 7 digits");
+  float sr, si;
+  const unsigned long long qr = digit_bytes(x.x, e, sr), qi = digit_bytes(x.y, e, si);
+  const uint32_t rl = (uint32_t)qr, rh = (uint32_t)(qr >> 32), il = (uint32_t)qi, ih = (uint32_t)(qi >> 32);
+#define RID_DIGIT_PAIR(S, RB, IB) \
+  w[S] = __byte_perm(__float_as_uint(digit_value<S>(RB, sr)), __float_as_uint(digit_value<S>(IB, si)), 0x7632);
+  RID_DIGIT_PAIR(0, rh >> 16, ih >> 16)
+  RID_DIGIT_PAIR(1, (rh >> 8) & 0xFF, (ih >> 8) & 0xFF)
+  RID_DIGIT_PAIR(2, rh & 0xFF, ih & 0xFF)
+  RID_DIGIT_PAIR(3, rl >> 24, il >> 24)
+  RID_DIGIT_PAIR(4, (rl >> 16) & 0xFF, (il >> 16) & 0xFF)
+  RID_DIGIT_PAIR(5, (rl >> 8) & 0xFF, (il >> 8) & 0xFF)
+  RID_DIGIT_PAIR(6, rl & 0xFF, il & 0xFF)
+#undef RID_DIGIT_PAIR
+}
+
+// One warp per (column j, chunk c): 128 complex rows = 256 real values; a
+// lane takes 4 consecutive complex rows, so every slice row is written with
+// one 16-byte store per lane.
 __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict__ A, int64_t lda, int64_t m,
                                                       int64_t n, int NC, int64_t KP,
                                                       uint16_t* __restrict__ slices, int* __restrict__ a_exp,
@@ -185,25 +237,22 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict_
        t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t j = t / NC;
     const int c = (int)(t - j * NC);
+    const int64_t r0 = (int64_t)c * 128 + 4 * lane;
+    const double2* col = A + j * lda;
     double2 x[4];
     int e = TC_EXP_ZERO;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int64_t r = (int64_t)c * 128 + lane + 32 * u;
-      x[u] = r < m ? __ldg(A + j * lda + r) : make_double2(0.0, 0.0);
+      x[u] = r0 + u < m ? __ldcs(col + r0 + u) : make_double2(0.0, 0.0);
       e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
     }
     e = __reduce_max_sync(0xffffffffu, e);
+    uint32_t w[4][TC_S];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int64_t r = (int64_t)c * 128 + lane + 32 * u;
-      uint16_t re[TC_S], im[TC_S];
-      digits_of(x[u].x, e, re);
-      digits_of(x[u].y, e, im);
+    for (int u = 0; u < 4; ++u) digit_words(x[u], e, w[u]);
 #pragma unroll
-      for (int s = 0; s < TC_S; ++s)
-        *(uint32_t*)(slices + s * slice_stride + j * KP + 2 * r) = (uint32_t)re[s] | ((uint32_t)im[s] << 16);
-    }
+    for (int s = 0; s < TC_S; ++s)
+      __stcs((uint4*)(slices + s * slice_stride + j * KP + 2 * r0), make_uint4(w[0][s], w[1][s], w[2][s], w[3][s]));
     if (lane == 0) {
       a_exp[j * NC + c] = e;
       atomicMax(a_exp_max + j, e);
@@ -212,13 +261,6 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict_
 }
 
 // ---- the tensor-core product ----------------------------------------------------------
-__device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y, int z) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], [%2];"
-      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
-      : "memory");
-}
-
 struct TcArgs {
   int n, l2, l2p, NC, chunks_per_split, ntiles, tile_w;
   uint32_t stage_bytes;   // bytes landing in one stage: S A tiles of 128 rows + S Omega tiles of tile_w rows
