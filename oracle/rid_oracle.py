@@ -42,6 +42,7 @@ __all__ = [
     "uniform53_pair",
     "complex_gaussian",
     "gaussian_test_matrix",
+    "round_test_matrix",
     "probe_matrix",
     "randomize",
     "householder_reflector",
@@ -153,6 +154,29 @@ def complex_gaussian(rows, cols, seed, stream, row0=0, col0=0):
 def gaussian_test_matrix(l, m, seed):
     """The l x m complex Gaussian test matrix Omega of the randomization step."""
     return complex_gaussian(l, m, seed, STREAM_OMEGA)
+
+
+def round_test_matrix(Omega, bits):
+    """Omega with every entry rounded to `bits` bits below its row's largest entry.
+
+    Row r gets the exponent E_r with |Re w|, |Im w| < 2^E_r for all its entries
+    (E_r = the largest binary exponent e of x = f 2^e, 1/2 <= |f| < 1), and each
+    real part is rounded to the nearest multiple of 2^(E_r - bits), ties to even.
+    Any random matrix serves as the test matrix of the randomization (Sec. 2
+    uses the SRFT); a rounded one holds bits / 8 base-256 digits exactly.
+    """
+    Omega = np.array(Omega, dtype=np.complex128)
+    for r in range(Omega.shape[0]):
+        row = Omega[r]
+        parts = np.concatenate([row.real, row.imag])
+        nz = parts[parts != 0.0]
+        if nz.size == 0:
+            continue
+        E = int(np.max(np.frexp(nz)[1]))
+        re = np.ldexp(np.rint(np.ldexp(row.real, bits - E)), E - bits)
+        im = np.ldexp(np.rint(np.ldexp(row.imag, bits - E)), E - bits)
+        Omega[r] = re + 1j * im
+    return Omega
 
 
 def probe_matrix(n, r, seed):

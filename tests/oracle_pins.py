@@ -284,6 +284,29 @@ def pin_error_estimate_left(o):
         assert exact <= upper
 
 
+def pin_round_test_matrix(o):
+    """Rounded rows: multiples of 2^(E - bits) with E the row's exponent, within
+    half a step of the input, ties to even, idempotent; an entry that is already
+    on the grid is unchanged (the row maximum keeps its value at any bits >= 1
+    when it is a power of two)."""
+    Om = o.gaussian_test_matrix(6, 300, 5)
+    for bits in (8, 16, 24):
+        R = o.round_test_matrix(Om, bits)
+        for r in range(Om.shape[0]):
+            parts = np.concatenate([Om[r].real, Om[r].imag])
+            E = max(math.frexp(float(x))[1] for x in parts if x != 0.0)
+            step = 2.0 ** (E - bits)
+            for x, y in ((Om[r].real, R[r].real), (Om[r].imag, R[r].imag)):
+                assert np.all(np.abs(y - x) <= step / 2)
+                assert np.all(np.mod(y, step) == 0.0)
+        assert np.array_equal(o.round_test_matrix(R, bits), R)
+    # exact halves go to the even multiple: row maximum 0.75 (E = 0), step 2^-2
+    row = np.array([[0.75 + 0.375j, 0.625 - 0.125j, 0.5 + 0.0j]])
+    R = o.round_test_matrix(row, 2)
+    assert np.array_equal(R, np.array([[0.75 + 0.5j, 0.5 - 0.0j, 0.5 + 0.0j]]))
+    assert np.array_equal(o.round_test_matrix(np.zeros((1, 3), complex), 8), np.zeros((1, 3), complex))
+
+
 # --- the paper's SRFT ---------------------------------------------------------
 def pin_srft(o):
     """S F D A equals rows s of numpy's FFT (along columns) of D A."""
@@ -300,5 +323,5 @@ def pin_srft(o):
 ALL_PINS = [
     pin_philox_kat, pin_uniform53, pin_gaussian_distribution, pin_randomize_exact,
     pin_qr_lapack, pin_qr_pivot_rule, pin_rank_deficient, pin_factor_r, pin_exact_rank,
-    pin_spectrum_bound, pin_brute_force, pin_error_estimate, pin_error_estimate_left, pin_srft,
+    pin_spectrum_bound, pin_brute_force, pin_error_estimate, pin_error_estimate_left, pin_round_test_matrix, pin_srft,
 ]
