@@ -141,9 +141,11 @@ def max_over_ranks(x, world):
 # ---------------------------------------------------------------------------
 # CPU oracle on a bounded column slab (the cpu_baseline and --impl reference)
 # ---------------------------------------------------------------------------
-def oracle_slab_setup(cfg, A_slab_host):
+def oracle_slab_setup(cfg, A_slab_host, omega_bits=0):
     import oracle
     Omega = oracle.gaussian_test_matrix(cfg.l, cfg.m, cfg.seed)   # untimed: plan creation
+    if omega_bits:
+        Omega = oracle.round_test_matrix(Omega, omega_bits)
     probes = oracle.probe_matrix(A_slab_host.shape[1], 8, 1)
     return Omega, probes
 
@@ -181,7 +183,7 @@ def run_reference(args, cfg, world, rank):
     else:   # no GPU: the same recipe on the host at the slab's width
         small = synth.scaled_config(cfg, cfg.m, ns)
         A_slab = synth.host_matrix(small)
-    Omega, probes = oracle_slab_setup(cfg, A_slab)
+    Omega, probes = oracle_slab_setup(cfg, A_slab, args.omega_bits)
     for _ in range(args.warmup):
         oracle_slab_step(cfg, Omega, A_slab, probes)
     t0 = time.perf_counter()
@@ -209,6 +211,8 @@ def workload_config(cfg, args):
     return {"workload": f"{cfg.name}: {ctype} {kind}, m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
                         f"{cfg.a_bytes / 2**30:.0f} GiB",
             "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode, "estimator": args.estimator,
+            "omega": ("complex Gaussian (FP64)" if not args.omega_bits else
+                      f"complex Gaussian rounded to {args.omega_bits} bits below each row's maximum"),
             "l2": "inputs larger than L2 (A is %.0f GiB, L2 129 MB)" % (cfg.a_bytes / 2**30)}
 
 
@@ -233,6 +237,8 @@ def run_ours(args, cfg, world, rank, local):
     rows = args.estimator == "rows"
     if rows:
         plan.set_probes(args.nprobe, 1)       # the error's products ride along in the sketch
+    if args.omega_bits:
+        plan.round_omega(args.omega_bits)     # Omega (and the probes) rounded: bits / 8 digits
     Y = rid.colmajor_empty(l, n, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     T = rid.colmajor_empty(k, n - k, device=dev)
@@ -306,7 +312,8 @@ def run_ours(args, cfg, world, rank, local):
         # the emulation's own work: BF16 slice-pair products of the real
         # (2l x 2m) x (2m x n) problem, 2 flops per multiply-add (28 pairs for the
         # FP64-grade digits, 6 for the BF16x3 splits of the mixed mode)
-        pairs = 28 if args.mode == "fp64_emulated" else 6
+        so = (args.omega_bits + 7) // 8 if args.omega_bits else 7
+        pairs = sum(1 for s_ in range(so) for t_ in range(7) if s_ + t_ <= 6) if args.mode == "fp64_emulated" else 6
         tc_flops = pairs * 2.0 * (2 * ls) * (2 * m) * n
         achieved = tc_flops / t_prod / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
@@ -346,6 +353,8 @@ def run_ours(args, cfg, world, rank, local):
         "clocks": clocks,
     }
 
+    if args.mode == "fp64_emulated" and not args.omega_bits and args.rounded_variant:
+        line["omega_rounded_24bit"] = time_rounded_omega(args, cfg, A, stream, world, rank)
     if args.e2e_steps > 0:
         line["e2e"] = run_e2e(args, cfg, plan, A, Y, perm, T, stream, world)
     if args.mode == "bf16":
@@ -355,6 +364,50 @@ def run_ours(args, cfg, world, rank, local):
     plan.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def time_rounded_omega(args, cfg, A, stream, world, rank):
+    """The same step with the test matrix (and row probes) rounded to 24 bits
+    below each row's maximum: the emulated product then multiplies 18 digit
+    pairs instead of 28 and stays exact for that Omega.  Reported beside the
+    headline, which uses the unrounded Gaussian Omega."""
+    import torch
+    import paper_1205_3830_gb300 as rid
+    m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
+    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, dtype=A.dtype, mode="fp64_emulated", stream=stream)
+    plan.enable_timing()
+    rows = args.estimator == "rows"
+    if rows:
+        plan.set_probes(args.nprobe, 1)
+    plan.round_omega(24)
+    Y = rid.colmajor_empty(l, n, device=A.device)
+    perm = torch.empty(n, dtype=torch.int32, device=A.device)
+    T = rid.colmajor_empty(k, n - k, device=A.device)
+
+    def step():
+        plan.sketch(A, Y)
+        plan.select(Y, perm)
+        plan.solve(Y, T)
+        return plan.error_sketched(perm, T) if rows else plan.error(A, perm, T, args.nprobe, 1)
+
+    for _ in range(3):
+        step()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 3
+    e0.record(stream)
+    prod = []
+    for _ in range(reps):
+        est, upper = step()
+        prod.append(plan.sketch_times()[1])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = max_over_ranks(e0.elapsed_time(e1), world) / reps
+    plan.close()
+    return {"value": world * cfg.a_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "ms_per_step": ms, "steps": reps,
+            "product_ms": statistics.mean(prod), "digit_pairs": 18, "error_estimate": {"est": est, "upper": upper},
+            "omega": "complex Gaussian rounded to 24 bits below each row's maximum (ties to even)"}
 
 
 def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
@@ -435,7 +488,7 @@ def cpu_baseline(args, cfg, A):
     import numpy as np
     ns = args.ref_cols
     A_slab = np.asfortranarray(A[:, :ns].cpu().numpy())
-    Omega, probes = oracle_slab_setup(cfg, A_slab)
+    Omega, probes = oracle_slab_setup(cfg, A_slab, args.omega_bits)
     t0 = time.perf_counter()
     oracle_slab_step(cfg, Omega, A_slab, probes)
     dt = time.perf_counter() - t0
@@ -584,6 +637,10 @@ def main():
     ap.add_argument("--config", default="large_tall")
     ap.add_argument("--mode", default="fp64_emulated", choices=("fp64", "fp64_emulated", "bf16"))
     ap.add_argument("--nprobe", type=int, default=8)
+    ap.add_argument("--no-rounded-variant", dest="rounded_variant", action="store_false",
+                    help="skip the secondary measurement with a 24-bit rounded test matrix")
+    ap.add_argument("--omega-bits", type=int, default=0,
+                    help="round the test matrix to this many bits below each row's maximum (0: unrounded)")
     ap.add_argument("--estimator", choices=("rows", "columns"), default=None,
                     help="error estimate from row probes multiplied in the sketch (default for the FP64 modes) "
                          "or from column probes in a second pass over A (default for bf16)")

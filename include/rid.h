@@ -156,6 +156,21 @@ RID_API rid_status rid_error(rid_plan_t plan, const void* A, int64_t lda, const 
                      const void* T, int64_t ldt, int32_t nprobe, uint64_t probe_seed,
                      double out[2]);
 
+/* Round the test matrix: every entry of each row of Omega (and of the row
+ * probes, if set) is rounded to `bits` bits below the row's largest entry:
+ * with E_r the exponent of the row (|Re w|, |Im w| < 2^E_r, E_r the exponent
+ * of x = f 2^E_r, 1/2 <= |f| < 1), each real part becomes the nearest
+ * multiple of 2^(E_r - bits), ties to even (a value that would reach
+ * +-2^E_r takes the multiple below it).  Omega stays a seeded random test
+ * matrix (Sec. 2 only needs one; the paper's own is the SRFT); rounded, it
+ * holds bits / 8 base-256 digits, and RID_FP64_EMULATED multiplies only
+ * those: 28 digit-pair products become 18 at bits = 24 and 13 at 16, with the
+ * product still exact for that Omega.  bits in {8, 16, ..., 48}
+ * (RID_EINVAL otherwise).  Later rid_plan_use_srft / rid_plan_set_probes
+ * round the rows they draw the same way; rid_plan_set_omega takes the
+ * caller's Omega unrounded and ends the rounding.  Synchronizes the stream. */
+RID_API rid_status rid_plan_round_omega(rid_plan_t plan, int32_t bits);
+
 /* Row probes for the error of the ID (Sec. 3.3), computed in the sketch's
  * own pass over A.  Appends nprobe rows g_q to Omega: an nprobe x m complex
  * Gaussian G, entry (q, i) from the Philox block at counter (i lo, i hi, q, 6)

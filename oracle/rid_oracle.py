@@ -161,9 +161,11 @@ def round_test_matrix(Omega, bits):
 
     Row r gets the exponent E_r with |Re w|, |Im w| < 2^E_r for all its entries
     (E_r = the largest binary exponent e of x = f 2^e, 1/2 <= |f| < 1), and each
-    real part is rounded to the nearest multiple of 2^(E_r - bits), ties to even.
-    Any random matrix serves as the test matrix of the randomization (Sec. 2
-    uses the SRFT); a rounded one holds bits / 8 base-256 digits exactly.
+    real part is rounded to the nearest multiple of 2^(E_r - bits), ties to even;
+    a value that would reach +-2^E_r takes the multiple just below it, so the
+    row keeps its exponent.  Any random matrix serves as the test matrix of the
+    randomization (Sec. 2 uses the SRFT); a rounded one holds bits / 8 base-256
+    digits exactly.
     """
     Omega = np.array(Omega, dtype=np.complex128)
     for r in range(Omega.shape[0]):
@@ -173,8 +175,9 @@ def round_test_matrix(Omega, bits):
         if nz.size == 0:
             continue
         E = int(np.max(np.frexp(nz)[1]))
-        re = np.ldexp(np.rint(np.ldexp(row.real, bits - E)), E - bits)
-        im = np.ldexp(np.rint(np.ldexp(row.imag, bits - E)), E - bits)
+        top = 2.0 ** bits - 1.0
+        re = np.ldexp(np.clip(np.rint(np.ldexp(row.real, bits - E)), -top, top), E - bits)
+        im = np.ldexp(np.clip(np.rint(np.ldexp(row.imag, bits - E)), -top, top), E - bits)
         Omega[r] = re + 1j * im
     return Omega
 

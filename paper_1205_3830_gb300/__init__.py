@@ -73,6 +73,7 @@ class Plan:
         self.dtype = dtype
         self.mode = mode
         self.nrow = 0
+        self.omega_bits = 0
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
                                    torch.device(device).index or 0)
         if stream is None:
@@ -167,6 +168,13 @@ class Plan:
                                   max(_ld(T), self.k), int(nprobe), int(probe_seed) & (2 ** 64 - 1),
                                   out), "rid_error")
         return float(out[0]), float(out[1])
+
+    def round_omega(self, bits=24):
+        """Round every row of Omega (and of the row probes) to `bits` bits below
+        the row's largest entry; the emulated sketch then multiplies bits / 8
+        digits of it (synchronizes)."""
+        check(self._lib.rid_plan_round_omega(self._h, int(bits)), "rid_plan_round_omega")
+        self.omega_bits = int(bits)
 
     def set_probes(self, nprobe=8, probe_seed=1):
         """Row probes G (nprobe x m) multiplied by every later sketch in its pass

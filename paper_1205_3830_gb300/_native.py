@@ -31,6 +31,7 @@ SIGNATURES = {
     "rid_solve": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),
     "rid_error": (ctypes.c_int, [_c_plan, _p, _i64, _p, _p, _i64, _i32, _u64,
                                  ctypes.POINTER(ctypes.c_double)]),
+    "rid_plan_round_omega": (ctypes.c_int, [_c_plan, _i32]),
     "rid_plan_set_probes": (ctypes.c_int, [_c_plan, _i32, _u64]),
     "rid_error_sketched": (ctypes.c_int, [_c_plan, _p, _p, _i64, ctypes.POINTER(ctypes.c_double)]),
     "rid_sync_status": (ctypes.c_int, [_c_plan]),

@@ -282,6 +282,7 @@ rid_status rid_plan_set_omega(rid_plan_t p, const void* omega, int64_t ldo) {
   if (!g.ok) return RID_ECUDA;
   cudaError_t e = cudaMemcpy2DAsync(p->omega, p->ldo * sizeof(double2), omega, ldo * sizeof(double2),
                                     p->m * sizeof(double2), p->l, cudaMemcpyDeviceToDevice, p->stream);
+  p->omega_bits = 0;                // a caller's Omega is taken as it is
   if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
     // the tensor-core paths keep Omega in split form: rebuild it
     rid_tc_plan_free(p);
@@ -296,12 +297,30 @@ rid_status rid_plan_use_srft(rid_plan_t p, uint64_t srft_seed) {
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
   cudaError_t e = rid_launch_srft(p->omega, p->l, p->m, p->ldo, srft_seed, p->stream);
+  if (e == cudaSuccess && p->omega_bits > 0)
+    e = rid_launch_round_rows(p->omega, p->l, p->m, p->ldo, p->omega_bits, p->stream);
   if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
     rid_tc_plan_free(p);          // the tensor-core paths keep Omega in split form
     const rid_status s = rid_tc_plan_init(p);
     if (s != RID_OK) return s;
   }
   return from_cuda(e);
+}
+
+rid_status rid_plan_round_omega(rid_plan_t p, int32_t bits) {
+  if (!p || bits < 8 || bits > 48 || bits % 8 != 0) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e = rid_launch_round_rows(p->omega, p->ls, p->m, p->ldo, bits, p->stream);
+  if (e == cudaSuccess && p->nrow > 0) e = rid_launch_row_probe_norms(p);   // ||g_q||^2 of the rounded probes
+  if (e != cudaSuccess) return from_cuda(e);
+  p->omega_bits = (p->omega_bits > 0 && p->omega_bits < bits) ? p->omega_bits : bits;
+  if (p->mode != RID_FP64_NATIVE) {
+    rid_tc_plan_free(p);          // the tensor-core paths keep Omega in split form
+    const rid_status s = rid_tc_plan_init(p);
+    if (s != RID_OK) return s;
+  }
+  return from_cuda(cudaStreamSynchronize(p->stream));
 }
 
 rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
@@ -335,6 +354,9 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
     if (e == cudaSuccess)
       e = rid_launch_gaussian((double2*)base + (int64_t)p->l * p->ldo, nprobe, p->m, p->ldo, 1, probe_seed,
                               RID_STREAM_LPROBES, p->stream);
+    if (e == cudaSuccess && p->omega_bits > 0)
+      e = rid_launch_round_rows((double2*)base + (int64_t)p->l * p->ldo, nprobe, p->m, p->ldo, p->omega_bits,
+                                p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
       cudaFree(base);

@@ -23,6 +23,7 @@ struct rid_plan_s {
                            // the test matrix, then the row probes G (rows l..ls-1)
   int64_t ldo;
   int32_t ls;              // rows the sketch computes: l + nrow
+  int32_t omega_bits;      // 0, or the bits every row of Omega is rounded to (rid_plan_round_omega)
   int* status;             // device status word (RID_OK / RID_ERANK)
 
   // sketch (native FP64): split-K partial sums, split_k x ls x n (ld = ls)
@@ -90,6 +91,9 @@ struct rid_plan_s {
 cudaError_t rid_launch_gaussian(double2* out, int64_t rows, int64_t cols, int64_t row_stride,
                                 int64_t col_stride, uint64_t seed, uint32_t stream_id,
                                 cudaStream_t stream);
+
+// Rows of Omega rounded to `bits` bits below each row's largest entry (ties to even).
+cudaError_t rid_launch_round_rows(double2* om, int64_t rows, int64_t m, int64_t ldo, int bits, cudaStream_t stream);
 
 // Omega = rows s_1..s_l of F D (the paper's subsampled randomized Fourier transform).
 cudaError_t rid_launch_srft(double2* out, int64_t l, int64_t m, int64_t ldo, uint64_t seed, cudaStream_t stream);

@@ -1,5 +1,7 @@
 // Seeded Gaussian matrices on the device: the test matrix Omega of the
 // randomization step (Sec. 2) and the probes of the error estimate.
+#include <climits>
+
 #include "rid_internal.cuh"
 
 namespace {
@@ -73,5 +75,53 @@ cudaError_t rid_launch_srft(double2* out, int64_t l, int64_t m, int64_t ldo, uin
   int64_t blocks = (total + 255) / 256;
   if (blocks > 152 * 64) blocks = 152 * 64;
   srft_kernel<<<(unsigned)blocks, 256, 0, stream>>>(out, l, m, ldo, seed);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Rounded test matrix: every entry of a row rounded to `bits` bits below the
+// row's largest entry.  Row r gets E_r with |Re w|, |Im w| < 2^E_r (E = the
+// exponent of x = f 2^E, 1/2 <= |f| < 1; zeros ignored), and each real part
+// becomes the nearest multiple of 2^(E_r - bits), ties to even, except that a
+// value which would reach +-2^E_r takes the multiple below (the row keeps
+// E_r).  The rounded row then holds ceil(bits / 8) base-256 digits exactly.
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ int frexp_exp(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  return ex == 0 ? INT_MIN : ex - 1022;      // subnormals and zero carry no exponent here
+}
+
+__global__ void __launch_bounds__(256) round_rows_kernel(double2* __restrict__ om, int64_t ldo, int64_t m,
+                                                         int bits) {
+  __shared__ int red[8];
+  double2* row = om + (int64_t)blockIdx.x * ldo;
+  int e = INT_MIN;
+  for (int64_t j = threadIdx.x; j < m; j += 256) {
+    const double2 w = row[j];
+    e = max(e, max(frexp_exp(w.x), frexp_exp(w.y)));
+  }
+  e = __reduce_max_sync(0xffffffffu, e);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = e;
+  __syncthreads();
+  int E = red[0];
+  for (int w = 1; w < 8; ++w) E = max(E, red[w]);
+  if (E == INT_MIN) return;                   // an all-zero row stays zero
+  // a value that would round up to +-2^E takes the multiple below: the row keeps E
+  const double top = scalbn(1.0, bits) - 1.0;
+  for (int64_t j = threadIdx.x; j < m; j += 256) {
+    const double2 w = row[j];
+    row[j] = make_double2(scalbn(fmin(fmax(rint(scalbn(w.x, bits - E)), -top), top), E - bits),
+                          scalbn(fmin(fmax(rint(scalbn(w.y, bits - E)), -top), top), E - bits));
+  }
+}
+
+}  // namespace
+
+cudaError_t rid_launch_round_rows(double2* om, int64_t rows, int64_t m, int64_t ldo, int bits, cudaStream_t stream) {
+  if (rows <= 0) return cudaSuccess;
+  round_rows_kernel<<<(unsigned)rows, 256, 0, stream>>>(om, ldo, m, bits);
   return cudaGetLastError();
 }

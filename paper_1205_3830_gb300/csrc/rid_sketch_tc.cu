@@ -48,10 +48,21 @@ namespace {
 constexpr int TC_S = 7;                 // digits per value: 56 bits
 constexpr int TC_G = 4;                 // accumulator groups
 constexpr int TC_KC = 256;              // chunk of the reduction with exact FP32 sums
-constexpr int TC_KS = 32;               // K per pipeline stage: 64-byte tile rows, 2 MMAs per slice pair
-constexpr int TC_STAGES = TC_KS == 16 ? 4 : 2;
-constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // 128 rows x (2 TC_KS) bytes
-constexpr int TC_STAGE_BYTES = 2 * TC_S * TC_TILE_BYTES;
+#ifndef RID_TC_KS
+#define RID_TC_KS 32
+#endif
+constexpr int TC_KS = RID_TC_KS;        // K per pipeline stage (32: 64-byte tile rows, 2 MMAs per slice pair)
+constexpr int TC_MAX_STAGES = 6;        // stages in flight: as many as fit in shared memory, at most this
+constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // an A tile: 128 rows x (2 TC_KS) bytes
+constexpr int TC_SMEM_LIMIT = 232448;   // dynamic + static shared memory of one CTA
+#ifndef RID_TC_PREFETCH
+#define RID_TC_PREFETCH 0
+#endif
+constexpr int TC_PREFETCH = RID_TC_PREFETCH;   // stages ahead whose A tiles are prefetched into L2
+#ifndef RID_TC_OPAD
+#define RID_TC_OPAD 1024
+#endif
+constexpr int TC_OPAD = RID_TC_OPAD;           // Omega tiles start at multiples of this in a stage
 constexpr int TC_THREADS = 512;         // warps 0-11 flush, 12 TMA, 13 MMA + TMEM, 14-15 idle
 constexpr int TC_FLUSH_WARPS = 12;
 constexpr int TC_LAUNCH_REGS = 128;    // 65536 / 512: the pool the setmaxnreg split assumes
@@ -60,6 +71,10 @@ constexpr long long TC_WAIT_BUDGET = 4000000000ll;   // clock cycles (~2 s)
 
 struct TcState {
   int S;
+  int nstages;            // pipeline stages that fit in shared memory
+  uint32_t stage_smem, o_off, o_tile_smem;
+  int dyn_smem;           // dynamic shared memory of the product kernel
+  int so;                 // Omega digits used: S, or bits / 8 for a rounded Omega
   int64_t KP;             // padded reduction length (multiple of TC_KC)
   int NC;                 // chunks
   int l2;                 // 2l rows of Omega'
@@ -263,7 +278,12 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict_
 // ---- the tensor-core product ----------------------------------------------------------
 struct TcArgs {
   int n, l2, l2p, NC, chunks_per_split, ntiles, tile_w;
-  uint32_t stage_bytes;   // bytes landing in one stage: S A tiles of 128 rows + S Omega tiles of tile_w rows
+  uint32_t stage_bytes;   // bytes landing in one stage: S A tiles of 128 rows + so Omega tiles of tile_w rows
+  int so;                 // Omega digits that can be non-zero (S, or fewer for a rounded Omega)
+  int nstages;            // pipeline stages
+  uint32_t stage_smem;    // shared memory of one stage (1024-byte multiple)
+  uint32_t o_off;         // offset of the Omega tiles in a stage
+  uint32_t o_tile_smem;   // shared memory of one Omega tile (1024-byte multiple)
   int cx, cy;             // cluster: cx N-tiles (share A tiles) x cy column blocks (share Omega tiles)
   const int* a_exp;
   const int* a_exp_max;
@@ -276,11 +296,46 @@ __device__ __forceinline__ int group_of(int d) { return d >= 3 ? 3 : d; }
 // Descriptor of a 128-row tile of TC_KS bf16 per row (swizzle matching the tensor map).
 __device__ __forceinline__ uint64_t tile_desc(const void* p) { return TC_KS == 16 ? desc_sw32(p) : desc_sw64(p); }
 
+// One stage's products: the slice pairs (s, t) with s < SO (the Omega digits
+// that can be non-zero), t < S and s + t <= S - 1, diagonal by diagonal from
+// the smallest (group 3 holds d >= 3), each group waiting for its flush before
+// its first product of a chunk.  Descriptor start addresses are in 16-byte
+// units (low 14 bits): a tile offset within shared memory adds without carry.
+template <int SO>
+__device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t db0, uint64_t o_step, uint32_t idesc,
+                                          int b, int cl, int stages_per_chunk, uint64_t* acc_empty,
+                                          uint64_t* acc_full) {
+  constexpr uint64_t a_step = TC_TILE_BYTES >> 4;
+#pragma unroll
+  for (int d = TC_S - 1; d >= 0; --d) {
+    const int g = group_of(d);
+    const bool group_start = (d == TC_S - 1) || (d < 3);   // first diagonal of its group
+    if (b == 0 && group_start && cl > 0) {
+      if (!mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)) return false;
+      tc_fence_after();
+    }
+#pragma unroll
+    for (int s = 0; s <= d; ++s) {
+      const int t = d - s;
+      if (s >= SO || t >= TC_S) continue;
+      const uint64_t da = da0 + a_step * t, db = db0 + o_step * s;
+#pragma unroll
+      for (int kk = 0; kk < TC_KS / 16; ++kk) {   // K16 steps are 32 bytes apart in a row
+        const uint32_t acc = (b == 0 && group_start && s == 0 && kk == 0) ? 0u : 1u;
+        mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+      }
+    }
+    const bool group_end = (d <= 3);     // last diagonal of its group in this stage
+    if (b == stages_per_chunk - 1 && group_end) mma_commit(&acc_full[g]);
+  }
+  return true;
+}
+
 __global__ void __launch_bounds__(TC_THREADS, 1)
 sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_om, TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[TC_STAGES], empty_bar[TC_STAGES];
+  __shared__ uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES];
   __shared__ uint64_t acc_full[TC_G], acc_empty[TC_G], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
@@ -306,7 +361,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 
   if (warp == 13) tmem_alloc(&tmem_slot, 512);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < TC_STAGES; ++i) {
+    for (int i = 0; i < a.nstages; ++i) {
       mbar_init(&full_bar[i], 1);
       mbar_init(&empty_bar[i], a.cx * a.cy);   // every CTA of the cluster releases the slot
     }
@@ -324,8 +379,9 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
-  auto a_tile = [&](int slot, int s) { return smem + slot * TC_STAGE_BYTES + s * TC_TILE_BYTES; };
-  auto o_tile = [&](int slot, int s) { return smem + slot * TC_STAGE_BYTES + (TC_S + s) * TC_TILE_BYTES; };
+  auto a_tile = [&](int slot, int s) { return smem + slot * a.stage_smem + s * TC_TILE_BYTES; };
+  auto o_tile = [&](int slot, int s) { return smem + slot * a.stage_smem + a.o_off + s * a.o_tile_smem; };
+  const int NS = a.nstages;
   auto fail = [&](int code) {
     s_abort = 1;
     atomicCAS(a.err, 0, code);
@@ -340,69 +396,72 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
       prefetch_tensormap(&map_a);
       prefetch_tensormap(&map_om);
       const int iters = nchunks * (TC_KC / TC_KS);
-      int it = 0;
+      int it = 0, slot = 0, round = 0;
       for (; it < iters && !s_abort; ++it) {
-        const int slot = it % TC_STAGES, round = it / TC_STAGES;
         if (round > 0 && !mbar_wait(&empty_bar[slot], (round - 1) & 1, TC_WAIT_BUDGET)) {
           fail(11);
           break;
         }
         const int c = c_begin + it / (TC_KC / TC_KS);
         const int x = c * TC_KC + (it % (TC_KC / TC_KS)) * TC_KS;
+        if (TC_PREFETCH > 0 && it + TC_PREFETCH < iters) {
+          const int ip = it + TC_PREFETCH;
+          const int xp = (c_begin + ip / (TC_KC / TC_KS)) * TC_KC + (ip % (TC_KC / TC_KS)) * TC_KS;
+          for (int s = rx; s < TC_S; s += a.cx) tma_prefetch_3d(&map_a, xp, jb * 128, s);
+        }
         // the stage's 2S tiles arrive here whoever issued them
         mbar_arrive_expect_tx(&full_bar[slot], a.stage_bytes);
         for (int s = rx; s < TC_S; s += a.cx)
           tma_load_3d_multicast(&map_a, &full_bar[slot], a_tile(slot, s), x, jb * 128, s, row_mask);
-        for (int s = ry; s < TC_S; s += a.cy)
+        for (int s = ry; s < a.so; s += a.cy)
           tma_load_3d_multicast(&map_om, &full_bar[slot], o_tile(slot, s), x, row0, s, col_mask);
+        if (++slot == NS) {
+          slot = 0;
+          ++round;
+        }
       }
       // tail: before the CTA may exit, every slot must have been released by
       // every CTA of the cluster (their commits arrive here), or, after an
       // error, every load issued into this CTA must have landed
-      for (int k = max(0, it - TC_STAGES); k < it; ++k) {
-        const bool ok = s_abort ? mbar_wait(&full_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET)
-                                : mbar_wait(&empty_bar[k % TC_STAGES], (k / TC_STAGES) & 1, TC_WAIT_BUDGET);
+      for (int k = max(0, it - NS); k < it; ++k) {
+        const bool ok = s_abort ? mbar_wait(&full_bar[k % NS], (k / NS) & 1, TC_WAIT_BUDGET)
+                                : mbar_wait(&empty_bar[k % NS], (k / NS) & 1, TC_WAIT_BUDGET);
         if (!ok) fail(12);
       }
     } else if (warp == 13 && lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t idesc = idesc_bf16_f32(128, n_mma);
       const int stages_per_chunk = TC_KC / TC_KS;
+      // descriptor start addresses are in 16-byte units (low 14 bits): a tile
+      // offset within the CTA's shared memory adds without carry
+      const uint64_t o_step = a.o_tile_smem >> 4;
+      int slot = 0, round = 0;
       for (int cl = 0; cl < nchunks && !s_abort; ++cl) {
         for (int b = 0; b < stages_per_chunk && !s_abort; ++b) {
-          const int it = cl * stages_per_chunk + b;
-          const int slot = it % TC_STAGES, round = it / TC_STAGES;
           if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET)) {
             fail(21);
             break;
           }
           tc_fence_after();
-#pragma unroll
-          for (int d = TC_S - 1; d >= 0; --d) {
-            const int g = group_of(d);
-            const bool group_start = (d == TC_S - 1) || (d < 3);   // first diagonal of its group
-            if (b == 0 && group_start && cl > 0) {
-              if (!mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)) {
-                fail(22);
-                break;
-              }
-              tc_fence_after();
-            }
-#pragma unroll
-            for (int s = 0; s <= d; ++s) {
-              const int t = d - s;
-              if (s >= TC_S || t >= TC_S) continue;
-              const uint64_t da = tile_desc(a_tile(slot, t)), db = tile_desc(o_tile(slot, s));
-#pragma unroll
-              for (int kk = 0; kk < TC_KS / 16; ++kk) {   // K16 steps are 32 bytes apart in a row
-                const uint32_t acc = (b == 0 && group_start && s == 0 && kk == 0) ? 0u : 1u;
-                mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
-              }
-            }
-            const bool group_end = (d <= 3);     // last diagonal of its group in this stage
-            if (b == stages_per_chunk - 1 && group_end) mma_commit(&acc_full[g]);
+          const uint64_t da0 = tile_desc(a_tile(slot, 0)), db0 = tile_desc(o_tile(slot, 0));
+          bool ok = true;
+          switch (a.so) {      // the Omega digit count picks a fully unrolled issue sequence
+#define RID_MMA_STAGE(SO) \
+            case SO: ok = mma_stage<SO>(tmem, da0, db0, o_step, idesc, b, cl, stages_per_chunk, acc_empty, acc_full); break;
+            RID_MMA_STAGE(1) RID_MMA_STAGE(2) RID_MMA_STAGE(3) RID_MMA_STAGE(4) RID_MMA_STAGE(5) RID_MMA_STAGE(6)
+            RID_MMA_STAGE(7)
+#undef RID_MMA_STAGE
+            default: ok = false;
+          }
+          if (!ok) {
+            fail(22);
+            break;
           }
           mma_commit_multicast(&empty_bar[slot], all_mask);
+          if (++slot == NS) {
+            slot = 0;
+            ++round;
+          }
         }
       }
       mma_commit(&mma_done);
@@ -564,6 +623,9 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   TcState* st = (TcState*)calloc(1, sizeof(TcState));
   if (!st) return RID_ENOMEM;
   st->S = TC_S;
+  // a rounded Omega holds omega_bits / 8 digits relative to its row exponent,
+  // the same exponent omega_exp_kernel takes, so the others are exactly zero
+  st->so = p->omega_bits > 0 ? (p->omega_bits + 7) / 8 : TC_S;
   st->NC = (int)((2 * p->m + TC_KC - 1) / TC_KC);
   st->KP = (int64_t)st->NC * TC_KC;
   st->l2 = 2 * p->ls;         // the test matrix and the row probes
@@ -575,6 +637,18 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     free(st);
     return RID_EUNSUPPORTED;
   }
+  // Stage layout: S A tiles, then so Omega tiles of tile_w rows, each a
+  // multiple of 1024 bytes; as many stages as shared memory holds.
+  st->o_tile_smem = (uint32_t)((st->tile_w * TC_KS * 2 + TC_OPAD - 1) / TC_OPAD * TC_OPAD);
+  st->o_off = (uint32_t)(TC_S * TC_TILE_BYTES);
+  st->stage_smem = st->o_off + (uint32_t)st->so * st->o_tile_smem;
+  st->nstages = (int)((TC_SMEM_LIMIT - 2048 - 1024) / st->stage_smem);
+  if (st->nstages > TC_MAX_STAGES) st->nstages = TC_MAX_STAGES;
+  if (st->nstages < 2) {
+    free(st);
+    return RID_EUNSUPPORTED;
+  }
+  st->dyn_smem = (int)(st->nstages * st->stage_smem + 1024);
   // Clusters span the N-tiles of one column block (they share its A tiles).
   // Sharing Omega tiles across column blocks too (cy > 1) measured slower:
   // larger clusters pack GPCs less densely and run in lockstep.
@@ -587,7 +661,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3(st->cx, st->nblocks_p, 1);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = TC_STAGES * TC_STAGE_BYTES + 1024;
+    cfg.dynamicSmemBytes = st->dyn_smem;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = st->cx;
     attr[0].val.clusterDim.y = st->cy;
@@ -595,7 +669,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_STAGES * TC_STAGE_BYTES + 1024);
+    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->dyn_smem);
     if (cudaOccupancyMaxActiveClusters(&clusters, sketch_tc_kernel, &cfg) != cudaSuccess || clusters < 1) {
       cudaGetLastError();
       clusters = p->num_sms / (st->cx * st->cy);
@@ -655,7 +729,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   }
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             TC_STAGES * TC_STAGE_BYTES + 1024);
+                             st->dyn_smem);
   if (e == cudaSuccess) {
     // setmaxnreg moves registers between warpgroups inside the launch
     // allocation; it is only safe if the kernel launches with exactly the
@@ -702,14 +776,15 @@ cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda,
   }
   if (p->timing) cudaEventRecord(p->ev[1], p->stream);
   TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
-              (uint32_t)(TC_S * TC_TILE_BYTES + TC_S * st->tile_w * TC_KS * 2), st->cx, st->cy,
+              (uint32_t)(TC_S * TC_TILE_BYTES + st->so * st->tile_w * TC_KS * 2), st->so, st->nstages,
+              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, st->cy,
               st->a_exp, st->a_exp_max, st->partial, st->err};
   {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = dim3((unsigned)st->ntiles, (unsigned)st->nblocks_p, (unsigned)st->ksplit);
     cfg.blockDim = dim3(TC_THREADS);
-    cfg.dynamicSmemBytes = TC_STAGES * TC_STAGE_BYTES + 1024;
+    cfg.dynamicSmemBytes = st->dyn_smem;
     cfg.stream = p->stream;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = st->cx;

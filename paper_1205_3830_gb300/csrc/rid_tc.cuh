@@ -168,6 +168,14 @@ __device__ __forceinline__ void cluster_sync() {
 }
 // 3D tile load delivered to the same shared-memory offset (and the same
 // barrier offset) in every CTA of `cta_mask`.
+// Bring a 3D tile of the tensor into L2 ahead of its load (no shared memory,
+// no barrier; coordinates follow the same rules as the load).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(x),
+               "r"(y), "r"(z)
+               : "memory");
+}
+
 __device__ __forceinline__ void tma_load_3d_multicast(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
                                                       int z, uint16_t cta_mask) {
   asm volatile(

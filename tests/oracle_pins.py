@@ -305,6 +305,9 @@ def pin_round_test_matrix(o):
     R = o.round_test_matrix(row, 2)
     assert np.array_equal(R, np.array([[0.75 + 0.5j, 0.5 - 0.0j, 0.5 + 0.0j]]))
     assert np.array_equal(o.round_test_matrix(np.zeros((1, 3), complex), 8), np.zeros((1, 3), complex))
+    # a value that would round up to 2^E keeps the exponent: 1 - 2^-30 (E = 0) -> 255/256 at 8 bits
+    row = np.array([[1.0 - 2.0 ** -30 - 1j * (1.0 - 2.0 ** -30), 0.25 + 0.0j]])
+    assert np.array_equal(o.round_test_matrix(row, 8), np.array([[255 / 256 - 255j / 256, 0.25 + 0.0j]]))
 
 
 # --- the paper's SRFT ---------------------------------------------------------

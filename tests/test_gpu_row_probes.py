@@ -20,7 +20,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U64, dot_bound, to_dev_colmajor, to_host
+from gpu_util import row_probe_tolerances, to_dev_colmajor, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -63,29 +63,6 @@ def run_with_probes(rid, A, k, l, seed, mode, nprobe, probe_seed, perm=None, T=N
         return est, up, to_host(perm_d), to_host(T_d)
 
 
-def tolerances(A, perm, T, G, mode):
-    """(tol_est, tol_upper): the bound of the module docstring."""
-    m, n = A.shape
-    k = T.shape[0]
-    J, Jc = perm[:k], perm[k:]
-    gk = 2 * k * U64 / (1 - 2 * k * U64)
-    gm = 2 * m * U64 / (1 - 2 * m * U64)
-    X = G @ A
-    dX = dot_bound(G, A)
-    if mode == "fp64_emulated":
-        dX = dX + 2.0 ** -46 * (2 * m) * np.outer(np.abs(G).max(axis=1), np.abs(A).max(axis=0))
-    P = oracle.interpolation_matrix(perm, T, n)
-    absT = np.abs(T)
-    dZ = dX[:, Jc] + dX[:, J] @ absT + 4 * gk * (np.abs(X[:, J]) @ absT)
-    dZ = dZ + 4 * (gm + gk) * (np.abs(G) @ (np.abs(A) + np.abs(A[:, J]) @ np.abs(P)))[:, Jc]
-    B = np.linalg.norm(dZ, axis=1)
-    gn = np.linalg.norm(G, axis=1)
-    EF = np.linalg.norm(A - A[:, J] @ P)
-    tol_est = np.max(B / gn) + 1e-13 * EF
-    tol_up = 10 * math.sqrt(2 / math.pi) * (np.max(B) + 1e-13 * EF * np.max(gn))
-    return tol_est, tol_up
-
-
 @pytest.mark.parametrize("mode", MODES)
 @pytest.mark.parametrize("nprobe", [1, 8, 16])
 @pytest.mark.parametrize("shape", SHAPES, ids=str)
@@ -97,7 +74,7 @@ def test_row_probe_estimate_matches_oracle(rid, shape, nprobe, mode):
     est, up, _, _ = run_with_probes(rid, A, k, l, 9, mode, nprobe, 41, perm, T)
     G = oracle.left_probe_matrix(nprobe, m, 41)
     est_o, up_o, _ = oracle.error_estimate_left(A, perm, T, G)
-    tol_est, tol_up = tolerances(A, perm, T, G, mode)
+    tol_est, tol_up = row_probe_tolerances(A, perm, T, G, mode)
     assert abs(est - est_o) <= tol_est + 1e-14 * est_o
     assert abs(up - up_o) <= tol_up + 1e-14 * up_o
     if n > k:
@@ -149,7 +126,7 @@ def test_row_probes_with_srft(rid):
     perm_h, T_h = to_host(perm), to_host(T)
     G = oracle.left_probe_matrix(6, m, 8)
     est_o, up_o, _ = oracle.error_estimate_left(A, perm_h, T_h, G)
-    tol_est, tol_up = tolerances(A, perm_h, T_h, G, "fp64_emulated")
+    tol_est, tol_up = row_probe_tolerances(A, perm_h, T_h, G, "fp64_emulated")
     assert abs(est - est_o) <= tol_est + 1e-14 * est_o
     assert abs(up - up_o) <= tol_up + 1e-14 * up_o
 

@@ -44,8 +44,10 @@ MUTATIONS = [
      "g_norm = np.sqrt(np.sum(G.real ** 2, axis=1))", [pins.pin_error_estimate_left]),
     ("left_probe_P_not_applied", "E = A - A[:, np.asarray(perm)[:k]] @ P", "E = A - A[:, np.asarray(perm)[:k]] @ P.conj()",
      [pins.pin_error_estimate_left]),
-    ("round_ties_up", "re = np.ldexp(np.rint(np.ldexp(row.real, bits - E)), E - bits)",
-     "re = np.ldexp(np.floor(np.ldexp(row.real, bits - E) + 0.5), E - bits)", [pins.pin_round_test_matrix]),
+    ("round_ties_up", "re = np.ldexp(np.clip(np.rint(np.ldexp(row.real, bits - E)), -top, top), E - bits)",
+     "re = np.ldexp(np.clip(np.floor(np.ldexp(row.real, bits - E) + 0.5), -top, top), E - bits)",
+     [pins.pin_round_test_matrix]),
+    ("round_no_clamp", "top = 2.0 ** bits - 1.0", "top = 2.0 ** bits", [pins.pin_round_test_matrix]),
     ("round_coarse_exponent", "E = int(np.max(np.frexp(nz)[1]))", "E = int(np.max(np.frexp(nz)[1])) + 1",
      [pins.pin_round_test_matrix]),
     ("srft_phase_sign", "DA = np.exp(2j * np.pi * phi)[:, None] * A", "DA = np.exp(-2j * np.pi * phi)[:, None] * A",
