@@ -4,6 +4,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string.h>
 
 #include "rid_internal.cuh"
@@ -39,6 +40,48 @@ static int rid_tc_error_word(const rid_plan_s* p) {
   if (p->mode == RID_FP64_EMULATED) return rid_tc_error_word_fp64(p);
   if (p->mode == RID_MIXED_BF16) return rid_mx_error_word(p);
   return 0;
+}
+
+namespace {
+
+constexpr int POOL_MAX_DEVICES = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pools[POOL_MAX_DEVICES] = {};
+
+// The library's memory pool on `device`, created on first use; it keeps freed
+// memory (release threshold: unlimited) so plan after plan reuses it.
+cudaMemPool_t pool_for(int device) {
+  if (device < 0 || device >= POOL_MAX_DEVICES) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  if (!g_pools[device]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[device] = pool;
+  }
+  return g_pools[device];
+}
+
+}  // namespace
+
+cudaError_t rid_dev_alloc(void** ptr, size_t bytes, cudaStream_t stream, int device) {
+  cudaMemPool_t pool = pool_for(device);
+  if (!pool) return cudaErrorMemoryAllocation;
+  const cudaError_t e = cudaMallocFromPoolAsync(ptr, bytes, pool, stream);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
+void rid_dev_free(void* ptr, cudaStream_t stream) {
+  if (ptr) cudaFreeAsync(ptr, stream);
 }
 
 namespace {
@@ -212,8 +255,8 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
 
   const Layout L = plan_layout(p);
   char* base = nullptr;
-  e = cudaMalloc((void**)&base, L.total);
-  if (e != cudaSuccess) { free(p); cudaGetLastError(); return RID_ENOMEM; }
+  e = rid_dev_alloc((void**)&base, L.total, p->stream, p->device);
+  if (e != cudaSuccess) { free(p); return RID_ENOMEM; }
   p->ws_bytes = L.total;
   p->ws_base = base;
   p->omega = (double2*)(base + L.omega);
@@ -239,15 +282,15 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   if (e == cudaSuccess)
     e = rid_launch_gaussian(p->omega, l, m, p->ldo, 1, seed, RID_STREAM_OMEGA, p->stream);
   if (e != cudaSuccess) {
-    cudaFree(base);
+    rid_dev_free(base, p->stream);
     free(p);
     return RID_ECUDA;
   }
   if (mode != RID_FP64_NATIVE) {
     const rid_status s = rid_tc_plan_init(p);
     if (s != RID_OK) {
+      rid_dev_free(base, p->stream);
       cudaStreamSynchronize(p->stream);
-      cudaFree(base);
       free(p);
       return s;
     }
@@ -263,8 +306,8 @@ rid_status rid_plan_destroy(rid_plan_t p) {
   if (p->timing)
     for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
   rid_tc_plan_free(p);
-  if (p->probe_base) cudaFree(p->probe_base);
-  cudaFree(p->ws_base);
+  rid_dev_free(p->probe_base, p->stream);
+  rid_dev_free(p->ws_base, p->stream);
   free(p);
   return RID_OK;
 }
@@ -344,10 +387,7 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
     o_norm = take((size_t)nprobe * sizeof(double));
     o_part = take((size_t)lp_grid * RID_MAX_PROBES * sizeof(double));
     o_sk = take(p->mode == RID_FP64_NATIVE && p->split_k > 1 ? (size_t)p->split_k * ls * p->n * sizeof(double2) : 0);
-    if (cudaMalloc((void**)&base, total) != cudaSuccess) {
-      cudaGetLastError();
-      return RID_ENOMEM;
-    }
+    if (rid_dev_alloc((void**)&base, total, p->stream, p->device) != cudaSuccess) return RID_ENOMEM;
     // the l rows of the test matrix, then G (Philox stream 6, key probe_seed)
     e = cudaMemcpyAsync(base, p->omega, (size_t)p->l * p->ldo * sizeof(double2), cudaMemcpyDeviceToDevice,
                         p->stream);
@@ -359,14 +399,14 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
                                 p->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
-      cudaFree(base);
+      rid_dev_free(base, p->stream);
       return from_cuda(e);
     }
   }
   // switch the plan over (the old Omega is no longer read)
   rid_tc_plan_free(p);
   if (nprobe > 0) {
-    if (p->probe_base) cudaFree(p->probe_base);
+    rid_dev_free(p->probe_base, p->stream);
     p->probe_base = base;
     p->probe_bytes = total;
     p->omega = (double2*)base;

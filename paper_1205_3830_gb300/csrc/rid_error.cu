@@ -353,8 +353,10 @@ cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p) {
 cudaError_t rid_launch_error_sketched(const rid_plan_s* p, const int32_t* perm, const double2* T, int64_t ldt) {
   const int64_t ncols = p->n - p->k;
   const size_t smem = (size_t)p->k * p->nrow * sizeof(double2);   // <= 512 * 16 * 16 = 128 KiB
+  // one fixed limit (k <= 512, r <= 16): the attribute is process-wide and
+  // plans on other host threads launch this kernel concurrently
   cudaError_t e = cudaFuncSetAttribute(row_probe_resid_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)(512 * RID_MAX_PROBES * sizeof(double2)));
   if (e != cudaSuccess) return e;
   row_probe_resid_kernel<<<p->lp_grid, LP_THREADS, smem, p->stream>>>(p->xrow, p->nrow, perm, T, ldt, p->k, ncols,
                                                                       p->lp_part);

@@ -85,6 +85,15 @@ struct rid_plan_s {
 #define RID_STREAM_LPROBES 6u
 
 // ---------------------------------------------------------------------------
+// Device memory of plans: a library-private stream-ordered pool per device
+// (allocation and release are ordered on the plan's stream; nothing
+// synchronizes the device, and freed memory stays in the pool for the next
+// plan).
+// ---------------------------------------------------------------------------
+cudaError_t rid_dev_alloc(void** ptr, size_t bytes, cudaStream_t stream, int device);
+void rid_dev_free(void* ptr, cudaStream_t stream);
+
+// ---------------------------------------------------------------------------
 // Launchers (each returns cudaGetLastError() of its launches).
 // ---------------------------------------------------------------------------
 // Gaussian matrix: entry (i, j) at out[i * row_stride + j * col_stride].

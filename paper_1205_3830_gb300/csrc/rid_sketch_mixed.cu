@@ -26,6 +26,8 @@ constexpr int MX_KS = 32;                  // K per stage (64-byte rows)
 constexpr int MX_STAGES = 3;
 constexpr int MX_THREADS = 192;            // warp 0 TMA, 1 MMA + TMEM, 2-5 epilogue
 constexpr long long MX_WAIT_BUDGET = 4000000000ll;
+constexpr int MX_SMEM_MAX = MX_STAGES * MX_S * (128 + 256) * MX_KS * 2 + 1024;   // 222208 bytes
+static_assert(MX_SMEM_MAX <= 232448 - 1024, "mixed stages exceed shared memory");
 
 struct MxState {
   int64_t KP;              // padded 2m (multiple of MX_KS)
@@ -297,8 +299,7 @@ int make_map(CUtensorMap* map, const void* base, int64_t KP, int64_t rows, int b
 void rid_mx_plan_free(rid_plan_s* p) {
   MxState* st = (MxState*)p->tc_state;
   if (!st) return;
-  cudaStreamSynchronize(p->stream);
-  cudaFree(st->om_slices);
+  rid_dev_free(st->om_slices, p->stream);   // released in stream order
   free(st);
   p->tc_state = nullptr;
   p->tc_bytes = 0;
@@ -335,8 +336,7 @@ rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run) {
     return RID_OK;
   }
   char* base = nullptr;
-  if (cudaMalloc((void**)&base, total) != cudaSuccess) {
-    cudaGetLastError();
+  if (rid_dev_alloc((void**)&base, total, p->stream, p->device) != cudaSuccess) {
     free(st);
     return RID_ENOMEM;
   }
@@ -361,7 +361,10 @@ rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run) {
     e = cudaGetLastError();
   }
   const int smem = MX_STAGES * MX_S * (128 * MX_KS * 2 + st->tile_w * MX_KS * 2) + 1024;
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(sketch_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  // the attribute is process-wide and plans of other shapes launch the kernel
+  // from other host threads: always the bound for the widest tile (256 rows)
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(sketch_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, MX_SMEM_MAX);
   if (e != cudaSuccess) {
     rid_mx_plan_free(p);
     return RID_ECUDA;

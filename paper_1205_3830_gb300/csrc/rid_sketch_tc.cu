@@ -55,6 +55,10 @@ constexpr int TC_KS = RID_TC_KS;        // K per pipeline stage (32: 64-byte til
 constexpr int TC_MAX_STAGES = 6;        // stages in flight: as many as fit in shared memory, at most this
 constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // an A tile: 128 rows x (2 TC_KS) bytes
 constexpr int TC_SMEM_LIMIT = 232448;   // dynamic + static shared memory of one CTA
+// The dynamic shared memory attribute is process-wide and plans of other
+// shapes launch the kernel from other host threads: it is always set to this
+// bound, which every plan's stages fit under.
+constexpr int TC_DYN_SMEM_MAX = TC_SMEM_LIMIT - 2048;
 #ifndef RID_TC_PREFETCH
 #define RID_TC_PREFETCH 0
 #endif
@@ -669,7 +673,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, st->dyn_smem);
+    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
     if (cudaOccupancyMaxActiveClusters(&clusters, sketch_tc_kernel, &cfg) != cudaSuccess || clusters < 1) {
       cudaGetLastError();
       clusters = p->num_sms / (st->cx * st->cy);
@@ -692,8 +696,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     return RID_OK;
   }
   char* base = nullptr;
-  if (cudaMalloc((void**)&base, total) != cudaSuccess) {
-    cudaGetLastError();
+  if (rid_dev_alloc((void**)&base, total, p->stream, p->device) != cudaSuccess) {
     free(st);
     return RID_ENOMEM;
   }
@@ -728,8 +731,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             st->dyn_smem);
+    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
   if (e == cudaSuccess) {
     // setmaxnreg moves registers between warpgroups inside the launch
     // allocation; it is only safe if the kernel launches with exactly the
@@ -751,8 +753,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
 void rid_tc_plan_free_fp64(rid_plan_s* p) {
   TcState* st = (TcState*)p->tc_state;
   if (!st) return;
-  cudaStreamSynchronize(p->stream);
-  cudaFree(st->om_slices);   // start of the single allocation
+  rid_dev_free(st->om_slices, p->stream);   // start of the single allocation, released in stream order
   free(st);
   p->tc_state = nullptr;
   p->tc_bytes = 0;

@@ -67,8 +67,10 @@ cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy,
   int nr = 0;
   const size_t smem = rid_solve_smem_bytes(p->k, &nr);
   if (smem > SOLVE_SMEM_BUDGET) return cudaErrorInvalidValue;
+  // one fixed limit for every plan: the attribute is process-wide, and plans
+  // on other host threads launch this kernel concurrently
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+                                       (int)SOLVE_SMEM_BUDGET);
   if (e != cudaSuccess) return e;
   const unsigned blocks = (unsigned)((ncols + nr - 1) / nr);
   solve_kernel<<<blocks, SOLVE_THREADS, smem, p->stream>>>(Y, ldy, p->k, p->n, nr, T, ldt);

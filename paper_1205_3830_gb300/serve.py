@@ -25,14 +25,24 @@ from . import Plan, _native, colmajor_empty, MODES, _DTYPES
 from ._native import check
 
 
-def footprint(m, n, k, l, dtype=torch.complex128, mode="fp64_emulated"):
-    """Device bytes one request of this shape holds while it runs."""
+ROW_PROBE_MODES = ("fp64", "fp64_emulated")   # modes whose sketch can carry the row probes
+
+
+def footprint(m, n, k, l, dtype=torch.complex128, mode="fp64_emulated", nprobe=8):
+    """Device bytes one request of this shape holds while it runs: the plan
+    (with its sketch widened by the row probes, where the mode takes them),
+    the probe rows and X = G A, and the outputs Y, perm, T."""
     lib = _native.load()
     b = ctypes.c_size_t()
-    check(lib.rid_plan_footprint(int(m), int(n), int(k), int(l), _DTYPES[dtype], MODES[mode], ctypes.byref(b)),
+    rows = l + (nprobe if mode in ROW_PROBE_MODES else 0)
+    check(lib.rid_plan_footprint(int(m), int(n), int(k), int(rows), _DTYPES[dtype], MODES[mode], ctypes.byref(b)),
           "rid_plan_footprint")
+    probes = 0
+    if mode in ROW_PROBE_MODES:
+        ldo = (m + 15) // 16 * 16
+        probes = 16 * rows * ldo + 16 * nprobe * n + (1 << 16)
     outputs = 16 * l * n + 4 * n + 16 * k * max(0, n - k)
-    return int(b.value) + outputs
+    return int(b.value) + probes + outputs
 
 
 class Request:
@@ -76,7 +86,7 @@ class Server:
     # -- client side ---------------------------------------------------------------
     def submit(self, rid, A, k, l, seed, nprobe=8, probe_seed=1):
         m, n = A.shape
-        nbytes = footprint(m, n, k, l, A.dtype, self.mode)
+        nbytes = footprint(m, n, k, l, A.dtype, self.mode, nprobe)
         if nbytes > self.budget:
             raise ValueError(f"request {rid} needs {nbytes} bytes, above the server's budget {self.budget}")
         req = Request(rid, A, k, l, seed, nprobe, probe_seed, nbytes)
@@ -141,17 +151,26 @@ class Server:
 
 
 def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None):
-    """One whole ID on `stream`; returns host copies of J, T and the estimate."""
+    """One whole ID on `stream`; returns host copies of J, T and the estimate.
+    In the FP64 modes the error comes from row probes that the sketch
+    multiplies in its one pass over A; the mixed mode takes column probes."""
     m, n = A.shape
     stream = stream or torch.cuda.current_stream(A.device)
     with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream) as plan:
-        Y = colmajor_empty(l, n, device=A.device)
-        perm = torch.empty(n, dtype=torch.int32, device=A.device)
-        T = colmajor_empty(k, n - k, device=A.device)
+        rows = mode in ROW_PROBE_MODES
+        if rows:
+            plan.set_probes(nprobe, probe_seed)
+        with torch.cuda.stream(stream):
+            Y = colmajor_empty(l, n, device=A.device)
+            perm = torch.empty(n, dtype=torch.int32, device=A.device)
+            T = colmajor_empty(k, n - k, device=A.device)
         plan.sketch(A, Y)
         plan.select(Y, perm)
         plan.solve(Y, T)
-        est, upper = plan.error(A, perm, T, nprobe, probe_seed)     # synchronizes the stream
+        if rows:
+            est, upper = plan.error_sketched(perm, T)                # synchronizes the stream
+        else:
+            est, upper = plan.error(A, perm, T, nprobe, probe_seed)
         plan.sync_status()
         return {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper}
 
