@@ -271,6 +271,21 @@ RID_API rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int
                                  int32_t tile, double* err_out, int32_t* status_out, void* workspace,
                                  size_t ws_bytes, void* stream);
 
+/* The two halves of rid_batch_run, for callers that run one batch many
+ * times or capture it in a CUDA graph:
+ *   rid_batch_prepare checks the items (RID_EINVAL / RID_EUNSUPPORTED as
+ *   rid_batch_run), orders them by cost (largest first) and stages their
+ *   descriptors in `workspace`; it synchronizes the stream once.
+ *   rid_batch_launch then runs the prepared batch: one memset of the work
+ *   queue and one persistent kernel launch on `stream`, nothing else (no host
+ *   copies, no synchronization), so it can be captured in a CUDA graph and
+ *   replayed.  count and nprobe must match the prepare call; the pointers of
+ *   the items (A, Y, perm, T) must stay valid while launches may run. */
+RID_API rid_status rid_batch_prepare(const rid_batch_item* items, int32_t count, int32_t nprobe, void* workspace,
+                                     size_t ws_bytes, void* stream);
+RID_API rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t probe_seed, int32_t tile,
+                                    double* err_out, int32_t* status_out, void* workspace, void* stream);
+
 /* Static, human-readable name of a status code. */
 RID_API const char* rid_status_string(rid_status status);
 

@@ -216,11 +216,13 @@ class Plan:
 
 
 class Batch:
-    """Many independent complex128 IDs run together by rid_batch_run.
+    """Many independent complex128 IDs run together in one persistent launch.
 
     problems: list of (A, k, l, seed) with A a column-major complex128 device
-    tensor.  Outputs (Y holding R, perm, T) are allocated here; run() launches
-    all problems in one persistent kernel on the current stream.
+    tensor.  Outputs (Y holding R, perm, T) are allocated here and the batch is
+    prepared once (rid_batch_prepare: checks, cost order, descriptors on the
+    device); run() launches it (rid_batch_launch) on the current stream, and
+    capture() records that launch in a CUDA graph for replay().
     """
 
     _tile_cache = {}
@@ -253,14 +255,37 @@ class Batch:
         self.err = torch.empty(2 * max(1, self.count), dtype=torch.float64, device=self.device)
         self.status = torch.empty(max(1, self.count), dtype=torch.int32, device=self.device)
         self.signature = (self.count, sum(int(p[0].shape[0]) * int(p[0].shape[1]) for p in problems) // max(1, self.count))
+        self.graph = None
+        stream = torch.cuda.current_stream(self.device)
+        check(self._lib.rid_batch_prepare(ctypes.byref(self.items), self.count, self.nprobe,
+                                          ctypes.c_void_p(self.ws.data_ptr()), self.ws.numel(),
+                                          ctypes.c_void_p(stream.cuda_stream)), "rid_batch_prepare")
+
+    def _launch(self, tile, stream):
+        check(self._lib.rid_batch_launch(self.count, self.nprobe, self.probe_seed & (2 ** 64 - 1), int(tile),
+                                         ctypes.c_void_p(self.err.data_ptr()), ctypes.c_void_p(self.status.data_ptr()),
+                                         ctypes.c_void_p(self.ws.data_ptr()), ctypes.c_void_p(stream.cuda_stream)),
+              "rid_batch_launch")
 
     def run(self, tile=None, stream=None):
+        """Launch the prepared batch (one memset, one persistent kernel)."""
         tile = tile or self._tile_cache.get(self.signature, 32)
-        stream = stream or torch.cuda.current_stream(self.device)
-        check(self._lib.rid_batch_run(ctypes.byref(self.items), self.count, self.nprobe,
-                                      self.probe_seed & (2 ** 64 - 1), int(tile), ctypes.c_void_p(self.err.data_ptr()),
-                                      ctypes.c_void_p(self.status.data_ptr()), ctypes.c_void_p(self.ws.data_ptr()),
-                                      self.ws.numel(), ctypes.c_void_p(stream.cuda_stream)), "rid_batch_run")
+        self._launch(tile, stream or torch.cuda.current_stream(self.device))
+        return self
+
+    def capture(self, tile=None):
+        """Record the batch's launch in a CUDA graph; replay() then runs it."""
+        tile = tile or self._tile_cache.get(self.signature, 32)
+        side = torch.cuda.Stream(self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, stream=side):
+            self._launch(tile, side)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        return self
+
+    def replay(self):
+        self.graph.replay()
         return self
 
     def autotune(self, tiles=(16, 32), reps=2):

@@ -423,12 +423,10 @@ rid_status rid_batch_workspace(int32_t count, size_t* bytes) {
   return RID_OK;
 }
 
-rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t nprobe, uint64_t probe_seed,
-                         int32_t tile, double* err_out, int32_t* status_out, void* workspace, size_t ws_bytes,
-                         void* stream) {
-  if (count < 0 || (count > 0 && (!items || !err_out || !status_out || !workspace))) return RID_EINVAL;
+rid_status rid_batch_prepare(const rid_batch_item* items, int32_t count, int32_t nprobe, void* workspace,
+                             size_t ws_bytes, void* stream) {
+  if (count < 0 || (count > 0 && (!items || !workspace))) return RID_EINVAL;
   if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
-  if (tile != 16 && tile != 32) return RID_EINVAL;
   size_t need = 0;
   rid_batch_workspace(count, &need);
   if (ws_bytes < need) return RID_EINVAL;
@@ -437,10 +435,12 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
   BatchItemDev* dev = (BatchItemDev*)malloc(sizeof(BatchItemDev) * (size_t)count);
   int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
   double* cost = (double*)malloc(sizeof(double) * (size_t)count);
-  if (!dev || !order || !cost) {
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
+  if (!dev || !order || !cost || !tmp) {
     free(dev);
     free(order);
     free(cost);
+    free(tmp);
     return RID_ENOMEM;
   }
   rid_status st = RID_OK;
@@ -456,16 +456,8 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
     order[i] = i;
     cost[i] = 8.0 * x.l * (double)x.m * (double)x.n + 8.0 * nprobe * (double)x.m * (double)x.n;
   }
-  if (st != RID_OK) {
-    free(dev);
-    free(order);
-    free(cost);
-    return st;
-  }
-  // largest first: a simple insertion-free sort by cost
-  {
-    int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
-    // bottom-up merge sort on order[] by descending cost
+  if (st == RID_OK) {
+    // largest first: bottom-up merge sort of order[] by descending cost (stable)
     for (int32_t w = 1; w < count; w *= 2) {
       for (int32_t lo = 0; lo < count; lo += 2 * w) {
         int32_t mid = lo + w < count ? lo + w : count, hi = lo + 2 * w < count ? lo + 2 * w : count;
@@ -476,35 +468,54 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
       }
       for (int32_t i = 0; i < count; ++i) order[i] = tmp[i];
     }
-    free(tmp);
   }
+  cudaError_t e = cudaSuccess;
+  if (st == RID_OK) {
+    cudaStream_t s = (cudaStream_t)stream;
+    char* ws = (char*)workspace;
+    e = cudaMemcpyAsync(ws, dev, sizeof(BatchItemDev) * (size_t)count, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ws + (size_t)count * sizeof(BatchItemDev), order, sizeof(int32_t) * (size_t)count,
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);      // the host arrays are pageable
+    // the per-tile shared memory is fixed, so setting it here never races
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(16));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(32));
+  }
+  free(dev);
+  free(order);
+  free(cost);
+  free(tmp);
+  if (st != RID_OK) return st;
+  return e == cudaSuccess ? RID_OK : RID_ECUDA;
+}
+
+rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t probe_seed, int32_t tile, double* err_out,
+                            int32_t* status_out, void* workspace, void* stream) {
+  if (count < 0 || (count > 0 && (!err_out || !status_out || !workspace))) return RID_EINVAL;
+  if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  if (tile != 16 && tile != 32) return RID_EINVAL;
+  if (count == 0) return RID_OK;
   cudaStream_t s = (cudaStream_t)stream;
   char* ws = (char*)workspace;
   BatchItemDev* d_items = (BatchItemDev*)ws;
   int32_t* d_order = (int32_t*)(ws + (size_t)count * sizeof(BatchItemDev));
   unsigned* d_next = (unsigned*)(ws + (size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)));
-  cudaError_t e = cudaMemcpyAsync(d_items, dev, sizeof(BatchItemDev) * (size_t)count, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(d_order, order, sizeof(int32_t) * (size_t)count, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_next, 0, sizeof(unsigned), s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);      // the host arrays are pageable
-  free(dev);
-  free(order);
-  free(cost);
-  if (e != cudaSuccess) return RID_ECUDA;
+  if (cudaMemsetAsync(d_next, 0, sizeof(unsigned), s) != cudaSuccess) return RID_ECUDA;
   int dev_id = 0, sms = 0;
-  cudaGetDevice(&dev_id);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id);
+  if (cudaGetDevice(&dev_id) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess)
+    return RID_ECUDA;
   const size_t smem = batch_smem_bytes(tile);
   BatchArgs args{d_items, d_order, count, d_next, nprobe, probe_seed, err_out, status_out, tile};
   // persistent grid: as many CTAs as can be resident at once
   int per_sm = 1;
-  if (tile == 16) {
-    cudaFuncSetAttribute(batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (tile == 16)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16>, BT_THREADS, smem);
-  } else {
-    cudaFuncSetAttribute(batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32>, BT_THREADS, smem);
-  }
   if (per_sm < 1) per_sm = 1;
   const int grid = sms * per_sm < count ? sms * per_sm : count;
   if (tile == 16)
@@ -512,6 +523,16 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
   else
     batch_kernel<32><<<grid, BT_THREADS, smem, s>>>(args);
   return cudaGetLastError() == cudaSuccess ? RID_OK : RID_ECUDA;
+}
+
+rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t nprobe, uint64_t probe_seed,
+                         int32_t tile, double* err_out, int32_t* status_out, void* workspace, size_t ws_bytes,
+                         void* stream) {
+  if (count < 0 || (count > 0 && (!items || !err_out || !status_out || !workspace))) return RID_EINVAL;
+  if (tile != 16 && tile != 32) return RID_EINVAL;
+  const rid_status st = rid_batch_prepare(items, count, nprobe, workspace, ws_bytes, stream);
+  if (st != RID_OK) return st;
+  return rid_batch_launch(count, nprobe, probe_seed, tile, err_out, status_out, workspace, stream);
 }
 
 }  // extern "C"

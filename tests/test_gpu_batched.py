@@ -97,3 +97,23 @@ def test_batch_autotune_picks_a_tile(rid):
     b = rid.Batch([(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs])
     tile, ms = b.autotune()
     assert tile in (16, 32) and ms > 0
+
+
+def test_batch_graph_replay_equals_direct_launch(rid):
+    """The prepared batch captured in a CUDA graph: replays give the direct
+    launch's results bit for bit, and a replay after the outputs were wiped
+    writes them again."""
+    probs = make_problems(10, seed=9)
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    b = rid.Batch(dev, nprobe=6, probe_seed=2)
+    ref = [dict(x, T=x["T"].clone(), perm=x["perm"].clone()) for x in b.run(tile=32).results()]
+    b.capture(tile=32)
+    for rep in range(2):
+        for t in b.T:
+            t.zero_()
+        b.err.zero_()
+        b.replay()
+        got = b.results()
+        for a, c in zip(ref, got):
+            assert torch.equal(a["perm"], c["perm"]) and torch.equal(a["T"], c["T"])
+            assert a["est"] == c["est"] and a["upper"] == c["upper"] and c["status"] == 0
