@@ -171,6 +171,20 @@ RID_API rid_status rid_error(rid_plan_t plan, const void* A, int64_t lda, const 
  * caller's Omega unrounded and ends the rounding.  Synchronizes the stream. */
 RID_API rid_status rid_plan_round_omega(rid_plan_t plan, int32_t bits);
 
+/* The sketch of a column range: Y(:, c) = Omega A(:, c) (and X(:, c) = G A(:, c)
+ * for the row probes) for c = col0 .. col0 + ncols - 1, so that a caller can
+ * sketch A panel by panel as its columns reach the device (a host->device
+ * copy of the next panel overlaps the sketch of this one).  A and Y point to
+ * column 0 of the whole matrices as for rid_sketch; col0 a multiple of 128,
+ * ncols a multiple of 128 unless the range ends at column n (RID_EINVAL
+ * otherwise).  Each column's arithmetic is the same as in rid_sketch, so
+ * covering all columns once, in any ranges, gives rid_sketch's Y and X bit for
+ * bit.  Modes RID_FP64_NATIVE and RID_FP64_EMULATED (RID_EUNSUPPORTED
+ * otherwise).  Ranges of one plan are sketched in stream order; the row-probe
+ * error may follow once every column has been sketched. */
+RID_API rid_status rid_sketch_cols(rid_plan_t plan, const void* A, int64_t lda, void* Y, int64_t ldy,
+                                   int64_t col0, int64_t ncols);
+
 /* Row probes for the error of the ID (Sec. 3.3), computed in the sketch's
  * own pass over A.  Appends nprobe rows g_q to Omega: an nprobe x m complex
  * Gaussian G, entry (q, i) from the Philox block at counter (i lo, i hi, q, 6)

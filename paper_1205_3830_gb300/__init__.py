@@ -139,6 +139,15 @@ class Plan:
                                    ctypes.c_void_p(Y.data_ptr()), _ld(Y)), "rid_sketch")
         return Y
 
+    def sketch_cols(self, A, Y, col0, ncols):
+        """Columns col0 .. col0 + ncols - 1 of Y = Omega A (A, Y: the whole
+        matrices); panels covering every column give sketch()'s Y bit for bit."""
+        assert A.is_cuda and A.dtype == self.dtype and tuple(A.shape) == (self.m, self.n) and A.stride(0) == 1
+        check(self._lib.rid_sketch_cols(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
+                                        ctypes.c_void_p(Y.data_ptr()), _ld(Y), int(col0), int(ncols)),
+              "rid_sketch_cols")
+        return Y
+
     def select(self, Y, perm=None):
         """Pivoted QR of Y in place; returns perm (int32[n], J = perm[:k])."""
         assert Y.is_cuda and Y.dtype == torch.complex128 and Y.stride(0) == 1

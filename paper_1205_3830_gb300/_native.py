@@ -27,6 +27,7 @@ SIGNATURES = {
     "rid_plan_set_omega": (ctypes.c_int, [_c_plan, _p, _i64]),
     "rid_plan_use_srft": (ctypes.c_int, [_c_plan, _u64]),
     "rid_sketch": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),
+    "rid_sketch_cols": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64, _i64, _i64]),
     "rid_select": (ctypes.c_int, [_c_plan, _p, _i64, _p]),
     "rid_solve": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),
     "rid_error": (ctypes.c_int, [_c_plan, _p, _i64, _p, _p, _i64, _i32, _u64,

@@ -14,6 +14,8 @@
 rid_status rid_tc_plan_init_fp64(rid_plan_s* p);
 void rid_tc_plan_free_fp64(rid_plan_s* p);
 cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy,
+                                    int64_t col0, int64_t ncols);
 int rid_tc_error_word_fp64(const rid_plan_s* p);
 rid_status rid_mx_plan_init(rid_plan_s* p);
 rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run);
@@ -438,9 +440,27 @@ rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t
   if (!g.ok) return RID_ECUDA;
   cudaError_t e;
   if (p->mode == RID_FP64_NATIVE)
-    e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy);
+    e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy, 0, p->n);
   else
     e = rid_tc_sketch(p, A, lda, (double2*)Y, ldy);
+  if (e == cudaSuccess && p->nrow > 0) p->x_valid = 1;
+  return from_cuda(e);
+}
+
+rid_status rid_sketch_cols(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t ldy, int64_t col0,
+                           int64_t ncols) {
+  if (!p || !A || !Y || lda < p->m || ldy < p->l) return RID_EINVAL;
+  if (col0 < 0 || ncols < 0 || col0 + ncols > p->n || col0 % 128 != 0) return RID_EINVAL;
+  if (ncols % 128 != 0 && col0 + ncols != p->n) return RID_EINVAL;
+  if (!aligned16(Y) || ((uintptr_t)A & (p->dtype == RID_C128 ? 15u : 7u))) return RID_EINVAL;
+  if (p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED) return RID_EUNSUPPORTED;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  cudaError_t e;
+  if (p->mode == RID_FP64_NATIVE)
+    e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy, col0, ncols);
+  else
+    e = rid_tc_sketch_cols_fp64(p, A, lda, (double2*)Y, ldy, col0, ncols);
   if (e == cudaSuccess && p->nrow > 0) p->x_valid = 1;
   return from_cuda(e);
 }

@@ -108,7 +108,7 @@ cudaError_t rid_launch_round_rows(double2* om, int64_t rows, int64_t m, int64_t 
 cudaError_t rid_launch_srft(double2* out, int64_t l, int64_t m, int64_t ldo, uint64_t seed, cudaStream_t stream);
 
 cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_t lda, double2* Y,
-                                   int64_t ldy);
+                                   int64_t ldy, int64_t col0, int64_t ncols);
 
 cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm);
 // CTAs of the cooperative select for n columns on this device (0: not available).

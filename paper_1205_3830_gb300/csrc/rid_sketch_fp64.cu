@@ -95,9 +95,15 @@ __global__ void splitk_reduce_kernel(const double2* __restrict__ part, int64_t s
 }  // namespace
 
 cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_t lda, double2* Y,
-                                   int64_t ldy) {
+                                   int64_t ldy, int64_t col0, int64_t ncols) {
+  // columns col0 .. col0 + ncols - 1: every column is independent
+  if (ncols <= 0) return cudaSuccess;
   const int64_t ls = p->ls, ly = p->l, ldx = p->nrow > 0 ? p->nrow : 1;
-  const dim3 grid((unsigned)((ls + BL - 1) / BL), (unsigned)((p->n + BN - 1) / BN),
+  A += col0 * lda;
+  Y += col0 * ldy;
+  double2* X = p->xrow ? p->xrow + col0 * ldx : nullptr;
+  const int64_t n = ncols;
+  const dim3 grid((unsigned)((ls + BL - 1) / BL), (unsigned)((n + BN - 1) / BN),
                   (unsigned)p->split_k);
   if (p->timing) {
     cudaEventRecord(p->ev[0], p->stream);
@@ -105,23 +111,23 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
   }
   if (p->split_k == 1) {
     sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, Y, ldy, 0, ls,
-                                                    p->m, p->n, p->k_per_split, ly, p->xrow, ldx);
+                                                    p->m, n, p->k_per_split, ly, X, ldx);
     if (p->timing) {
       cudaEventRecord(p->ev[2], p->stream);
       cudaEventRecord(p->ev[3], p->stream);
     }
     return cudaGetLastError();
   }
-  const int64_t stride = ls * p->n;
+  const int64_t stride = ls * n;
   sketch_fp64_kernel<<<grid, 256, 0, p->stream>>>(p->omega, p->ldo, A, lda, p->sk_partial, ls,
-                                                  stride, ls, p->m, p->n, p->k_per_split, ls, nullptr, 0);
+                                                  stride, ls, p->m, n, p->k_per_split, ls, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   int64_t blocks = (stride + 255) / 256;
   if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
   if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->sk_partial, stride,
-                                                                p->split_k, Y, ldy, ls, p->n, ly, p->xrow, ldx);
+                                                                p->split_k, Y, ldy, ls, n, ly, X, ldx);
   if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return cudaGetLastError();
 }

@@ -246,12 +246,13 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 // lane takes 4 consecutive complex rows, so every slice row is written with
 // one 16-byte store per lane.
 __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict__ A, int64_t lda, int64_t m,
-                                                      int64_t n, int NC, int64_t KP,
+                                                      int64_t n, int NC, int64_t KP, int64_t slice_stride,
                                                       uint16_t* __restrict__ slices, int* __restrict__ a_exp,
                                                       int* __restrict__ a_exp_max) {
+  // A, slices, a_exp and a_exp_max start at the first column of the range
+  // (n columns); slice_stride separates the digit planes of the whole matrix
   const int lane = threadIdx.x & 31;
   const int64_t tasks = n * NC;
-  const int64_t slice_stride = n * KP;
   for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks;
        t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const int64_t j = t / NC;
@@ -289,6 +290,7 @@ struct TcArgs {
   uint32_t o_off;         // offset of the Omega tiles in a stage
   uint32_t o_tile_smem;   // shared memory of one Omega tile (1024-byte multiple)
   int cx, cy;             // cluster: cx N-tiles (share A tiles) x cy column blocks (share Omega tiles)
+  int jb0;                // first column block of the launch (a column range of the sketch)
   const int* a_exp;
   const int* a_exp_max;
   float2* partial;
@@ -349,7 +351,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
   // all N-tiles of cy column blocks.  Each A tile is loaded once per cluster
   // row and multicast to the cx CTAs that use it; each Omega tile once per
   // cluster column and multicast to the cy CTAs that use it.
-  const int nb = blockIdx.x, jb = blockIdx.y, ks = blockIdx.z;
+  const int nb = blockIdx.x, jb = blockIdx.y + a.jb0, ks = blockIdx.z;
   const int rx = nb % a.cx, ry = jb % a.cy;
   const uint32_t my_rank = (uint32_t)(rx + ry * a.cx);
   const uint16_t row_mask = (uint16_t)(((1u << a.cx) - 1u) << (ry * a.cx));
@@ -551,11 +553,12 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
 __global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit, int64_t n, int l, int l2p,
                                  const int* __restrict__ om_exp, const int* __restrict__ a_exp_max,
                                  double2* __restrict__ Y, int64_t ldy, int ly, double2* __restrict__ X,
-                                 int64_t ldx) {
-  const int64_t total = n * l;
+                                 int64_t ldx, int64_t j0, int64_t ncols) {
+  // columns j0 .. j0 + ncols - 1 of the n-column partial sums
+  const int64_t total = ncols * l;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / l;
-    const int i = (int)(e - j * l);
+    const int64_t j = j0 + e / l;
+    const int i = (int)(e - (j - j0) * l);
     double re = 0.0, im = 0.0;
     for (int s = 0; s < ksplit; ++s) {
       const float2* p = partial + ((int64_t)s * n + j) * l2p + 2 * i;
@@ -759,31 +762,39 @@ void rid_tc_plan_free_fp64(rid_plan_s* p) {
   p->tc_bytes = 0;
 }
 
-cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
+// Columns col0 .. col0 + ncols - 1 of the sketch (col0 a multiple of 128).  The
+// K-split is the plan's, so any set of column ranges gives the same Y as one
+// call over all columns.
+cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy,
+                                    int64_t col0, int64_t ncols) {
   const TcState* st = (const TcState*)p->tc_state;
   if (!st) return cudaErrorNotSupported;
+  if (ncols <= 0) return cudaSuccess;
   const double2* A = (const double2*)A_;
   if (p->timing) cudaEventRecord(p->ev[0], p->stream);
   // 0x80808080 is below every exponent: the running maximum starts there
-  cudaError_t e = cudaMemsetAsync(st->a_exp_max, 0x80, (size_t)p->n * 4, p->stream);
+  cudaError_t e = cudaMemsetAsync(st->a_exp_max + col0, 0x80, (size_t)ncols * 4, p->stream);
   if (e != cudaSuccess) return e;
   {
-    const int64_t tasks = p->n * (int64_t)st->NC;
+    const int64_t tasks = ncols * (int64_t)st->NC;
     int64_t blocks = (tasks * 32 + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
-    a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, p->n, st->NC, st->KP, st->a_slices,
-                                                             st->a_exp, st->a_exp_max);
+    a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A + col0 * lda, lda, p->m, ncols, st->NC, st->KP,
+                                                             p->n * st->KP, st->a_slices + col0 * st->KP,
+                                                             st->a_exp + col0 * st->NC, st->a_exp_max + col0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p->timing) cudaEventRecord(p->ev[1], p->stream);
+  const int jb0 = (int)(col0 / 128);
+  const int nblocks = (int)((ncols + 127) / 128);
   TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
               (uint32_t)(TC_S * TC_TILE_BYTES + st->so * st->tile_w * TC_KS * 2), st->so, st->nstages,
-              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, st->cy,
+              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, st->cy, jb0,
               st->a_exp, st->a_exp_max, st->partial, st->err};
   {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)st->ntiles, (unsigned)st->nblocks_p, (unsigned)st->ksplit);
+    cfg.gridDim = dim3((unsigned)st->ntiles, (unsigned)((nblocks + st->cy - 1) / st->cy * st->cy), (unsigned)st->ksplit);
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = st->dyn_smem;
     cfg.stream = p->stream;
@@ -798,16 +809,20 @@ cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda,
   }
   if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   {
-    const int64_t total = p->n * (int64_t)p->ls;
+    const int64_t total = ncols * (int64_t)p->ls;
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
     tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->ls, st->l2p,
                                                                st->om_exp, st->a_exp_max, Y, ldy, p->l, p->xrow,
-                                                               p->nrow > 0 ? p->nrow : 1);
+                                                               p->nrow > 0 ? p->nrow : 1, col0, ncols);
     e = cudaGetLastError();
   }
   if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return e;
+}
+
+cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
+  return rid_tc_sketch_cols_fp64(p, A_, lda, Y, ldy, 0, p->n);
 }
 
 int rid_tc_error_word_fp64(const rid_plan_s* p) {

@@ -157,3 +157,39 @@ def test_row_probe_argument_errors(rid):
     with rid.Plan(m, n, k, l, seed=1, dtype=torch.complex64, mode="bf16") as plan:
         with pytest.raises(RIDError, match="EUNSUPPORTED"):
             plan.set_probes(4, 1)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("shape", [(2048, 1000, 20, 30), (700, 384, 10, 16), (3000, 129, 5, 9)], ids=str)
+def test_sketch_by_column_panels_equals_one_sketch(rid, shape, mode):
+    """Panels of columns, sketched in any order, give rid_sketch's Y and the
+    same row-probe estimate, bit for bit."""
+    m, n, k, l = shape
+    A = to_dev_colmajor(lowrank(m, n, k))
+    with rid.Plan(m, n, k, l, seed=21, mode=mode) as plan:
+        plan.set_probes(8, 3)
+        Y0 = plan.sketch(A).clone()
+        R = Y0.clone()
+        perm = plan.select(R)
+        T = plan.solve(R)
+        e0 = plan.error_sketched(perm, T)
+        Y1 = torch.full_like(Y0, float("nan"))
+        starts = list(range(0, n, 256))
+        for c0 in reversed(starts):                       # out of order on purpose
+            plan.sketch_cols(A, Y1, c0, min(256, n - c0))
+        e1 = plan.error_sketched(perm, T)
+    assert torch.equal(Y0, Y1)
+    assert e0 == e1
+
+
+
+def test_sketch_cols_argument_errors(rid):
+    from paper_1205_3830_gb300._native import RIDError
+    m, n, k, l = 300, 400, 5, 10
+    A = to_dev_colmajor(lowrank(m, n, k))
+    with rid.Plan(m, n, k, l, seed=1, mode="fp64_emulated") as plan:
+        Y = plan.sketch(A)
+        for c0, nc in ((64, 128), (0, 100), (256, 256), (-128, 128)):
+            with pytest.raises(RIDError, match="EINVAL"):
+                plan.sketch_cols(A, Y, c0, nc)
+        plan.sketch_cols(A, Y, 256, 144)                  # the last, ragged panel
