@@ -97,29 +97,46 @@ __device__ __forceinline__ bool zlarfg_scalars(double2 alpha, double xnorm2, dou
   return true;
 }
 
-// H^H applied to one column, held in registers: x = in[0..rows),
-// out = x - v (conj(tau) v^H x), and the returned sum_{i>0} |out_i|^2 (valid
-// in lane 0 when norm is set).  R = ceil(rows / 32) register chunks per lane;
-// v is zero beyond rows, so only the stores are predicated.  Both select paths
-// call this, so they round alike.
-template <int R>
-__device__ __forceinline__ double reflect_column(const double2* __restrict__ in, double2* __restrict__ out,
-                                                 const double2* __restrict__ v, double2 ctau, int rows, int lane,
-                                                 bool norm) {
-  double2 x[R];
-  double2 w0 = make_double2(0.0, 0.0), w1 = make_double2(0.0, 0.0);   // two chains for the FP64 pipe
+// Warp sums of two values by reduce-scatter: lanes 0-15 finish the first,
+// lanes 16-31 the second (5 additions per lane instead of 10).  The result of
+// each value is the one a plain xor butterfly leaves in lane 0.
+__device__ __forceinline__ void warp_sum2(double& a, double& b, int lane) {
+  const bool hi = lane & 16;
+  double k = hi ? b : a;
+  k += __shfl_xor_sync(0xffffffffu, hi ? a : b, 16);
 #pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int i = lane + 32 * u;
-    x[u] = (i < rows) ? __ldcg(in + i) : make_double2(0.0, 0.0);
-    if (u & 1) w1 = cfma_conj(v[i], x[u], w1);
-    else w0 = cfma_conj(v[i], x[u], w0);
-  }
-  double2 w = make_double2(w0.x + w1.x, w0.y + w1.y);
-  w.x = warp_sum(w.x);
-  w.y = warp_sum(w.y);
-  const double2 s = cmul(ctau, w);                // conj(tau) (v^H x)
-  double nu0 = 0.0, nu1 = 0.0;
+  for (int off = 8; off > 0; off >>= 1) k += __shfl_xor_sync(0xffffffffu, k, off);
+  a = __shfl_sync(0xffffffffu, k, 0);
+  b = __shfl_sync(0xffffffffu, k, 16);
+}
+
+// The same for four values: lanes 0-7, 8-15, 16-23, 24-31 finish a, b, c, d
+// (6 additions per lane instead of 20); each result equals warp_sum2's.
+__device__ __forceinline__ void warp_sum4(double& a, double& b, double& c, double& d, int lane) {
+  const bool hi16 = lane & 16, hi8 = lane & 8;
+  double k0 = hi16 ? c : a, k1 = hi16 ? d : b;
+  k0 += __shfl_xor_sync(0xffffffffu, hi16 ? a : c, 16);
+  k1 += __shfl_xor_sync(0xffffffffu, hi16 ? b : d, 16);
+  double k = hi8 ? k1 : k0;
+  k += __shfl_xor_sync(0xffffffffu, hi8 ? k0 : k1, 8);
+#pragma unroll
+  for (int off = 4; off > 0; off >>= 1) k += __shfl_xor_sync(0xffffffffu, k, off);
+  a = __shfl_sync(0xffffffffu, k, 0);
+  b = __shfl_sync(0xffffffffu, k, 8);
+  c = __shfl_sync(0xffffffffu, k, 16);
+  d = __shfl_sync(0xffffffffu, k, 24);
+}
+
+// Per column, in registers: x = in[0..rows); w = v^H x (one chain over the
+// lane's chunks); out = x - v (conj(tau) w) by a fused complex
+// multiply-subtract; nu = sum_{i>0} |out_i|^2 (real and imaginary chains).
+// R = ceil(rows / 32) chunks per lane; v is zero beyond rows, so only the
+// stores are predicated.  The single and the paired form give every column
+// the same arithmetic in the same order, so which columns a warp pairs never
+// changes a result, and both select paths round alike.
+template <int R>
+__device__ __forceinline__ void column_update(double2 (&x)[R], const double2* __restrict__ v, double2 s,
+                                              double2* __restrict__ out, int rows, int lane, double& nr, double& ni) {
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int i = lane + 32 * u;
@@ -130,11 +147,59 @@ __device__ __forceinline__ double reflect_column(const double2* __restrict__ in,
     x[u].y = fma(-vi.y, s.x, x[u].y);
     if (i < rows) out[i] = x[u];
     if (u > 0 || lane > 0) {
-      nu0 = fma(x[u].x, x[u].x, nu0);
-      nu1 = fma(x[u].y, x[u].y, nu1);
+      nr = fma(x[u].x, x[u].x, nr);
+      ni = fma(x[u].y, x[u].y, ni);
     }
   }
-  return norm ? warp_sum(nu0 + nu1) : 0.0;
+}
+
+template <int R>
+__device__ __forceinline__ double reflect_column(const double2* __restrict__ in, double2* __restrict__ out,
+                                                 const double2* __restrict__ v, double2 ctau, int rows, int lane,
+                                                 bool norm) {
+  double2 x[R];
+  double2 w = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    x[u] = (i < rows) ? __ldcg(in + i) : make_double2(0.0, 0.0);
+    w = cfma_conj(v[i], x[u], w);
+  }
+  warp_sum2(w.x, w.y, lane);
+  double nr = 0.0, ni = 0.0;
+  column_update<R>(x, v, cmul(ctau, w), out, rows, lane, nr, ni);
+  if (!norm) return 0.0;
+  double nu = nr + ni;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) nu += __shfl_xor_sync(0xffffffffu, nu, off);
+  return __shfl_sync(0xffffffffu, nu, 0);
+}
+
+// Two columns at once: independent chains for the FP64 pipe and shared
+// reduce-scatter sums.
+template <int R>
+__device__ __forceinline__ void reflect_pair(const double2* __restrict__ in0, double2* __restrict__ out0,
+                                             const double2* __restrict__ in1, double2* __restrict__ out1,
+                                             const double2* __restrict__ v, double2 ctau, int rows, int lane,
+                                             bool norm, double& nu0, double& nu1) {
+  double2 x[R], y[R];
+  double2 w0 = make_double2(0.0, 0.0), w1 = make_double2(0.0, 0.0);
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int i = lane + 32 * u;
+    x[u] = (i < rows) ? __ldcg(in0 + i) : make_double2(0.0, 0.0);
+    y[u] = (i < rows) ? __ldcg(in1 + i) : make_double2(0.0, 0.0);
+    const double2 vi = v[i];
+    w0 = cfma_conj(vi, x[u], w0);
+    w1 = cfma_conj(vi, y[u], w1);
+  }
+  warp_sum4(w0.x, w0.y, w1.x, w1.y, lane);
+  double nr0 = 0.0, ni0 = 0.0, nr1 = 0.0, ni1 = 0.0;
+  column_update<R>(x, v, cmul(ctau, w0), out0, rows, lane, nr0, ni0);
+  column_update<R>(y, v, cmul(ctau, w1), out1, rows, lane, nr1, ni1);
+  nu0 = nr0 + ni0;
+  nu1 = nr1 + ni1;
+  if (norm) warp_sum2(nu0, nu1, lane);
 }
 
 // RMAX: the largest chunk count a kernel instantiation handles (8: l <= 256,
@@ -153,6 +218,29 @@ __device__ __forceinline__ double reflect_any(const double2* in, double2* out, c
     default: break;
   }
   return 0.0;
+}
+
+// Pairs only where two columns of registers fit without spilling at two CTAs
+// per SM (RMAX = 8, up to 6 chunks); returns false when the caller must take
+// the columns one at a time.
+#ifndef RID_SEL_PAIR_MAX
+#define RID_SEL_PAIR_MAX 6
+#endif
+template <int RMAX>
+__device__ __forceinline__ bool reflect_any_pair(const double2* in0, double2* out0, const double2* in1, double2* out1,
+                                                 const double2* v, double2 ctau, int rows, int lane, bool norm,
+                                                 double& nu0, double& nu1) {
+  if (RMAX > 8) return false;
+  switch ((rows + 31) >> 5) {
+#define RID_PAIR_CASE(R) \
+    case R: reflect_pair<(R <= 8 ? R : 1)>(in0, out0, in1, out1, v, ctau, rows, lane, norm, nu0, nu1); return true;
+    RID_PAIR_CASE(1) RID_PAIR_CASE(2) RID_PAIR_CASE(3) RID_PAIR_CASE(4) RID_PAIR_CASE(5) RID_PAIR_CASE(6)
+#if RID_SEL_PAIR_MAX >= 7
+    RID_PAIR_CASE(7)
+#endif
+#undef RID_PAIR_CASE
+    default: return false;
+  }
 }
 
 constexpr int rid_min_blocks(int rmax) { return rmax <= 8 ? 2 : 1; }
@@ -268,10 +356,21 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_step_
   const int64_t gwarp = ((int64_t)blockIdx.x * QR_THREADS + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t)gridDim.x * QR_WARPS;
   ArgMax best{-1.0, INT_MAX};
-  for (int64_t c = j + 1 + gwarp; c < a.n; c += nwarps) {
+  for (int64_t c = j + 1 + gwarp; c < a.n; c += 2 * nwarps) {
+    const int64_t c2 = c + nwarps;
     double2* col = a.Y + c * a.ldy + j;
-    const double nu = reflect_any<RMAX>(col, col, v, ctau, rows, lane, true);
-    best = better(best, ArgMax{nu, (int)c});
+    double nu0 = 0.0, nu1 = 0.0;
+    if (c2 < a.n && reflect_any_pair<RMAX>(col, col, a.Y + c2 * a.ldy + j, a.Y + c2 * a.ldy + j, v, ctau, rows,
+                                           lane, true, nu0, nu1)) {
+      best = better(best, ArgMax{nu0, (int)c});
+      best = better(best, ArgMax{nu1, (int)c2});
+      continue;
+    }
+    best = better(best, ArgMax{reflect_any<RMAX>(col, col, v, ctau, rows, lane, true), (int)c});
+    if (c2 < a.n) {
+      double2* col2 = a.Y + c2 * a.ldy + j;
+      best = better(best, ArgMax{reflect_any<RMAX>(col2, col2, v, ctau, rows, lane, true), (int)c2});
+    }
   }
   if (j + 1 >= a.k) return;                         // last step: no further pivot
   if (post_and_check_last(a, best)) pivot_and_reflect(a, j + 1);
@@ -364,6 +463,7 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
   __shared__ double2 rc[32 * QR_PER_LANE];   // column j of R with reflector j below it
   __shared__ double2 s_tau, s_scale;
   __shared__ int s_b;
+  __shared__ ArgMax s_win;
   const int lane = threadIdx.x & 31;
   const int G = gridDim.x;
   const int l = a.l;
@@ -388,23 +488,27 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
 
   for (int j = 0; j < a.k; ++j) {
     const int buf = j & 1;
-    // pivot j: the best posted pair (ties to the lowest position)
-    ArgMax w{-1.0, INT_MAX};
-    int wb = -1;
-    for (int b = threadIdx.x; b < G; b += QR_THREADS) {
-      const ArgMax o{__ldcg(a.val + (int64_t)buf * G + b), __ldcg(a.idx + (int64_t)buf * G + b)};
-      const ArgMax nb = better(w, o);
-      if (nb.i != w.i) {
-        w = nb;
-        wb = b;
+    // pivot j: the best posted pair (ties to the lowest position), by warp 0
+    if (threadIdx.x < 32) {
+      ArgMax w{-1.0, INT_MAX};
+      int wb = -1;
+      for (int b = lane; b < G; b += 32) {
+        const ArgMax o{__ldcg(a.val + (int64_t)buf * G + b), __ldcg(a.idx + (int64_t)buf * G + b)};
+        const ArgMax nb = better(w, o);
+        if (nb.i != w.i) {
+          w = nb;
+          wb = b;
+        }
       }
+      const ArgMax rw = warp_argmax(w);
+      if (wb >= 0 && w.i == rw.i) s_b = wb;
+      if (lane == 0) s_win = rw;
     }
-    const ArgMax r = block_argmax(w);
-    if (wb >= 0 && w.i == r.i) s_b = wb;
     // column j - 1 of R, held since the last step, into its slot
     if (j > 0 && blockIdx.x == (j - 1) % G)
       for (int i = threadIdx.x; i < l; i += QR_THREADS) a.Y[(int64_t)(j - 1) * a.ldy + i] = rc[i];
     __syncthreads();
+    const ArgMax r = s_win;
     if (!(r.v > 0.0)) {                                  // rank(Y) = j < k (Sec. 2)
       if (blockIdx.x == 0 && threadIdx.x == 0) *a.status = RID_ERANK;
       return;
@@ -445,14 +549,36 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     const double2 ctau = make_double2(s_tau.x, -s_tau.y);
     const bool more = j + 1 < a.k;
     ArgMax best{-1.0, INT_MAX};
-    for (int64_t c = j + 1 + gwarp; c < a.n; c += nwarps) {
-      const int64_t src = (c == p) ? j : c;
+    // each CTA an even contiguous share of positions j+1 .. n-1; its warps
+    // take them in pairs (c, c + QR_WARPS)
+    const int64_t first = j + 1, span = a.n - first;
+    const int64_t lo = first + span * blockIdx.x / G, hi = first + span * (blockIdx.x + 1) / G;
+    const int wid = threadIdx.x >> 5;
+    for (int64_t c = lo + wid; c < hi; c += 2 * QR_WARPS) {
+      const int64_t c2 = c + QR_WARPS;
+      const int64_t src = (c == p) ? j : c, src2 = (c2 == p) ? j : c2;
       const double2* in = a.Y + src * a.ldy;
       double2* out = a.Y + c * a.ldy;
+      const double2* in2 = a.Y + src2 * a.ldy;
+      double2* out2 = a.Y + c2 * a.ldy;
       if (src != c)
         for (int i = lane; i < j; i += 32) out[i] = __ldcg(in + i);     // the rows above j move along
-      const double nu = reflect_any<RMAX>(in + j, out + j, v, ctau, rows, lane, more);
-      if (more) best = better(best, ArgMax{nu, (int)c});
+      if (c2 < hi && src2 != c2)
+        for (int i = lane; i < j; i += 32) out2[i] = __ldcg(in2 + i);
+      double nu0 = 0.0, nu1 = 0.0;
+      if (c2 < hi && reflect_any_pair<RMAX>(in + j, out + j, in2 + j, out2 + j, v, ctau, rows, lane, more, nu0, nu1)) {
+        if (more) {
+          best = better(best, ArgMax{nu0, (int)c});
+          best = better(best, ArgMax{nu1, (int)c2});
+        }
+        continue;
+      }
+      nu0 = reflect_any<RMAX>(in + j, out + j, v, ctau, rows, lane, more);
+      if (more) best = better(best, ArgMax{nu0, (int)c});
+      if (c2 < hi) {
+        nu1 = reflect_any<RMAX>(in2 + j, out2 + j, v, ctau, rows, lane, more);
+        if (more) best = better(best, ArgMax{nu1, (int)c2});
+      }
     }
     if (more) post_candidate(a, best, (j + 1) & 1);
     if (!grid_sync(a)) return;       // after the last step too: slot k-1 may still be read
