@@ -6,12 +6,16 @@
 // is divided by R1_jj, then column j of R1 (rows 0..j-1, staged in shared
 // memory) updates every row above it.  R1 (k x k, at most a few hundred KB)
 // stays in L2 for all CTAs.
+#include <climits>
+#include <cstdint>
+
 #include "rid_internal.cuh"
 
 namespace {
 
 constexpr int SOLVE_THREADS = 256;
 constexpr size_t SOLVE_SMEM_BUDGET = 200 * 1024;
+constexpr size_t SOLVE_SMEM_LIMIT = 227 * 1024;    // shared memory of an SM available to CTAs
 
 __global__ void __launch_bounds__(SOLVE_THREADS)
 solve_kernel(const double2* __restrict__ Y, int64_t ldy, int k, int64_t n, int nr,
@@ -60,13 +64,41 @@ size_t rid_solve_smem_bytes(int k, int* nr_out) {
   return (size_t)(k * nr + k) * sizeof(double2);
 }
 
+namespace {
+
+// Right-hand sides per CTA: the FP64 pipe of an SM is shared by its CTAs, so
+// the time is set by the busiest SM, ceil(CTAs / SMs) blocks of nr columns.
+// Among widths that fit (and keep a step's update worth a barrier, nr >= 8),
+// take the one that minimizes that product.
+int solve_block_width(int k, int64_t ncols, int sms, int nr_max) {
+  int best = nr_max;
+  int64_t best_cost = INT64_MAX;
+  for (int nr = nr_max; nr >= 8 || (nr >= 1 && nr == nr_max); --nr) {
+    const size_t smem = (size_t)(k * nr + k) * sizeof(double2);
+    int per_sm = (int)((size_t)(SOLVE_SMEM_LIMIT) / smem);
+    if (per_sm > 2048 / SOLVE_THREADS) per_sm = 2048 / SOLVE_THREADS;
+    if (per_sm < 1) continue;
+    const int64_t ctas = (ncols + nr - 1) / nr;
+    const int64_t waves = (ctas + (int64_t)sms * per_sm - 1) / ((int64_t)sms * per_sm);
+    const int64_t cost = ((ctas + sms - 1) / sms) * nr + waves;   // busiest SM's columns (+ a wave tie-break)
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = nr;
+    }
+  }
+  return best;
+}
+
+}  // namespace
+
 cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy, double2* T,
                              int64_t ldt) {
   const int64_t ncols = p->n - p->k;
   if (ncols <= 0) return cudaSuccess;
-  int nr = 0;
-  const size_t smem = rid_solve_smem_bytes(p->k, &nr);
-  if (smem > SOLVE_SMEM_BUDGET) return cudaErrorInvalidValue;
+  int nr_max = 0;
+  if (rid_solve_smem_bytes(p->k, &nr_max) > SOLVE_SMEM_BUDGET) return cudaErrorInvalidValue;
+  const int nr = solve_block_width(p->k, ncols, p->num_sms, nr_max);
+  const size_t smem = (size_t)(p->k * nr + p->k) * sizeof(double2);
   // one fixed limit for every plan: the attribute is process-wide, and plans
   // on other host threads launch this kernel concurrently
   cudaError_t e = cudaFuncSetAttribute(solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
