@@ -24,6 +24,11 @@ constexpr int BT_MAX_L = 128;
 constexpr int BT_MAX_K = 64;
 constexpr int BT_MAX_N = 4096;
 constexpr int BT_NR = 32;                  // right-hand sides per solve block
+// Omega drawn once per problem into the CTA's slice of the workspace when
+// l m is at most this many entries (2 MiB); larger problems draw each K chunk
+// where it is used.  The draw is a Philox block plus an FP64 log and sincospi
+// per entry, so drawing it once per column tile multiplied the FP64 work.
+constexpr int64_t BT_OMEGA_CAP = 131072;
 
 struct BatchItemDev {
   int64_t m, n;
@@ -48,6 +53,7 @@ struct BatchArgs {
   double* err_out;            // 2 per problem
   int32_t* status_out;        // per problem
   int ct;                     // sketch column tile: 16 or 32 (tuned)
+  double2* omega_ws;          // BT_OMEGA_CAP entries per CTA
 };
 
 __device__ __forceinline__ double warp_sum(double x) {
@@ -70,11 +76,20 @@ __device__ double block_sum(double x, double* red) {
 
 // ---- step 1: Y = Omega A, column tiles of ct, K chunks of BT_KC rows ------------------
 template <int CT>
-__device__ void batch_sketch(const BatchItemDev& it, double2* smem) {
+__device__ void batch_sketch(const BatchItemDev& it, double2* smem, double2* __restrict__ om) {
   const int l = it.l;
   const int64_t m = it.m, n = it.n;
   double2* As = smem;                                  // CT x (BT_KC + 1)
   double2* Os = smem + CT * (BT_KC + 1);               // l x (BT_KC + 1)
+  // Omega once, row-major l x m, into this CTA's workspace (when it fits)
+  const bool cached = (int64_t)l * m <= BT_OMEGA_CAP;
+  if (cached) {
+    for (int64_t e = threadIdx.x; e < (int64_t)l * m; e += BT_THREADS) {
+      const int64_t i = e / m, r = e - i * m;
+      om[e] = philox_complex_normal((uint64_t)i, (uint64_t)r, it.seed, RID_STREAM_OMEGA);
+    }
+    __syncthreads();
+  }
   constexpr int MAXE = (BT_MAX_L * CT + BT_THREADS - 1) / BT_THREADS;
   for (int64_t c0 = 0; c0 < n; c0 += CT) {
     double2 acc[MAXE];
@@ -91,7 +106,9 @@ __device__ void batch_sketch(const BatchItemDev& it, double2* smem) {
         const int i = e / BT_KC, rr = e % BT_KC;
         const int64_t gr = r0 + rr;
         Os[i * (BT_KC + 1) + rr] =
-            gr < m ? philox_complex_normal((uint64_t)i, (uint64_t)gr, it.seed, RID_STREAM_OMEGA) : make_double2(0.0, 0.0);
+            gr >= m ? make_double2(0.0, 0.0)
+                    : (cached ? om[i * m + gr]
+                              : philox_complex_normal((uint64_t)i, (uint64_t)gr, it.seed, RID_STREAM_OMEGA));
       }
       __syncthreads();
 #pragma unroll
@@ -378,7 +395,7 @@ __global__ void __launch_bounds__(BT_THREADS) batch_kernel(BatchArgs a) {
     if (t >= a.count) break;
     const BatchItemDev it = a.items[a.order[t]];
     const int pid = a.order[t];
-    batch_sketch<CT>(it, smem);
+    batch_sketch<CT>(it, smem, a.omega_ws + (int64_t)blockIdx.x * BT_OMEGA_CAP);
     // scratch of the later steps shares the sketch's shared memory
     double* nu = (double*)smem;                                   // n doubles
     double2* v = (double2*)(nu + BT_MAX_N);                        // l entries
@@ -413,13 +430,49 @@ size_t batch_smem_bytes(int ct) {
   return s;
 }
 
+// Resident CTAs of the persistent kernel for `tile`, at most `count`.  The
+// shared-memory attributes are fixed per tile, so setting them here before
+// the occupancy query never races and always gives the launch's answer.
+int batch_grid(int tile, int32_t count) {
+  cudaFuncSetAttribute(batch_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(16));
+  cudaFuncSetAttribute(batch_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem_bytes(32));
+  int dev_id = 0, sms = 0;
+  if (cudaGetDevice(&dev_id) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  const size_t smem = batch_smem_bytes(tile);
+  int per_sm = 1;
+  if (tile == 16)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16>, BT_THREADS, smem);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32>, BT_THREADS, smem);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm < count ? sms * per_sm : count;
+}
+
+int batch_grid_max(int32_t count) {
+  if (count == 0) return 0;
+  const int a = batch_grid(16, count), b = batch_grid(32, count);
+  if (a < 0 || b < 0) return -1;
+  return a > b ? a : b;
+}
+
+// The per-CTA Omega slices start after the descriptors, the order and the queue counter.
+size_t omega_offset(int32_t count) {
+  return ((size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)) + sizeof(unsigned) + 255) / 256 * 256;
+}
+
 }  // namespace
 
 extern "C" {
 
 rid_status rid_batch_workspace(int32_t count, size_t* bytes) {
   if (count < 0 || !bytes) return RID_EINVAL;
-  *bytes = (size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)) + 256;
+  const int grid = batch_grid_max(count);
+  if (grid < 0) return RID_ECUDA;
+  *bytes = omega_offset(count) + (size_t)grid * BT_OMEGA_CAP * sizeof(double2);
   return RID_OK;
 }
 
@@ -504,20 +557,13 @@ rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t probe_seed, 
   int32_t* d_order = (int32_t*)(ws + (size_t)count * sizeof(BatchItemDev));
   unsigned* d_next = (unsigned*)(ws + (size_t)count * (sizeof(BatchItemDev) + sizeof(int32_t)));
   if (cudaMemsetAsync(d_next, 0, sizeof(unsigned), s) != cudaSuccess) return RID_ECUDA;
-  int dev_id = 0, sms = 0;
-  if (cudaGetDevice(&dev_id) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev_id) != cudaSuccess)
-    return RID_ECUDA;
   const size_t smem = batch_smem_bytes(tile);
-  BatchArgs args{d_items, d_order, count, d_next, nprobe, probe_seed, err_out, status_out, tile};
-  // persistent grid: as many CTAs as can be resident at once
-  int per_sm = 1;
-  if (tile == 16)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<16>, BT_THREADS, smem);
-  else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_kernel<32>, BT_THREADS, smem);
-  if (per_sm < 1) per_sm = 1;
-  const int grid = sms * per_sm < count ? sms * per_sm : count;
+  BatchArgs args{d_items, d_order, count, d_next, nprobe, probe_seed, err_out, status_out, tile,
+                 (double2*)(ws + omega_offset(count))};
+  // persistent grid: as many CTAs as can be resident at once (the workspace
+  // holds an Omega slice for each)
+  const int grid = batch_grid(tile, count);
+  if (grid < 1) return RID_ECUDA;
   if (tile == 16)
     batch_kernel<16><<<grid, BT_THREADS, smem, s>>>(args);
   else
