@@ -343,6 +343,9 @@ def run_ours(args, cfg, world, rank, local):
         "config": workload_config(cfg, args),
         "roofline": roof,
         "id_roofline_frac": id_frac,
+        # algorithmic FP64 work of the whole ID: sketch (with the row probes), QR, solve, error
+        "gflops": world * (sketch_flops + 16.0 * n * (l * k - k * k / 2) + 4.0 * k * k * (n - k) +
+                           (8.0 * k * (n - k) * args.nprobe if rows else 8.0 * m * n * args.nprobe)) / (ms_step / 1e3) / 1e9,
         "step_ms": per,
         "sketch_kernel_ms": {"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2]},
         "gpu_launches": launches,
