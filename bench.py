@@ -426,10 +426,11 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     perm_h = torch.empty(cfg.n, dtype=torch.int32, pin_memory=True)
     T_h = torch.empty((cfg.n - cfg.k, cfg.k), dtype=torch.complex128, pin_memory=True).t()
     torch.cuda.synchronize()
-    rows = args.estimator == "rows" and args.mode in ("fp64", "fp64_emulated")
+    rows = args.estimator == "rows"
+    pipelined = rows and args.mode in ("fp64", "fp64_emulated")     # modes with column-range sketches
     n = cfg.n
     width = max(128, (n // 8 + 127) // 128 * 128)
-    panels = [(c0, min(width, n - c0)) for c0 in range(0, n, width)] if rows else [(0, n)]
+    panels = [(c0, min(width, n - c0)) for c0 in range(0, n, width)] if pipelined else [(0, n)]
     copy_stream = torch.cuda.Stream(A.device)
     landed = [torch.cuda.Event() for _ in panels]
     done = [torch.cuda.Event() for _ in panels]
@@ -449,7 +450,7 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     for step in range(args.e2e_steps):
         for i, (c0, nc) in enumerate(panels):
             stream.wait_event(landed[i])
-            if rows:
+            if pipelined:
                 plan.sketch_cols(A, Y, c0, nc)
             else:
                 plan.sketch(A, Y)
@@ -473,7 +474,8 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     return {"value": world * cfg.a_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": args.e2e_steps,
             "pipeline": (f"A in {len(panels)} column panels on a copy stream, overlapped with the sketch"
-                         if rows else "A copied whole, then the ID")}
+                         if pipelined else ("A copied whole; the next step's copy overlaps select, solve and "
+                                            "error" if rows else "A copied whole, then the ID"))}
 
 
 def compare_with_fp64(args, cfg, A, perm, T, stream, rank):
@@ -485,6 +487,9 @@ def compare_with_fp64(args, cfg, A, perm, T, stream, rank):
     m, n, k, l = cfg.m, cfg.n, cfg.k, cfg.l
     A128 = A.t().to(torch.complex128).t()
     plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, mode="fp64_emulated", stream=stream)
+    rows = args.estimator == "rows"
+    if rows:
+        plan.set_probes(args.nprobe, 1)
     Y = rid.colmajor_empty(l, n, device=A.device)
     perm2 = torch.empty(n, dtype=torch.int32, device=A.device)
     T2 = rid.colmajor_empty(k, n - k, device=A.device)
@@ -493,7 +498,7 @@ def compare_with_fp64(args, cfg, A, perm, T, stream, rank):
         plan.sketch(A128, Y)
         plan.select(Y, perm2)
         plan.solve(Y, T2)
-        return plan.error(A128, perm2, T2, args.nprobe, 1)
+        return plan.error_sketched(perm2, T2) if rows else plan.error(A128, perm2, T2, args.nprobe, 1)
 
     step()
     torch.cuda.synchronize()
@@ -676,8 +681,8 @@ def main():
     ap.add_argument("--omega-bits", type=int, default=0,
                     help="round the test matrix to this many bits below each row's maximum (0: unrounded)")
     ap.add_argument("--estimator", choices=("rows", "columns"), default=None,
-                    help="error estimate from row probes multiplied in the sketch (default for the FP64 modes) "
-                         "or from column probes in a second pass over A (default for bf16)")
+                    help="error estimate from row probes multiplied in the sketch's pass over A (default; FP64-grade "
+                         "in every mode) or from column probes in a second pass over A")
     ap.add_argument("--ref-cols", type=int, default=2048, help="column slab of the CPU oracle sample")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -689,9 +694,7 @@ def main():
     ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()
     if args.estimator is None:
-        args.estimator = "columns" if args.mode == "bf16" else "rows"
-    if args.estimator == "rows" and args.mode == "bf16":
-        ap.error("row probes need an FP64-grade sketch (--mode fp64 or fp64_emulated)")
+        args.estimator = "rows"
     import dataclasses
     import synth
     world, rank, local = init_dist()

@@ -192,8 +192,9 @@ RID_API rid_status rid_sketch_cols(rid_plan_t plan, const void* A, int64_t lda, 
  * Every later rid_sketch also computes X = G A (nprobe x n, plan memory) in
  * the same pass as Y = Omega A; Y is unchanged.  nprobe = 0 removes them.
  *   1 <= nprobe <= 16 and l + nprobe <= 512 (RID_EINVAL / RID_EUNSUPPORTED).
- *   Modes RID_FP64_NATIVE and RID_FP64_EMULATED only (RID_EUNSUPPORTED
- *   otherwise: an FP32-grade X cannot resolve an FP64-grade residual).
+ *   X is FP64-grade in every mode: RID_MIXED_BF16 plans multiply the probe
+ *   rows by the complex64 A (exact in FP64) on the FP64-emulated path while Y
+ *   takes the BF16x3 product, so their error estimate stays FP64.
  *   Allocates (l + nprobe) x m complex128 for Omega and G plus small buffers
  *   (RID_ENOMEM if that fails; the plan is then unchanged) and synchronizes
  *   the stream.  rid_plan_omega still returns the l rows of the test matrix. */

@@ -23,6 +23,10 @@ rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run);
 void rid_mx_plan_free(rid_plan_s* p);
 cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
 int rid_mx_error_word(const rid_plan_s* p);
+rid_status rid_tc_probe_init(rid_plan_s* p);
+void rid_tc_probe_free(rid_plan_s* p);
+cudaError_t rid_tc_probe_sketch(const rid_plan_s* p, const void* A, int64_t lda);
+int rid_tc_probe_error_word(const rid_plan_s* p);
 
 static rid_status rid_tc_plan_init(rid_plan_s* p) {
   if (p->mode == RID_FP64_EMULATED) return rid_tc_plan_init_fp64(p);
@@ -40,8 +44,14 @@ static cudaError_t rid_tc_sketch(const rid_plan_s* p, const void* A, int64_t lda
 }
 static int rid_tc_error_word(const rid_plan_s* p) {
   if (p->mode == RID_FP64_EMULATED) return rid_tc_error_word_fp64(p);
-  if (p->mode == RID_MIXED_BF16) return rid_mx_error_word(p);
+  if (p->mode == RID_MIXED_BF16) return rid_mx_error_word(p) | rid_tc_probe_error_word(p);
   return 0;
+}
+// The mixed mode's probe state follows the probe rows of Omega.
+static rid_status rid_probe_state_reset(rid_plan_s* p) {
+  rid_tc_probe_free(p);
+  if (p->mode == RID_MIXED_BF16 && p->nrow > 0) return rid_tc_probe_init(p);
+  return RID_OK;
 }
 
 namespace {
@@ -308,6 +318,7 @@ rid_status rid_plan_destroy(rid_plan_t p) {
   if (p->timing)
     for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
   rid_tc_plan_free(p);
+  rid_tc_probe_free(p);
   rid_dev_free(p->probe_base, p->stream);
   rid_dev_free(p->ws_base, p->stream);
   free(p);
@@ -364,13 +375,16 @@ rid_status rid_plan_round_omega(rid_plan_t p, int32_t bits) {
     rid_tc_plan_free(p);          // the tensor-core paths keep Omega in split form
     const rid_status s = rid_tc_plan_init(p);
     if (s != RID_OK) return s;
+    const rid_status ps = rid_probe_state_reset(p);
+    if (ps != RID_OK) return ps;
   }
   return from_cuda(cudaStreamSynchronize(p->stream));
 }
 
 rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
   if (!p || nprobe < 0 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
-  if (nprobe > 0 && p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED) return RID_EUNSUPPORTED;
+  if (nprobe > 0 && p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED && p->mode != RID_MIXED_BF16)
+    return RID_EUNSUPPORTED;
   if (p->l + nprobe > 512) return RID_EUNSUPPORTED;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
@@ -430,6 +444,8 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
     const rid_status s = rid_tc_plan_init(p);
     if (s != RID_OK) return s;
   }
+  const rid_status ps = rid_probe_state_reset(p);
+  if (ps != RID_OK) return ps;
   return from_cuda(cudaStreamSynchronize(p->stream));
 }
 
@@ -443,6 +459,7 @@ rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t
     e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy, 0, p->n);
   else
     e = rid_tc_sketch(p, A, lda, (double2*)Y, ldy);
+  if (e == cudaSuccess && p->mode == RID_MIXED_BF16 && p->nrow > 0) e = rid_tc_probe_sketch(p, A, lda);
   if (e == cudaSuccess && p->nrow > 0) p->x_valid = 1;
   return from_cuda(e);
 }
@@ -534,7 +551,7 @@ rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   out[2] = p->n > p->k ? 1 : 0;
   out[3] = p->n > p->k ? 6 : 5;
   out[4] = p->split_k;
-  out[5] = (int64_t)(p->ws_bytes + p->tc_bytes + p->probe_bytes);
+  out[5] = (int64_t)(p->ws_bytes + p->tc_bytes + p->probe_bytes + p->tc_probe_bytes);
   out[6] = p->mode;
   out[7] = p->dtype;
   return RID_OK;

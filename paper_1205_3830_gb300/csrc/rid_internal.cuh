@@ -75,6 +75,9 @@ struct rid_plan_s {
   // emulated / mixed sketch state (owned by the tensor-core path)
   void* tc_state;
   size_t tc_bytes;
+  // mixed-precision plans with row probes: the FP64-emulated state of the probe rows
+  void* tc_probe_state;
+  size_t tc_probe_bytes;
   int tc_sketch_launches;
 };
 

@@ -75,6 +75,8 @@ constexpr long long TC_WAIT_BUDGET = 4000000000ll;   // clock cycles (~2 s)
 
 struct TcState {
   int S;
+  int row0, nrows;        // the rows of Omega this state multiplies
+  bool a_c64;             // A is complex64 (converted exactly to FP64 before slicing)
   int nstages;            // pipeline stages that fit in shared memory
   uint32_t stage_smem, o_off, o_tile_smem;
   int dyn_smem;           // dynamic shared memory of the product kernel
@@ -245,7 +247,8 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 // One warp per (column j, chunk c): 128 complex rows = 256 real values; a
 // lane takes 4 consecutive complex rows, so every slice row is written with
 // one 16-byte store per lane.
-__global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict__ A, int64_t lda, int64_t m,
+template <typename TA>
+__global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, int64_t lda, int64_t m,
                                                       int64_t n, int NC, int64_t KP, int64_t slice_stride,
                                                       uint16_t* __restrict__ slices, int* __restrict__ a_exp,
                                                       int* __restrict__ a_exp_max) {
@@ -258,12 +261,17 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const double2* __restrict_
     const int64_t j = t / NC;
     const int c = (int)(t - j * NC);
     const int64_t r0 = (int64_t)c * 128 + 4 * lane;
-    const double2* col = A + j * lda;
+    const TA* col = A + j * lda;
     double2 x[4];
     int e = TC_EXP_ZERO;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      x[u] = r0 + u < m ? __ldcs(col + r0 + u) : make_double2(0.0, 0.0);
+      if (r0 + u < m) {
+        const TA v = __ldcs(col + r0 + u);
+        x[u] = make_double2((double)v.x, (double)v.y);     // exact for complex64 input
+      } else {
+        x[u] = make_double2(0.0, 0.0);
+      }
       e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
     }
     e = __reduce_max_sync(0xffffffffu, e);
@@ -625,17 +633,32 @@ void rid_tc_plan_free_fp64(rid_plan_s* p);
 
 // dry_run: compute p->tc_bytes (the device bytes the state needs) and return
 // without allocating or launching anything.
-rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
-  if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
+namespace {
+
+void tc_free_state(rid_plan_s* p, TcState* st) {
+  if (!st) return;
+  rid_dev_free(st->om_slices, p->stream);   // start of the single allocation, released in stream order
+  free(st);
+}
+
+// A tensor-core state for rows row0 .. row0 + nrows - 1 of Omega: their digit
+// planes, the A digit buffers, partial sums and tensor maps.  dry_run: only
+// the device bytes.
+rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64, TcState** out,
+                    size_t* bytes_out) {
+  *out = nullptr;
   TcState* st = (TcState*)calloc(1, sizeof(TcState));
   if (!st) return RID_ENOMEM;
   st->S = TC_S;
+  st->row0 = row0;
+  st->nrows = nrows;
+  st->a_c64 = a_c64;
   // a rounded Omega holds omega_bits / 8 digits relative to its row exponent,
   // the same exponent omega_exp_kernel takes, so the others are exactly zero
   st->so = p->omega_bits > 0 ? (p->omega_bits + 7) / 8 : TC_S;
   st->NC = (int)((2 * p->m + TC_KC - 1) / TC_KC);
   st->KP = (int64_t)st->NC * TC_KC;
-  st->l2 = 2 * p->ls;         // the test matrix and the row probes
+  st->l2 = 2 * nrows;
   st->ntiles = (st->l2 + 127) / 128;
   st->tile_w = ((st->l2 + st->ntiles - 1) / st->ntiles + 15) / 16 * 16;
   st->l2p = st->ntiles * st->tile_w;
@@ -693,8 +716,8 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
   const size_t total = al(om_bytes) + al(a_bytes) + al(aexp_bytes) + al((size_t)p->n * 4) +
                        al((size_t)st->l2 * 4) + al(part_bytes) + al(4);
+  *bytes_out = total;
   if (dry_run) {
-    p->tc_bytes = total;
     free(st);
     return RID_OK;
   }
@@ -712,25 +735,22 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   st->om_exp = (int*)take((size_t)st->l2 * 4);
   st->partial = (float2*)take(part_bytes);
   st->err = (int*)take(4);
-  p->tc_state = st;
-  p->tc_bytes = total;
-  p->tc_sketch_launches = 3;
 
   if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S, 128) ||
       make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S, st->tile_w)) {
-    rid_tc_plan_free_fp64(p);
+    tc_free_state(p, st);
     return RID_ECUDA;
   }
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
   if (e == cudaSuccess) {
-    omega_exp_kernel<<<p->ls, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, st->om_exp);
+    omega_exp_kernel<<<nrows, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m, st->om_exp);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) {
-    int64_t blocks = ((int64_t)p->ls * (st->KP / 2) + 255) / 256;
+    int64_t blocks = ((int64_t)nrows * (st->KP / 2) + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega, p->ldo, p->m, p->ls, st->KP,
-                                                                 st->om_exp, st->om_slices);
+    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m,
+                                                                 nrows, st->KP, st->om_exp, st->om_slices);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
@@ -742,36 +762,71 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, sketch_tc_kernel);
     if (e == cudaSuccess && fa.numRegs != TC_LAUNCH_REGS) {
-      rid_tc_plan_free_fp64(p);
+      tc_free_state(p, st);
       return RID_EUNSUPPORTED;
     }
   }
   if (e != cudaSuccess) {
-    rid_tc_plan_free_fp64(p);
+    tc_free_state(p, st);
     return RID_ECUDA;
+  }
+  *out = st;
+  return RID_OK;
+}
+
+}  // namespace
+
+rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
+  if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
+  TcState* st = nullptr;
+  size_t bytes = 0;
+  const rid_status s = tc_setup(p, dry_run, 0, p->ls, false, &st, &bytes);   // the test matrix and the row probes
+  if (s != RID_OK) return s;
+  p->tc_bytes = bytes;
+  if (!dry_run) {
+    p->tc_state = st;
+    p->tc_sketch_launches = 3;
   }
   return RID_OK;
 }
 
 void rid_tc_plan_free_fp64(rid_plan_s* p) {
-  TcState* st = (TcState*)p->tc_state;
-  if (!st) return;
-  rid_dev_free(st->om_slices, p->stream);   // start of the single allocation, released in stream order
-  free(st);
+  tc_free_state(p, (TcState*)p->tc_state);
   p->tc_state = nullptr;
   p->tc_bytes = 0;
 }
 
-// Columns col0 .. col0 + ncols - 1 of the sketch (col0 a multiple of 128).  The
-// K-split is the plan's, so any set of column ranges gives the same Y as one
-// call over all columns.
-cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy,
-                                    int64_t col0, int64_t ncols) {
-  const TcState* st = (const TcState*)p->tc_state;
+// Mixed-precision plans with row probes: an FP64-emulated state for the probe
+// rows alone, multiplied into X from the complex64 A (exact in FP64), so the
+// error estimate keeps FP64 grade while Y takes the BF16x3 product.
+rid_status rid_tc_probe_init(rid_plan_s* p) {
+  TcState* st = nullptr;
+  size_t bytes = 0;
+  const rid_status s = tc_setup(p, 0, p->l, p->nrow, p->dtype == RID_C64, &st, &bytes);
+  if (s != RID_OK) return s;
+  p->tc_probe_state = st;
+  p->tc_probe_bytes = bytes;
+  return RID_OK;
+}
+
+void rid_tc_probe_free(rid_plan_s* p) {
+  tc_free_state(p, (TcState*)p->tc_probe_state);
+  p->tc_probe_state = nullptr;
+  p->tc_probe_bytes = 0;
+}
+
+namespace {
+
+// Columns col0 .. col0 + ncols - 1 (col0 a multiple of 128) of the product of
+// the state's rows of Omega with A: rows below ly go to Y, the others to X.
+// The K-split is the state's, so any set of column ranges gives the same
+// result as one call over all columns.
+cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, int64_t lda, double2* Y, int64_t ldy,
+                      int ly, double2* X, int64_t ldx, int64_t col0, int64_t ncols, bool timing) {
   if (!st) return cudaErrorNotSupported;
   if (ncols <= 0) return cudaSuccess;
-  const double2* A = (const double2*)A_;
-  if (p->timing) cudaEventRecord(p->ev[0], p->stream);
+  timing = timing && p->timing;
+  if (timing) cudaEventRecord(p->ev[0], p->stream);
   // 0x80808080 is below every exponent: the running maximum starts there
   cudaError_t e = cudaMemsetAsync(st->a_exp_max + col0, 0x80, (size_t)ncols * 4, p->stream);
   if (e != cudaSuccess) return e;
@@ -779,12 +834,17 @@ cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A_, int64_t
     const int64_t tasks = ncols * (int64_t)st->NC;
     int64_t blocks = (tasks * 32 + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
-    a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A + col0 * lda, lda, p->m, ncols, st->NC, st->KP,
-                                                             p->n * st->KP, st->a_slices + col0 * st->KP,
-                                                             st->a_exp + col0 * st->NC, st->a_exp_max + col0);
+    if (st->a_c64)
+      a_slice_kernel<float2><<<(unsigned)blocks, 256, 0, p->stream>>>(
+          (const float2*)A_ + col0 * lda, lda, p->m, ncols, st->NC, st->KP, p->n * st->KP,
+          st->a_slices + col0 * st->KP, st->a_exp + col0 * st->NC, st->a_exp_max + col0);
+    else
+      a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
+          (const double2*)A_ + col0 * lda, lda, p->m, ncols, st->NC, st->KP, p->n * st->KP,
+          st->a_slices + col0 * st->KP, st->a_exp + col0 * st->NC, st->a_exp_max + col0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (p->timing) cudaEventRecord(p->ev[1], p->stream);
+  if (timing) cudaEventRecord(p->ev[1], p->stream);
   const int jb0 = (int)(col0 / 128);
   const int nblocks = (int)((ncols + 127) / 128);
   TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
@@ -807,31 +867,49 @@ cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A_, int64_t
     e = cudaLaunchKernelEx(&cfg, sketch_tc_kernel, st->map_a, st->map_om, args);
     if (e != cudaSuccess) return e;
   }
-  if (p->timing) cudaEventRecord(p->ev[2], p->stream);
+  if (timing) cudaEventRecord(p->ev[2], p->stream);
   {
-    const int64_t total = ncols * (int64_t)p->ls;
+    const int64_t total = ncols * (int64_t)st->nrows;
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->ls, st->l2p,
-                                                               st->om_exp, st->a_exp_max, Y, ldy, p->l, p->xrow,
-                                                               p->nrow > 0 ? p->nrow : 1, col0, ncols);
+    tc_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, st->nrows, st->l2p,
+                                                               st->om_exp, st->a_exp_max, Y, ldy, ly, X, ldx, col0,
+                                                               ncols);
     e = cudaGetLastError();
   }
-  if (p->timing) cudaEventRecord(p->ev[3], p->stream);
+  if (timing) cudaEventRecord(p->ev[3], p->stream);
   return e;
+}
+
+}  // namespace
+
+cudaError_t rid_tc_sketch_cols_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy,
+                                    int64_t col0, int64_t ncols) {
+  return tc_sketch(p, (const TcState*)p->tc_state, A_, lda, Y, ldy, p->l, p->xrow, p->nrow > 0 ? p->nrow : 1, col0,
+                   ncols, true);
 }
 
 cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
   return rid_tc_sketch_cols_fp64(p, A_, lda, Y, ldy, 0, p->n);
 }
 
-int rid_tc_error_word_fp64(const rid_plan_s* p) {
-  const TcState* st = (const TcState*)p->tc_state;
+// X = G A for a mixed-precision plan's row probes (every row goes to X).
+cudaError_t rid_tc_probe_sketch(const rid_plan_s* p, const void* A_, int64_t lda) {
+  return tc_sketch(p, (const TcState*)p->tc_probe_state, A_, lda, nullptr, 0, 0, p->xrow, p->nrow, 0, p->n, false);
+}
+
+namespace {
+int state_error_word(const rid_plan_s* p, const TcState* st) {
   if (!st) return 0;
   int h = 0;
   cudaMemcpyAsync(&h, st->err, 4, cudaMemcpyDeviceToHost, p->stream);
   cudaStreamSynchronize(p->stream);
   return h;
 }
+}  // namespace
+
+int rid_tc_error_word_fp64(const rid_plan_s* p) { return state_error_word(p, (const TcState*)p->tc_state); }
+
+int rid_tc_probe_error_word(const rid_plan_s* p) { return state_error_word(p, (const TcState*)p->tc_probe_state); }
 
 rid_status rid_tc_plan_init_fp64(rid_plan_s* p) { return rid_tc_plan_setup_fp64(p, 0); }

@@ -13,7 +13,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import U64, to_dev_colmajor, to_host
+from gpu_util import U64, row_probe_tolerances, to_dev_colmajor, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -77,3 +77,26 @@ def test_mixed_error_estimate_is_fp64(rid):
     w_abs[out["perm"][:k]] = np.abs(out["T"]) @ np.abs(omega[out["perm"][k:]])
     bound = 4 * (n + k) * U64 * np.linalg.norm(np.abs(A128) @ w_abs, axis=0)
     assert abs(est - est_o) <= np.max(bound / np.linalg.norm(omega, axis=0)) + 1e-13 * est_o
+
+
+@pytest.mark.parametrize("shape", [(4096, 600, 20, 30), (1000, 777, 17, 27)], ids=str)
+def test_mixed_row_probe_estimate_is_fp64(rid, shape):
+    """Row probes on a mixed plan: Y takes the BF16x3 product, X = G A the
+    FP64-emulated one on the complex64 A (exact in FP64), so the estimate
+    meets the FP64 row-probe bound against the oracle on the upcast A."""
+    m, n, k, l = shape
+    A = c64_lowrank(m, n, k)
+    with rid.Plan(m, n, k, l, seed=4, dtype=torch.complex64, mode="bf16") as plan:
+        plan.set_probes(8, 6)
+        Y = plan.sketch(to_dev_colmajor(A, torch.complex64))
+        perm = plan.select(Y)
+        T = plan.solve(Y)
+        est, up = plan.error_sketched(perm, T)
+    A128 = A.astype(np.complex128)
+    perm_h, T_h = to_host(perm), to_host(T)
+    G = oracle.left_probe_matrix(8, m, 6)
+    est_o, up_o, _ = oracle.error_estimate_left(A128, perm_h, T_h, G)
+    tol_est, tol_up = row_probe_tolerances(A128, perm_h, T_h, G, "fp64_emulated")
+    assert abs(est - est_o) <= tol_est + 1e-14 * est_o
+    assert abs(up - up_o) <= tol_up + 1e-14 * up_o
+    assert est_o > 100 * tol_est

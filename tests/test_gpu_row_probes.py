@@ -155,8 +155,10 @@ def test_row_probe_argument_errors(rid):
         with pytest.raises(RIDError, match="EUNSUPPORTED"):
             plan.set_probes(13, 1)                   # l + nprobe > 512
     with rid.Plan(m, n, k, l, seed=1, dtype=torch.complex64, mode="bf16") as plan:
+        plan.set_probes(4, 1)                        # mixed plans take FP64-grade row probes too
         with pytest.raises(RIDError, match="EUNSUPPORTED"):
-            plan.set_probes(4, 1)
+            plan.sketch_cols(torch.zeros((n, m), dtype=torch.complex64, device="cuda").t(),
+                             rid.colmajor_empty(l, n), 0, n)
 
 
 @pytest.mark.parametrize("mode", MODES)
