@@ -211,8 +211,9 @@ def workload_config(cfg, args):
     return {"workload": f"{cfg.name}: {ctype} {kind}, m={cfg.m}, n={cfg.n}, k={cfg.k}, l={cfg.l}, "
                         f"{cfg.a_bytes / 2**30:.0f} GiB",
             "m": cfg.m, "n": cfg.n, "k": cfg.k, "l": cfg.l, "nprobe": args.nprobe, "mode": args.mode, "estimator": args.estimator,
-            "omega": ("complex Gaussian (FP64)" if not args.omega_bits else
-                      f"complex Gaussian rounded to {args.omega_bits} bits below each row's maximum"),
+            "omega": (("subsampled randomized Fourier transform S F D" if args.omega == "srft" else "complex Gaussian")
+                      + (" (FP64)" if not args.omega_bits else
+                         f" rounded to {args.omega_bits} bits below each row's maximum")),
             "l2": "inputs larger than L2 (A is %.0f GiB, L2 129 MB)" % (cfg.a_bytes / 2**30)}
 
 
@@ -237,6 +238,8 @@ def run_ours(args, cfg, world, rank, local):
     rows = args.estimator == "rows"
     if rows:
         plan.set_probes(args.nprobe, 1)       # the error's products ride along in the sketch
+    if args.omega == "srft":
+        plan.use_srft(cfg.seed + 1)           # the paper's S F D in place of the Gaussian rows
     if args.omega_bits:
         plan.round_omega(args.omega_bits)     # Omega (and the probes) rounded: bits / 8 digits
     Y = rid.colmajor_empty(l, n, device=dev)
@@ -356,7 +359,7 @@ def run_ours(args, cfg, world, rank, local):
         "clocks": clocks,
     }
 
-    if args.mode == "fp64_emulated" and not args.omega_bits and args.rounded_variant:
+    if args.mode == "fp64_emulated" and not args.omega_bits and args.omega == "gaussian" and args.rounded_variant:
         line["omega_rounded_24bit"] = time_rounded_omega(args, cfg, A, stream, world, rank)
     if args.e2e_steps > 0:
         line["e2e"] = run_e2e(args, cfg, plan, A, Y, perm, T, stream, world)
@@ -678,6 +681,8 @@ def main():
     ap.add_argument("--nprobe", type=int, default=8)
     ap.add_argument("--no-rounded-variant", dest="rounded_variant", action="store_false",
                     help="skip the secondary measurement with a 24-bit rounded test matrix")
+    ap.add_argument("--omega", choices=("gaussian", "srft"), default="gaussian",
+                    help="test matrix: complex Gaussian or the paper's subsampled randomized Fourier transform")
     ap.add_argument("--omega-bits", type=int, default=0,
                     help="round the test matrix to this many bits below each row's maximum (0: unrounded)")
     ap.add_argument("--estimator", choices=("rows", "columns"), default=None,
