@@ -551,7 +551,10 @@ def device_lowrank(m, n, rank, eps, gen, device):
 
 def run_batched(args, world, rank, local):
     """4096 independent complex128 IDs (m, n ~ U[64, 1024], k ~ U[4, 64],
-    l = k + 8, A = X Y + 1e-10 N) per step, in one persistent launch."""
+    l = k + 8, A = X Y + 1e-10 N) per step.  Timed: the tensor-core batch (one
+    FP64-emulated plan per problem, all sketches in one CUDA graph, then one
+    persistent launch of select, solve and the row-probe error); beside it the
+    FP64 persistent batch (one launch, CUDA graph) and the plan path."""
     import torch
     import synth
     import paper_1205_3830_gb300 as rid
@@ -563,12 +566,11 @@ def run_batched(args, world, rank, local):
     gen = torch.Generator(device=dev)
     gen.manual_seed(synth.MASTER_SEED + 4 + rank)
     problems = [(device_lowrank(m, n, k, 1e-10, gen, dev), k, l, 1000 + i) for i, (m, n, k, l) in enumerate(shapes)]
-    batch = rid.Batch(problems, nprobe=args.nprobe, probe_seed=1)
-    tile, _ = batch.autotune()
-    batch.capture(tile)                       # one CUDA graph: queue reset + the persistent launch
+    r = args.nprobe
     stream = torch.cuda.current_stream(dev)
+    tcb = rid.BatchTC(problems, nprobe=r, probe_seed=1)
     for _ in range(args.warmup):
-        batch.replay()
+        tcb.run()
     barrier(world)
     torch.cuda.synchronize()
     sampler = ClockSampler(local)
@@ -576,22 +578,55 @@ def run_batched(args, world, rank, local):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        batch.replay()
+        tcb.run()
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), world) / args.steps
-    res = batch.results()
+    sketch_ms, post_ms = tcb.times()
+    res = tcb.results()
+    ok = int(sum(1 for x in res if x["status"] == 0))
+    tcb.close()
+    del tcb
+    torch.cuda.synchronize()
+
     a_bytes = sum(16.0 * m * n for (m, n, k, l) in shapes)
-    flops = sum(8.0 * l * m * n + 8.0 * m * n * args.nprobe + 16.0 * n * (l * k - k * k / 2) + 4.0 * k * k * (n - k)
-                for (m, n, k, l) in shapes)
-    achieved = flops / (ms / 1e3) / 1e12
+    pair_flops = sum(28 * 2.0 * (2 * (l + r)) * (2 * m) * n for (m, n, k, l) in shapes)
+    post_flops = sum(16.0 * n * (l * k - k * k / 2) + 4.0 * k * k * (n - k) + 8.0 * k * (n - k) * r
+                     for (m, n, k, l) in shapes)
+    peaks = measured_peaks()
+    bf16_sust = float(peaks.get("bf16_tflops_sustained", 1724.5))
+    tc_roof = {"bound": "tensor", "achieved": pair_flops / (sketch_ms / 1e3) / 1e12, "peak": bf16_sust,
+               "unit": "TFLOP/s", "traffic": None, "kernel": "sketch_tc_kernel (all problems, with slicing)",
+               "per_launch": "28 digit pairs x 2 x 2(l + r) x 2m x n per problem; time of the whole sketch phase",
+               "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops_sustained"}
+    tc_roof["frac"] = tc_roof["achieved"] / bf16_sust
+    post_roof = {"bound": "alu", "achieved": post_flops / (post_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                 "unit": "TFLOP/s", "traffic": None, "kernel": "batch_post_kernel",
+                 "per_launch": "sum over problems of QR 16n(lk - k^2/2) + solve 4k^2(n-k) + error 8k(n-k)r flops"}
+    post_roof["frac"] = post_roof["achieved"] / FP64_PEAK_TFLOPS
+    dominant, other = (post_roof, tc_roof) if post_ms >= sketch_ms else (tc_roof, post_roof)
+
+    # the FP64 persistent batch (one launch, captured in a CUDA graph)
+    batch = rid.Batch(problems, nprobe=r, probe_seed=1)
+    tile, _ = batch.autotune()
+    batch.capture(tile)
+    batch.replay()
+    torch.cuda.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for _ in range(2):
+        batch.replay()
+    f1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = f0.elapsed_time(f1) / 2
+    del batch
     # the plain FP64 GPU path on the same inputs: one plan per problem, in turn
     sub = min(64, len(problems))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for (A, k, l, sd) in problems[:sub]:
-        rid.decompose(A, k, l, seed=sd, mode="fp64", nprobe=args.nprobe, probe_seed=1)
+        rid.decompose(A, k, l, seed=sd, mode="fp64", nprobe=r, probe_seed=1)
     torch.cuda.synchronize()
     plan_ids_s = sub / (time.perf_counter() - t0)
     line = {
@@ -600,14 +635,18 @@ def run_batched(args, world, rank, local):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded, generated on the device)",
         "config": {"workload": f"batched: {len(shapes)} complex128 IDs, m, n ~ U[64, 1024], k ~ U[4, 64], l = k + 8, "
                                f"A = X Y + 1e-10 N ({a_bytes / 2**30:.1f} GiB in all)",
-                   "count": len(shapes), "nprobe": args.nprobe, "tile": tile, "cuda_graph": True,
-                   "l2": "inputs larger than L2 (%.1f GiB)" % (a_bytes / 2**30)},
+                   "count": len(shapes), "nprobe": r, "estimator": "rows",
+                   "path": "tensor-core batch: FP64-emulated plan per problem, sketches in one CUDA graph "
+                           "(32 branches), one persistent launch of select / solve / error",
+                   "cuda_graph": True, "l2": "inputs larger than L2 (%.1f GiB)" % (a_bytes / 2**30)},
         "ids_per_s": world * len(shapes) / (ms / 1e3),
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "batch_kernel",
-                     "per_launch": "sum over problems of 8lmn + 8mnr + QR + solve flops"},
-        "gpu_launches": args.steps,
-        "ranks_ok": int(sum(1 for r in res if r["status"] == 0)),
+        "phase_ms": {"sketches": sketch_ms, "select_solve_error": post_ms},
+        "roofline": dominant,
+        "roofline_other_phase": other,
+        "gpu_launches": args.steps * (3 * len(shapes) + 1),
+        "ranks_ok": ok,
+        "vs_fp64_batch": {"ids_per_s": world * len(shapes) / (fp64_ms / 1e3), "ms_per_step": fp64_ms, "tile": tile,
+                          "path": "one persistent FP64 launch (CTA per problem), CUDA graph"},
         "vs_fp64_plan_path": {"ids_per_s": plan_ids_s, "problems_timed": sub,
                               "accuracy": "same J, T within 1e-12 (tests/test_gpu_batched.py)"},
         "clocks": clocks,

@@ -301,6 +301,30 @@ RID_API rid_status rid_batch_prepare(const rid_batch_item* items, int32_t count,
 RID_API rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t probe_seed, int32_t tile,
                                     double* err_out, int32_t* status_out, void* workspace, void* stream);
 
+/* Batches on the tensor cores.  rid_batch_tc_create gives every problem its
+ * own RID_FP64_EMULATED plan with nprobe row probes (probe_seed), then records,
+ * once, a CUDA graph of every plan's sketch (Y = Omega A and X = G A, the
+ * problems spread over 32 concurrent branch streams, largest first) followed
+ * by one persistent launch that runs the pivoted QR, the solve and the
+ * row-probe error estimate (as rid_error_sketched) of every problem, writing
+ * err_out (device, double[2 count]) and status_out (device, int32[count]) as
+ * rid_batch_run does.  Items and their limits as for rid_batch_run, plus
+ * l + nprobe <= 512; A, Y and T 16-byte aligned.  The items' pointers and
+ * err_out / status_out must stay valid for the handle's life.  Plan memory is
+ * about the sum of rid_plan_footprint over the problems.  Creating
+ * synchronizes `stream`; rid_batch_tc_run launches the graph on `stream`
+ * (asynchronous).  The results equal those of the problems' own plans with
+ * rid_error_sketched, up to the rounding order of the QR. */
+typedef struct rid_batch_plan_s* rid_batch_plan_t;
+RID_API rid_status rid_batch_tc_create(rid_batch_plan_t* plan, const rid_batch_item* items, int32_t count,
+                                       int32_t nprobe, uint64_t probe_seed, double* err_out, int32_t* status_out,
+                                       void* stream);
+RID_API rid_status rid_batch_tc_run(rid_batch_plan_t plan, void* stream);
+/* Milliseconds of the last run: out[0] the sketches (all branches), out[1]
+ * the finishing launch (HOST double[2]); waits for that run to end. */
+RID_API rid_status rid_batch_tc_times(rid_batch_plan_t plan, double out[2]);
+RID_API rid_status rid_batch_tc_destroy(rid_batch_plan_t plan);
+
 /* Static, human-readable name of a status code. */
 RID_API const char* rid_status_string(rid_status status);
 

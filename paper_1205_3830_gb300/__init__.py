@@ -329,6 +329,73 @@ class Batch:
         return out
 
 
+class BatchTC:
+    """Many complex128 IDs on the tensor cores: one FP64-emulated plan per
+    problem with nprobe row probes, every sketch captured once in a CUDA graph
+    (concurrent branches), then one persistent launch of select, solve and the
+    row-probe error for all problems (rid_batch_tc_*).
+
+    problems: list of (A, k, l, seed) as for Batch.  run() replays the graph on
+    the current stream; results() as for Batch.
+    """
+
+    def __init__(self, problems, nprobe=8, probe_seed=1, device=None):
+        self._lib = _native.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self.nprobe, self.probe_seed = int(nprobe), int(probe_seed)
+        self.Y, self.perm, self.T, self.A = [], [], [], []
+        items = (_native.BatchItem * len(problems))()
+        for i, (A, k, l, seed) in enumerate(problems):
+            assert A.is_cuda and A.dtype == torch.complex128 and A.stride(0) == 1
+            m, n = A.shape
+            Y = colmajor_empty(l, n, device=self.device)
+            perm = torch.empty(n, dtype=torch.int32, device=self.device)
+            T = colmajor_empty(k, n - k, device=self.device)
+            self.A.append(A), self.Y.append(Y), self.perm.append(perm), self.T.append(T)
+            it = items[i]
+            it.m, it.n, it.k, it.l = m, n, int(k), int(l)
+            it.A, it.lda = A.data_ptr(), _ld(A)
+            it.Y, it.ldy = Y.data_ptr(), _ld(Y)
+            it.perm = perm.data_ptr()
+            it.T, it.ldt = (T.data_ptr() if T.numel() else 0), max(_ld(T), int(k))
+            it.seed = int(seed) & (2 ** 64 - 1)
+        self.items = items
+        self.count = len(problems)
+        self.err = torch.empty(2 * max(1, self.count), dtype=torch.float64, device=self.device)
+        self.status = torch.empty(max(1, self.count), dtype=torch.int32, device=self.device)
+        self._h = ctypes.c_void_p()
+        stream = torch.cuda.current_stream(self.device)
+        check(self._lib.rid_batch_tc_create(ctypes.byref(self._h), ctypes.byref(self.items), self.count,
+                                            self.nprobe, self.probe_seed & (2 ** 64 - 1),
+                                            ctypes.c_void_p(self.err.data_ptr()),
+                                            ctypes.c_void_p(self.status.data_ptr()),
+                                            ctypes.c_void_p(stream.cuda_stream)), "rid_batch_tc_create")
+
+    def run(self, stream=None):
+        stream = stream or torch.cuda.current_stream(self.device)
+        check(self._lib.rid_batch_tc_run(self._h, ctypes.c_void_p(stream.cuda_stream)), "rid_batch_tc_run")
+        return self
+
+    results = Batch.results
+
+    def times(self):
+        """(sketch ms, finishing ms) of the last run (waits for it)."""
+        out = (ctypes.c_double * 2)()
+        check(self._lib.rid_batch_tc_times(self._h, out), "rid_batch_tc_times")
+        return float(out[0]), float(out[1])
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rid_batch_tc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def batch_decompose(problems, nprobe=8, probe_seed=1, tile=None):
     """Run a list of (A, k, l, seed) problems as one batch; returns Batch.results()."""
     return Batch(problems, nprobe, probe_seed).run(tile).results()

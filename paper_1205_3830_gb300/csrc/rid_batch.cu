@@ -221,28 +221,38 @@ __device__ int batch_select(const BatchItemDev& it, double2* tau, double* nu, do
     for (int i = j + 1 + threadIdx.x; i < l; i += BT_THREADS)
       if (scale.x != 0.0 || scale.y != 0.0) colj[i] = cmul(colj[i], scale);
     __syncthreads();
-    // v = (1, Y(j+1:, j)); apply H^H to columns j+1..n-1, then their new norms
+    // v = (1, Y(j+1:, j)); apply H^H to columns j+1..n-1, then their new norms.
+    // One thread per column: the columns are short (l <= 128), so warp-wide
+    // sums would cost more FP64 additions than the products themselves.
     for (int i = threadIdx.x; i < l - j; i += BT_THREADS) v[i] = i == 0 ? make_double2(1.0, 0.0) : colj[j + i];
     __syncthreads();
     const double2 ctau = make_double2(tau[j].x, -tau[j].y);
-    for (int64_t c = j + 1 + warp; c < n; c += BT_WARPS) {
+    const int rows = l - j;
+    for (int64_t c = j + 1 + threadIdx.x; c < n; c += BT_THREADS) {
       double2* col = it.Y + c * it.ldy + j;
-      double2 w = make_double2(0.0, 0.0);
-      for (int i = lane; i < l - j; i += 32) w = cfma_conj(v[i], col[i], w);
-      w.x = warp_sum(w.x);
-      w.y = warp_sum(w.y);
-      const double2 s = cmul(ctau, w);
-      double nn = 0.0;
-      for (int i = lane; i < l - j; i += 32) {
-        const double2 vs = cmul(v[i], s);
-        double2 x = col[i];
-        x.x -= vs.x;
-        x.y -= vs.y;
-        col[i] = x;
-        if (i > 0) nn += cabs2(x);
+      double2 w0 = make_double2(0.0, 0.0), w1 = make_double2(0.0, 0.0);
+      int i = 0;
+      for (; i + 1 < rows; i += 2) {
+        w0 = cfma_conj(v[i], col[i], w0);
+        w1 = cfma_conj(v[i + 1], col[i + 1], w1);
       }
-      nn = warp_sum(nn);
-      if (lane == 0) nu[c] = nn;
+      if (i < rows) w0 = cfma_conj(v[i], col[i], w0);
+      const double2 s = cmul(ctau, make_double2(w0.x + w1.x, w0.y + w1.y));
+      double nr = 0.0, ni = 0.0;
+      for (i = 0; i < rows; ++i) {
+        const double2 vi = v[i];
+        double2 x = col[i];
+        x.x = fma(-vi.x, s.x, x.x);
+        x.x = fma(vi.y, s.y, x.x);
+        x.y = fma(-vi.x, s.y, x.y);
+        x.y = fma(-vi.y, s.x, x.y);
+        col[i] = x;
+        if (i > 0) {
+          nr = fma(x.x, x.x, nr);
+          ni = fma(x.y, x.y, ni);
+        }
+      }
+      nu[c] = nr + ni;
     }
     __syncthreads();
   }
@@ -417,6 +427,130 @@ __global__ void __launch_bounds__(BT_THREADS) batch_kernel(BatchArgs a) {
   }
 }
 
+// ---- the tensor-core batch: select, solve and the row-probe error after the sketches ----
+// Each problem's Y and X = G A come from its own FP64-emulated plan (captured
+// in one CUDA graph); this persistent kernel finishes every problem.
+struct PostItemDev {
+  const double2* X;            // r x n, column-major, ld r: the row probes' products
+  const double* g_norm2;       // r: ||g_q||^2
+};
+
+struct PostArgs {
+  const BatchItemDev* items;
+  const PostItemDev* post;
+  const int32_t* order;
+  int count;
+  unsigned* next;
+  int r;
+  double* err_out;
+  int32_t* status_out;
+};
+
+// (g_q E)(perm[k+i]) = X(q, perm[k+i]) - sum_a X(q, perm[a]) T(a, i): one warp
+// per column of T, lanes over a, fixed-order sums; est / upper as rid_error_sketched.
+__device__ void batch_error_rows(const BatchItemDev& it, const PostItemDev& pi, int r, double2* xj, double* red,
+                                 double* out) {
+  __shared__ double wsum[BT_WARPS][RID_MAX_PROBES];
+  const int k = it.k;
+  const int64_t ncols = it.n - k;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int e = threadIdx.x; e < k * r; e += BT_THREADS) {
+    const int q = e / k, a = e - q * k;
+    xj[e] = pi.X[q + (int64_t)it.perm[a] * r];          // xj[q * k + a] = X(q, perm[a])
+  }
+  __syncthreads();
+  // one thread per column of T (k <= 64: the sums stay in the thread)
+  double sq[RID_MAX_PROBES];
+#pragma unroll
+  for (int q = 0; q < RID_MAX_PROBES; ++q) sq[q] = 0.0;
+  for (int64_t i = threadIdx.x; i < ncols; i += BT_THREADS) {
+    double2 acc[RID_MAX_PROBES];
+#pragma unroll
+    for (int q = 0; q < RID_MAX_PROBES; ++q) acc[q] = make_double2(0.0, 0.0);
+    const double2* Ti = it.T + i * it.ldt;
+    for (int a = 0; a < k; ++a) {
+      const double2 t = Ti[a];
+#pragma unroll
+      for (int q = 0; q < RID_MAX_PROBES; ++q)
+        if (q < r) acc[q] = cfma(xj[q * k + a], t, acc[q]);
+    }
+    const int64_t col = it.perm[k + i];
+#pragma unroll
+    for (int q = 0; q < RID_MAX_PROBES; ++q) {
+      if (q < r) {
+        const double2 x = pi.X[q + col * r];
+        sq[q] += cabs2(make_double2(x.x - acc[q].x, x.y - acc[q].y));
+      }
+    }
+  }
+  // fixed-order sums: over the warp, then over the warps
+#pragma unroll
+  for (int q = 0; q < RID_MAX_PROBES; ++q) {
+    double v = sq[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    sq[q] = v;
+  }
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < RID_MAX_PROBES; ++q) wsum[warp][q] = sq[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double est = 0.0, zmax = 0.0;
+    for (int q = 0; q < r; ++q) {
+      double s2 = 0.0;
+      for (int w = 0; w < BT_WARPS; ++w) s2 += wsum[w][q];
+      const double zn = sqrt(s2);
+      const double ratio = zn / sqrt(pi.g_norm2[q]);
+      if (ratio > est) est = ratio;
+      if (zn > zmax) zmax = zn;
+    }
+    out[0] = est;
+    out[1] = 10.0 * sqrt(0.63661977236758134308 /* 2 / pi */) * zmax;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(BT_THREADS) batch_post_kernel(PostArgs a) {
+  extern __shared__ double2 smem[];
+  __shared__ double red[BT_WARPS];
+  __shared__ int s_task;
+  __shared__ double2 tau[BT_MAX_K];
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_task = (int)atomicAdd(a.next, 1u);
+    __syncthreads();
+    const int t = s_task;
+    if (t >= a.count) break;
+    const int pid = a.order[t];
+    const BatchItemDev it = a.items[pid];
+    double* nu = (double*)smem;                                   // n doubles
+    double2* v = (double2*)(nu + BT_MAX_N);                        // l entries
+    const int st = batch_select(it, tau, nu, red, v);
+    if (st != RID_OK) {
+      if (threadIdx.x == 0) {
+        a.status_out[pid] = st;
+        a.err_out[2 * pid] = -1.0;
+        a.err_out[2 * pid + 1] = -1.0;
+      }
+      continue;
+    }
+    batch_solve(it, smem, smem + BT_MAX_K * BT_NR);
+    batch_error_rows(it, a.post[pid], a.r, smem, red, a.err_out + 2 * pid);
+    if (threadIdx.x == 0) a.status_out[pid] = RID_OK;
+  }
+}
+
+size_t batch_post_smem_bytes() {
+  const size_t select = BT_MAX_N * sizeof(double) + BT_MAX_L * sizeof(double2);
+  const size_t solve = (size_t)(BT_MAX_K * BT_NR + BT_MAX_K) * sizeof(double2);
+  const size_t error = (size_t)BT_MAX_K * RID_MAX_PROBES * sizeof(double2);
+  size_t s = select;
+  if (solve > s) s = solve;
+  if (error > s) s = error;
+  return s;
+}
+
 size_t batch_smem_bytes(int ct) {
   const size_t sketch = (size_t)(ct + BT_MAX_L) * (BT_KC + 1) * sizeof(double2);
   const size_t select = BT_MAX_N * sizeof(double) + BT_MAX_L * sizeof(double2);
@@ -579,6 +713,232 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
   const rid_status st = rid_batch_prepare(items, count, nprobe, workspace, ws_bytes, stream);
   if (st != RID_OK) return st;
   return rid_batch_launch(count, nprobe, probe_seed, tile, err_out, status_out, workspace, stream);
+}
+
+// ---------------------------------------------------------------------------
+// The tensor-core batch: one FP64-emulated plan per problem, every plan's
+// sketch (Y and the row probes' X) captured once in a CUDA graph fanned out
+// over concurrent branch streams, then one persistent launch of select,
+// solve and the row-probe error for all problems.
+// ---------------------------------------------------------------------------
+struct rid_batch_plan_s {
+  int device;
+  int32_t count;
+  int nprobe;
+  rid_plan_t* plans;
+  cudaStream_t home;
+  cudaStream_t* branches;
+  int nbranch;
+  cudaEvent_t* events;       // fork, then one join per branch
+  cudaEvent_t times[3];      // start, before the finishing launch, end (event-record nodes of the graph)
+  cudaGraph_t graph;
+  cudaGraphExec_t exec;
+  char* dev;                 // items, post items, order, queue counter
+};
+
+static void batch_plan_release(rid_batch_plan_s* bp) {
+  if (!bp) return;
+  if (bp->home) cudaStreamSynchronize(bp->home);
+  if (bp->exec) cudaGraphExecDestroy(bp->exec);
+  if (bp->graph) cudaGraphDestroy(bp->graph);
+  if (bp->plans)
+    for (int32_t i = 0; i < bp->count; ++i)
+      if (bp->plans[i]) {
+        bp->plans[i]->stream = bp->home;      // every plan's memory is released in its home stream's order
+        rid_plan_destroy(bp->plans[i]);
+      }
+  if (bp->dev) rid_dev_free(bp->dev, bp->home);
+  if (bp->home) cudaStreamSynchronize(bp->home);
+  if (bp->events)
+    for (int i = 0; i < bp->nbranch + 1; ++i)
+      if (bp->events[i]) cudaEventDestroy(bp->events[i]);
+  for (int i = 0; i < 3; ++i)
+    if (bp->times[i]) cudaEventDestroy(bp->times[i]);
+  if (bp->branches)
+    for (int i = 0; i < bp->nbranch; ++i)
+      if (bp->branches[i]) cudaStreamDestroy(bp->branches[i]);
+  free(bp->plans);
+  free(bp->events);
+  free(bp->branches);
+  free(bp);
+}
+
+rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* items, int32_t count, int32_t nprobe,
+                               uint64_t probe_seed, double* err_out, int32_t* status_out, void* stream) {
+  if (!out) return RID_EINVAL;
+  *out = nullptr;
+  if (count < 1 || !items || !err_out || !status_out) return RID_EINVAL;
+  if (nprobe < 1 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  for (int32_t i = 0; i < count; ++i) {
+    const rid_batch_item& x = items[i];
+    if (x.m < 1 || x.n < 1 || x.k < 1 || x.l < x.k || x.k > x.m || x.k > x.n || x.lda < x.m || x.ldy < x.l ||
+        x.ldt < x.k || !x.A || !x.Y || !x.perm || (x.n > x.k && !x.T))
+      return RID_EINVAL;
+    if (x.l > BT_MAX_L || x.k > BT_MAX_K || x.n > BT_MAX_N || x.l + nprobe > 512) return RID_EUNSUPPORTED;
+    if (((uintptr_t)x.A & 15u) || ((uintptr_t)x.Y & 15u) || (x.T && ((uintptr_t)x.T & 15u))) return RID_EINVAL;
+  }
+  rid_batch_plan_s* bp = (rid_batch_plan_s*)calloc(1, sizeof(rid_batch_plan_s));
+  if (!bp) return RID_ENOMEM;
+  bp->count = count;
+  bp->nprobe = nprobe;
+  bp->home = (cudaStream_t)stream;
+  cudaGetDevice(&bp->device);
+  bp->plans = (rid_plan_t*)calloc((size_t)count, sizeof(rid_plan_t));
+  if (!bp->plans) {
+    free(bp);
+    return RID_ENOMEM;
+  }
+  rid_status st = RID_OK;
+  // one FP64-emulated plan per problem, with its row probes
+  for (int32_t i = 0; i < count && st == RID_OK; ++i) {
+    const rid_batch_item& x = items[i];
+    st = rid_plan_create(&bp->plans[i], x.m, x.n, x.k, x.l, RID_C128, RID_FP64_EMULATED, x.seed, stream);
+    if (st == RID_OK) st = rid_plan_set_probes(bp->plans[i], nprobe, probe_seed);
+  }
+  // the queue order (largest first) and the device descriptors
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
+  double* cost = (double*)malloc(sizeof(double) * (size_t)count);
+  int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
+  BatchItemDev* hitems = (BatchItemDev*)malloc(sizeof(BatchItemDev) * (size_t)count);
+  PostItemDev* hpost = (PostItemDev*)malloc(sizeof(PostItemDev) * (size_t)count);
+  if (st == RID_OK && (!order || !cost || !tmp || !hitems || !hpost)) st = RID_ENOMEM;
+  if (st == RID_OK) {
+    for (int32_t i = 0; i < count; ++i) {
+      const rid_batch_item& x = items[i];
+      hitems[i] = BatchItemDev{x.m, x.n, x.k, x.l, (const double2*)x.A, x.lda, (double2*)x.Y, x.ldy, x.perm,
+                               (double2*)x.T, x.ldt, x.seed};
+      hpost[i] = PostItemDev{bp->plans[i]->xrow, bp->plans[i]->grow_norm2};
+      order[i] = i;
+      cost[i] = 8.0 * (x.l + nprobe) * (double)x.m * (double)x.n + 16.0 * (double)x.n * x.l * x.k;
+    }
+    for (int32_t w = 1; w < count; w *= 2) {
+      for (int32_t lo = 0; lo < count; lo += 2 * w) {
+        int32_t mid = lo + w < count ? lo + w : count, hi = lo + 2 * w < count ? lo + 2 * w : count;
+        int32_t a = lo, b = mid, o = lo;
+        while (a < mid && b < hi) tmp[o++] = cost[order[a]] >= cost[order[b]] ? order[a++] : order[b++];
+        while (a < mid) tmp[o++] = order[a++];
+        while (b < hi) tmp[o++] = order[b++];
+      }
+      for (int32_t i = 0; i < count; ++i) order[i] = tmp[i];
+    }
+  }
+  const size_t off_post = (size_t)count * sizeof(BatchItemDev);
+  const size_t off_order = off_post + (size_t)count * sizeof(PostItemDev);
+  const size_t off_next = off_order + (size_t)count * sizeof(int32_t);
+  cudaError_t e = cudaSuccess;
+  if (st == RID_OK) {
+    if (rid_dev_alloc((void**)&bp->dev, off_next + 256, bp->home, bp->device) != cudaSuccess) st = RID_ENOMEM;
+  }
+  if (st == RID_OK) {
+    e = cudaMemcpyAsync(bp->dev, hitems, off_post, cudaMemcpyHostToDevice, bp->home);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bp->dev + off_post, hpost, off_order - off_post, cudaMemcpyHostToDevice, bp->home);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(bp->dev + off_order, order, off_next - off_order, cudaMemcpyHostToDevice, bp->home);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(bp->home);     // the host arrays are pageable
+    if (e != cudaSuccess) st = RID_ECUDA;
+  }
+  // branch streams and events
+  if (st == RID_OK) {
+    bp->nbranch = count < 32 ? count : 32;
+    bp->branches = (cudaStream_t*)calloc((size_t)bp->nbranch, sizeof(cudaStream_t));
+    bp->events = (cudaEvent_t*)calloc((size_t)bp->nbranch + 1, sizeof(cudaEvent_t));
+    if (!bp->branches || !bp->events) st = RID_ENOMEM;
+    for (int i = 0; st == RID_OK && i < bp->nbranch; ++i)
+      if (cudaStreamCreateWithFlags(&bp->branches[i], cudaStreamNonBlocking) != cudaSuccess) st = RID_ECUDA;
+    for (int i = 0; st == RID_OK && i < bp->nbranch + 1; ++i)
+      if (cudaEventCreateWithFlags(&bp->events[i], cudaEventDisableTiming) != cudaSuccess) st = RID_ECUDA;
+    for (int i = 0; st == RID_OK && i < 3; ++i)
+      if (cudaEventCreate(&bp->times[i]) != cudaSuccess) st = RID_ECUDA;
+  }
+  // the persistent finishing launch
+  int per_sm = 1, sms = 0;
+  if (st == RID_OK) {
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bp->device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_post_kernel, BT_THREADS, batch_post_smem_bytes());
+    if (per_sm < 1) per_sm = 1;
+  }
+  // capture: every plan's sketch on its branch, then the finishing kernel
+  cudaStream_t cap = nullptr;
+  if (st == RID_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) st = RID_ECUDA;
+  if (st == RID_OK) {
+    bool capturing = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (!capturing) st = RID_ECUDA;
+    if (st == RID_OK && cudaEventRecordWithFlags(bp->times[0], cap, cudaEventRecordExternal) != cudaSuccess) st = RID_ECUDA;
+    if (st == RID_OK && cudaEventRecord(bp->events[0], cap) != cudaSuccess) st = RID_ECUDA;
+    for (int b = 0; st == RID_OK && b < bp->nbranch; ++b)
+      if (cudaStreamWaitEvent(bp->branches[b], bp->events[0], 0) != cudaSuccess) st = RID_ECUDA;
+    for (int32_t t = 0; st == RID_OK && t < count; ++t) {
+      const int32_t i = order[t];
+      rid_plan_s* pl = bp->plans[i];
+      pl->stream = bp->branches[t % bp->nbranch];
+      st = rid_sketch(pl, items[i].A, items[i].lda, items[i].Y, items[i].ldy);
+    }
+    for (int b = 0; st == RID_OK && b < bp->nbranch; ++b) {
+      if (cudaEventRecord(bp->events[b + 1], bp->branches[b]) != cudaSuccess ||
+          cudaStreamWaitEvent(cap, bp->events[b + 1], 0) != cudaSuccess)
+        st = RID_ECUDA;
+    }
+    if (st == RID_OK && cudaEventRecordWithFlags(bp->times[1], cap, cudaEventRecordExternal) != cudaSuccess) st = RID_ECUDA;
+    if (st == RID_OK && cudaMemsetAsync(bp->dev + off_next, 0, sizeof(unsigned), cap) != cudaSuccess) st = RID_ECUDA;
+    if (st == RID_OK) {
+      PostArgs args{(const BatchItemDev*)bp->dev, (const PostItemDev*)(bp->dev + off_post),
+                    (const int32_t*)(bp->dev + off_order), count, (unsigned*)(bp->dev + off_next), nprobe, err_out,
+                    status_out};
+      const int grid = sms * per_sm < count ? sms * per_sm : count;
+      batch_post_kernel<<<grid, BT_THREADS, batch_post_smem_bytes(), cap>>>(args);
+      if (cudaGetLastError() != cudaSuccess) st = RID_ECUDA;
+    }
+    if (st == RID_OK && cudaEventRecordWithFlags(bp->times[2], cap, cudaEventRecordExternal) != cudaSuccess) st = RID_ECUDA;
+    if (capturing) {
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+      if (st == RID_OK && ce != cudaSuccess) st = RID_ECUDA;
+      if (st == RID_OK) {
+        bp->graph = g;
+        if (cudaGraphInstantiate(&bp->exec, g, 0) != cudaSuccess) st = RID_ECUDA;
+      } else if (g) {
+        cudaGraphDestroy(g);
+      }
+      cudaGetLastError();
+    }
+    for (int32_t i = 0; i < count; ++i)
+      if (bp->plans[i]) bp->plans[i]->stream = bp->home;
+  }
+  if (cap) cudaStreamDestroy(cap);
+  free(order);
+  free(cost);
+  free(tmp);
+  free(hitems);
+  free(hpost);
+  if (st != RID_OK) {
+    batch_plan_release(bp);
+    return st;
+  }
+  *out = bp;
+  return RID_OK;
+}
+
+rid_status rid_batch_tc_run(rid_batch_plan_t bp, void* stream) {
+  if (!bp || !bp->exec) return RID_EINVAL;
+  return cudaGraphLaunch(bp->exec, (cudaStream_t)stream) == cudaSuccess ? RID_OK : RID_ECUDA;
+}
+
+rid_status rid_batch_tc_times(rid_batch_plan_t bp, double out[2]) {
+  if (!bp || !out || !bp->exec) return RID_EINVAL;
+  float a = 0.f, b = 0.f;
+  if (cudaEventSynchronize(bp->times[2]) != cudaSuccess ||
+      cudaEventElapsedTime(&a, bp->times[0], bp->times[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&b, bp->times[1], bp->times[2]) != cudaSuccess)
+    return RID_ECUDA;
+  out[0] = a;
+  out[1] = b;
+  return RID_OK;
+}
+
+rid_status rid_batch_tc_destroy(rid_batch_plan_t bp) {
+  batch_plan_release(bp);
+  return RID_OK;
 }
 
 }  // extern "C"

@@ -117,3 +117,52 @@ def test_batch_graph_replay_equals_direct_launch(rid):
         for a, c in zip(ref, got):
             assert torch.equal(a["perm"], c["perm"]) and torch.equal(a["T"], c["T"])
             assert a["est"] == c["est"] and a["upper"] == c["upper"] and c["status"] == 0
+
+
+# ---- the tensor-core batch (rid_batch_tc_*) ---------------------------------------------
+def test_batch_tc_matches_oracle_and_plan_path(rid):
+    """Every problem's sketch on its own FP64-emulated plan, select / solve /
+    row-probe error in one launch: J as the oracle's, T within 1e-10, the
+    estimate within the row-probe rounding bound of the oracle's, and J, T as
+    the problem's own plan gives them."""
+    from gpu_util import row_probe_tolerances
+    probs = make_problems(20, seed=11)
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    b = rid.BatchTC(dev, nprobe=8, probe_seed=1)
+    res = b.run().results()
+    for (A, k, l, s), r, (Ad, _, _, _) in zip(probs, res, dev):
+        assert r["status"] == 0
+        out = oracle.rid(A, k, l, seed=s)
+        perm, T = to_host(r["perm"]), to_host(r["T"])
+        assert np.array_equal(perm[:k], out["J"])
+        if T.size:
+            assert np.abs(T - out["T"]).max() <= 1e-10 * np.abs(out["T"]).max()
+        G = oracle.left_probe_matrix(8, A.shape[0], 1)
+        est_o, up_o, _ = oracle.error_estimate_left(A, perm, T, G)
+        tol_est, tol_up = row_probe_tolerances(A, perm, T, G, "fp64_emulated")
+        assert abs(r["est"] - est_o) <= tol_est + 1e-14 * est_o
+        assert abs(r["upper"] - up_o) <= tol_up + 1e-14 * up_o
+        with rid.Plan(A.shape[0], A.shape[1], k, l, seed=s, mode="fp64_emulated") as plan:
+            plan.set_probes(8, 1)
+            Y = plan.sketch(Ad)
+            pp = plan.select(Y)
+            Tp = plan.solve(Y)
+            assert torch.equal(pp, r["perm"])
+            if T.size:
+                assert (Tp - r["T"]).abs().max().item() <= 1e-12 * Tp.abs().max().item()
+    b.close()
+
+
+def test_batch_tc_replays_and_reports_rank_deficiency(rid):
+    probs = make_problems(6, seed=12)
+    A0 = np.zeros((100, 80), dtype=np.complex128)
+    A0[:, 3] = 1.0                       # rank 1
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs] + [(to_dev_colmajor(A0), 4, 8, 1)]
+    b = rid.BatchTC(dev, nprobe=4, probe_seed=2)
+    first = [dict(x, T=x["T"].clone(), perm=x["perm"].clone()) for x in b.run().results()]
+    second = b.run().results()
+    for a, c in zip(first[:6], second[:6]):
+        assert torch.equal(a["perm"], c["perm"]) and torch.equal(a["T"], c["T"])
+        assert a["est"] == c["est"] and a["status"] == c["status"] == 0
+    assert second[6]["status"] == 4 and second[6]["est"] == -1.0
+    b.close()
