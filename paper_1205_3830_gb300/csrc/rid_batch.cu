@@ -1,14 +1,21 @@
-// Batched randomized IDs: many independent problems of uneven sizes in one
-// persistent launch.  A CTA takes whole problems from a work queue (one atomic
-// counter; problems are queued largest first) and runs every step of the ID for
-// its problem with CTA-wide synchronisation only, so no CTA ever waits on
-// another:
-//   sketch   Y = Omega A        (Sec. 2; Omega drawn on the fly from the
-//                                problem's seed, the same Philox counters as a
-//                                plan with that seed)
+// Batched randomized IDs: many independent problems of uneven sizes.
+//
+// The FP64 persistent batch (rid_batch_prepare / rid_batch_launch) runs all
+// problems in one launch.  A CTA takes whole problems from a work queue (one
+// atomic counter; problems are queued largest first) and runs every step of
+// the ID for its problem with CTA-wide synchronisation only, so no CTA ever
+// waits on another:
+//   sketch   Y = Omega A        (Sec. 2; Omega drawn once per problem from its
+//                                seed, the same Philox counters as a plan with
+//                                that seed, into the CTA's workspace slice)
 //   select   k Householder steps with column pivoting on Y (Sec. 2)
 //   solve    R1 T = R2 by back substitution (Sec. 2)
 //   error    probe estimate of ||A - A(:, J) P||_2 (Sec. 3.3)
+// The tensor-core batch (rid_batch_tc_*, at the end of this file) gives each
+// problem an FP64-emulated plan, records all their sketches in one CUDA graph
+// and finishes every problem (select, solve, row-probe error) in one
+// persistent launch of the same per-CTA QR and solve.
+//
 // All arithmetic is FP64; sums run in a fixed order, so a problem's result
 // does not depend on which CTA ran it or what ran beside it.
 #include <climits>

@@ -1,14 +1,17 @@
 // Truncated QR with column pivoting of the sketch Y (Sec. 2, "Y ~= Q R", with
 // the column permutation chosen by Businger-Golub pivoting).
 //
-// One launch per Householder step j.  Every CTA applies H_j^H to a set of
-// trailing columns (one warp per column, the column kept in registers between
-// the dot product and the update), recomputes the column's remaining norm
-// sum_{i>j} |Y_ic|^2 exactly, and posts its best (norm, column) pair.  The
-// last CTA to finish (found with a fence + atomic counter; no CTA ever waits
-// on another) reduces the pairs, swaps the pivot column into place and forms
-// the next reflector in LAPACK zlarfg convention, so the following launch can
-// start at once.  Ties go to the lowest column index.
+// Two launch schemes share one column update (reflect_column / reflect_pair):
+// a warp applies H_j^H to trailing columns, keeping each column in registers
+// between the dot product and the update, and recomputes its remaining norm
+// sum_{i>j} |Y_ic|^2 exactly.  Ties of the pivot norms go to the lowest column
+// index; reflectors follow LAPACK's zlarfg convention.
+//   - Plans: all k steps in one cooperative launch with a bounded grid
+//     barrier per step (select_coop_kernel, below).
+//   - The allocation-free entry: one launch per step; the last CTA to finish
+//     (a fence and an atomic ticket, so no CTA waits on another) reduces the
+//     posted (norm, column) pairs, swaps the pivot column into place and forms
+//     the next reflector.
 #include <climits>
 
 #include "rid_internal.cuh"
