@@ -359,10 +359,10 @@ def run_ours(args, cfg, world, rank, local):
         "clocks": clocks,
     }
 
-    if args.mode == "fp64_emulated" and not args.omega_bits and args.omega == "gaussian" and args.rounded_variant:
-        line["omega_rounded_24bit"] = time_rounded_omega(args, cfg, A, stream, world, rank)
     if args.e2e_steps > 0:
         line["e2e"] = run_e2e(args, cfg, plan, A, Y, perm, T, stream, world)
+    if args.mode == "fp64_emulated" and not args.omega_bits and args.omega == "gaussian" and args.rounded_variant:
+        line["omega_rounded_24bit"] = time_rounded_omega(args, cfg, A, stream, world, rank)
     if args.mode == "bf16":
         line["vs_fp64_path"] = compare_with_fp64(args, cfg, A, perm, T, stream, rank)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
