@@ -31,8 +31,8 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
 # valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
-TC_TRAFFIC = {"bytes_per_launch": 78.3e9,   # 16 x (4.839 + 0.055) GB, profiles/sketch_tc_kernel_65536x2048.md
-              "source_sha1": "c6b982fb1c91417307cf156618b07d32f120c128"}
+TC_TRAFFIC = {"bytes_per_launch": 78.4e9,   # 16 x (4.842 + 0.056) GB, profiles/sketch_tc_kernel_65536x2048.md
+              "source_sha1": "179d8f3fdf2ac9b1febe78eb2598d67572158563"}
 
 
 def tc_source_unchanged():
