@@ -29,14 +29,16 @@
 // Tiles.  M = 128 columns of A (TMEM lanes), N <= 128 rows of Omega' (TMEM
 // columns; the 2l rows are split evenly into N-tiles, a multiple of 16 each),
 // K in 32-element stages of 64-byte rows with the 64-byte swizzle: one stage
-// holds S A-slice tiles and S Omega-slice tiles.  The N-tiles of one column
-// block form a cluster: each A tile is loaded once and multicast to them, and
-// a stage is released by a multicast commit.  A K-split over CTAs balances
+// holds S A-slice tiles and S Omega-slice tiles.  The slicers write the digits
+// in exactly that shared-memory image, tile after tile, so a stage's A tiles
+// are one contiguous block in memory and arrive by one bulk copy (rather than
+// a tensor copy of 64-byte rows per tile).  The N-tiles of one column block
+// form a cluster: each A tile is loaded once and multicast to them, and a
+// stage is released by a multicast commit.  A K-split over CTAs balances
 // the waves; partial sums are reduced in a fixed order, so results are
 // deterministic.  Row probes (rows l.. of Omega) are sliced and multiplied
 // like the test matrix's rows and reduced into X instead of Y.
 #include <climits>
-#include <cudaTypedefs.h>
 
 #include "rid_internal.cuh"
 #include "rid_tc.cuh"
@@ -48,25 +50,16 @@ namespace {
 constexpr int TC_S = 7;                 // digits per value: 56 bits
 constexpr int TC_G = 4;                 // accumulator groups
 constexpr int TC_KC = 256;              // chunk of the reduction with exact FP32 sums
-#ifndef RID_TC_KS
-#define RID_TC_KS 32
-#endif
-constexpr int TC_KS = RID_TC_KS;        // K per pipeline stage (32: 64-byte tile rows, 2 MMAs per slice pair)
+constexpr int TC_KS = 32;               // K per pipeline stage: 64-byte tile rows, 2 MMAs per slice pair
+constexpr int TC_SPC = TC_KC / TC_KS;   // stages per chunk
 constexpr int TC_MAX_STAGES = 6;        // stages in flight: as many as fit in shared memory, at most this
 constexpr int TC_TILE_BYTES = 128 * TC_KS * 2;     // an A tile: 128 rows x (2 TC_KS) bytes
+constexpr int TC_TILE_ELEMS = 128 * TC_KS;         // the same in bf16 elements
 constexpr int TC_SMEM_LIMIT = 232448;   // dynamic + static shared memory of one CTA
 // The dynamic shared memory attribute is process-wide and plans of other
 // shapes launch the kernel from other host threads: it is always set to this
 // bound, which every plan's stages fit under.
 constexpr int TC_DYN_SMEM_MAX = TC_SMEM_LIMIT - 2048;
-#ifndef RID_TC_PREFETCH
-#define RID_TC_PREFETCH 0
-#endif
-constexpr int TC_PREFETCH = RID_TC_PREFETCH;   // stages ahead whose A tiles are prefetched into L2
-#ifndef RID_TC_OPAD
-#define RID_TC_OPAD 1024
-#endif
-constexpr int TC_OPAD = RID_TC_OPAD;           // Omega tiles start at multiples of this in a stage
 constexpr int TC_THREADS = 512;         // warps 0-11 flush, 12 TMA, 13 MMA + TMEM, 14-15 idle
 constexpr int TC_FLUSH_WARPS = 12;
 constexpr int TC_LAUNCH_REGS = 128;    // 65536 / 512: the pool the setmaxnreg split assumes
@@ -78,10 +71,11 @@ struct TcState {
   int row0, nrows;        // the rows of Omega this state multiplies
   bool a_c64;             // A is complex64 (converted exactly to FP64 before slicing)
   int nstages;            // pipeline stages that fit in shared memory
-  uint32_t stage_smem, o_off, o_tile_smem;
+  uint32_t stage_smem, o_off, o_tile_smem;   // o_tile_smem: tile_w (pairs: tile_w / 2) rows x 64 bytes
   int dyn_smem;           // dynamic shared memory of the product kernel
   int so;                 // Omega digits used: S, or bits / 8 for a rounded Omega
   int64_t KP;             // padded reduction length (multiple of TC_KC)
+  int64_t nst;            // K stages: KP / TC_KS
   int NC;                 // chunks
   int l2;                 // 2l rows of Omega'
   int ntiles;             // N-tiles of tile_w <= 128 rows (balanced: the cluster runs at the widest)
@@ -89,18 +83,35 @@ struct TcState {
   int nblocks;            // column blocks of 128
   int ksplit;             // K-splits
   int chunks_per_split;
-  int cx, cy;             // cluster shape (N-tiles x column blocks)
-  int nblocks_p;          // column blocks padded to a multiple of cy
-  uint16_t* om_slices;    // [S][l2][KP] bf16
+  bool pair;              // CTA pairs (M = 256) rather than single CTAs
+  int cx;                 // single CTAs: N-tiles per cluster
+  uint16_t* om_slices;    // tiles [N-tile][K stage][S][tile_w x TC_KS] bf16 (see omega_slice_kernel)
   int* om_exp;            // [l2]
-  uint16_t* a_slices;     // [S][n][KP] bf16
+  uint16_t* a_slices;     // tiles [column block][K stage][S][128 x TC_KS] bf16 (see a_slice_kernel);
+                          // pairs: one zero block past the last, the partner of an odd last block
   int* a_exp;             // [n][NC]
   int* a_exp_max;         // [n]
   float2* partial;        // [ksplit][n][l2p]: (hi, lo) of each running sum
   int l2p;
   int* err;               // device error word
-  CUtensorMap map_a, map_om;
 };
+
+// Byte offset of element k (0 <= k < TC_KS) of row r within a tile of 64-byte
+// rows in the 64-byte swizzle: the row's 16-byte chunk c sits at position
+// c ^ ((r >> 1) & 3), the image a tensor copy with that swizzle leaves in
+// shared memory (tiles start at multiples of 1024 bytes there).
+__host__ __device__ __forceinline__ int tile_offset(int r, int k) {
+  return r * (TC_KS * 2) + ((((k * 2) >> 4) ^ ((r >> 1) & 3)) << 4) + ((k * 2) & 15);
+}
+
+// Columns of one N-tile's MMA: its rows rounded up to 16; pairs take at least
+// 32 (each CTA supplies half).  The Omega slicer splits a pair's tile at half
+// of this.
+__host__ __device__ __forceinline__ int tile_mma_n(int tile_w, int l2, int nt, bool pair) {
+  const int rest = l2 - nt * tile_w;
+  const int nm = ((rest < tile_w ? rest : tile_w) + 15) & ~15;
+  return !pair ? nm : nm < 32 ? (tile_w < 32 ? tile_w : 32) : nm;
+}
 
 // ---- digits --------------------------------------------------------------------
 // Exponent e of x (|x| < 2^e, x = f 2^e with 1/2 <= |f| < 1); subnormals and
@@ -169,12 +180,20 @@ __global__ void omega_exp_kernel(const double2* __restrict__ om, int64_t ldo, in
   }
 }
 
-// Digits of Omega' rows: row 2i = (Re w_r, -Im w_r), row 2i+1 = (Im w_r, Re w_r).
+// Digits of Omega' rows: row 2i = (Re w_r, -Im w_r), row 2i+1 = (Im w_r, Re w_r),
+// written as the product kernel's Omega tiles in the swizzled image of
+// tile_offset: [N-tile][K stage][digit] tiles of tile_w rows x TC_KS bf16 for
+// single CTAs; for CTA pairs [N-tile][K stage][half][digit] tiles of
+// tile_w / 2 rows, half 0 holding the tile's rows below n / 2 and half 1 the
+// rest (n = tile_mma_n).  Rows past 2l stay as the caller zeroed them.
 __global__ void omega_slice_kernel(const double2* __restrict__ om, int64_t ldo, int64_t m, int l, int64_t KP,
-                                   const int* __restrict__ om_exp, uint16_t* __restrict__ slices) {
+                                   int tile_w, bool pair, const int* __restrict__ om_exp,
+                                   uint16_t* __restrict__ tiles) {
   const int64_t per_row = KP / 2;      // complex positions per row, incl. padding
   const int64_t total = (int64_t)l * per_row;
-  const int64_t slice_stride = (int64_t)2 * l * KP;
+  const int64_t nst = KP / TC_KS;
+  const int H = pair ? 2 : 1;
+  const int64_t tile_elems = (int64_t)(tile_w / H) * TC_KS;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int i = (int)(e / per_row);
     const int64_t r = e - (int64_t)i * per_row;
@@ -184,11 +203,21 @@ __global__ void omega_slice_kernel(const double2* __restrict__ om, int64_t ldo, 
     digits_of(w.x, ex, re);
     digits_of(-w.y, ex, nim);
     digits_of(w.y, ex, im);
-    for (int s = 0; s < TC_S; ++s) {
-      uint16_t* row0 = slices + s * slice_stride + (int64_t)(2 * i) * KP + 2 * r;
-      uint16_t* row1 = row0 + KP;
-      *(uint32_t*)row0 = (uint32_t)re[s] | ((uint32_t)nim[s] << 16);
-      *(uint32_t*)row1 = (uint32_t)im[s] | ((uint32_t)re[s] << 16);
+    const int64_t st = 2 * r / TC_KS;               // K stage of reals 2r, 2r + 1
+    const int k = (int)(2 * r - st * TC_KS);        // their position in the stage (even)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int row = 2 * i + h, nt = row / tile_w, rr = row - nt * tile_w;
+      int hh = 0, r = rr;
+      if (pair) {
+        const int half = tile_mma_n(tile_w, 2 * l, nt, true) / 2;
+        hh = rr >= half ? 1 : 0;
+        r = rr - hh * half;
+      }
+      uint16_t* dst = tiles + (((int64_t)nt * nst + st) * H + hh) * TC_S * tile_elems + tile_offset(r, k) / 2;
+      for (int s = 0; s < TC_S; ++s)
+        *(uint32_t*)(dst + s * tile_elems) =
+            h == 0 ? (uint32_t)re[s] | ((uint32_t)nim[s] << 16) : (uint32_t)im[s] | ((uint32_t)re[s] << 16);
     }
   }
 }
@@ -244,29 +273,39 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 #undef RID_DIGIT_PAIR
 }
 
-// One warp per (column j, chunk c): 128 complex rows = 256 real values; a
-// lane takes 4 consecutive complex rows, so every slice row is written with
-// one 16-byte store per lane.
+// A block of 8 warps takes 8 consecutive columns j0 .. j0+7 of one chunk c;
+// warp w slices column j0 + w: 128 complex rows = 256 real values, a lane 4
+// consecutive complex rows, i.e. one 16-byte chunk of one K stage's tile row.
+// Column j is row j % 128 of the tiles of column block j / 128:
+// [column block][K stage][digit] tiles of 128 rows x TC_KS bf16 in the
+// swizzled image of tile_offset.  The 8 rows of the block form one 512-byte
+// swizzle atom in each of the chunk's 8 stages x S digits: they are gathered
+// in shared memory and stored atom by atom, 512 contiguous bytes per warp
+// store.  Columns n .. n_pad - 1 (the last block's padding) get zero digits.
 template <typename TA>
 __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, int64_t lda, int64_t m,
-                                                      int64_t n, int NC, int64_t KP, int64_t slice_stride,
-                                                      uint16_t* __restrict__ slices, int* __restrict__ a_exp,
+                                                      int64_t n, int64_t n_pad, int NC,
+                                                      uint16_t* __restrict__ tiles, int* __restrict__ a_exp,
                                                       int* __restrict__ a_exp_max) {
-  // A, slices, a_exp and a_exp_max start at the first column of the range
-  // (n columns); slice_stride separates the digit planes of the whole matrix
-  const int lane = threadIdx.x & 31;
-  const int64_t tasks = n * NC;
-  for (int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < tasks;
-       t += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const int64_t j = t / NC;
-    const int c = (int)(t - j * NC);
+  // A, tiles, a_exp and a_exp_max start at the first column of the range
+  // (n columns, a multiple of 128 from the matrix's first column)
+  __shared__ uint4 atoms[TC_SPC * TC_S][8][4];        // [stage x digit][row][16-byte chunk]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t groups = n_pad / 8;                  // 8-column groups per chunk
+  const int64_t tasks = groups * NC;
+  const int64_t nst = (int64_t)NC * TC_SPC;
+  for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+    const int c = (int)(t / groups);
+    const int64_t j0 = (t - (int64_t)c * groups) * 8;
+    const int64_t j = j0 + warp;
+    const bool valid = j < n;
     const int64_t r0 = (int64_t)c * 128 + 4 * lane;
     const TA* col = A + j * lda;
     double2 x[4];
     int e = TC_EXP_ZERO;
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      if (r0 + u < m) {
+      if (valid && r0 + u < m) {
         const TA v = __ldcs(col + r0 + u);
         x[u] = make_double2((double)v.x, (double)v.y);     // exact for complex64 input
       } else {
@@ -278,27 +317,48 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, 
     uint32_t w[4][TC_S];
 #pragma unroll
     for (int u = 0; u < 4; ++u) digit_words(x[u], e, w[u]);
+    // reals 2 r0 .. 2 r0 + 7: stage lane / 4 of the chunk, elements 8 (lane % 4) .. + 7
+    // of tile row j % 128 (row `warp` of its atom; the swizzle depends on the row's bits 1-2)
+    const int row = (int)(j & 127);
+    const int pc = (lane & 3) ^ ((row >> 1) & 3);
 #pragma unroll
     for (int s = 0; s < TC_S; ++s)
-      __stcs((uint4*)(slices + s * slice_stride + j * KP + 2 * r0), make_uint4(w[0][s], w[1][s], w[2][s], w[3][s]));
-    if (lane == 0) {
+      atoms[(lane >> 2) * TC_S + s][warp][pc] = make_uint4(w[0][s], w[1][s], w[2][s], w[3][s]);
+    if (lane == 0 && valid) {
       a_exp[j * NC + c] = e;
       atomicMax(a_exp_max + j, e);
     }
+    __syncthreads();
+    uint16_t* dst = tiles + ((j0 >> 7) * nst + (int64_t)c * TC_SPC) * TC_S * TC_TILE_ELEMS + (j0 & 127) * TC_KS;
+    for (int a = warp; a < TC_SPC * TC_S; a += 8)       // atom a = (stage a / S, digit a % S)
+      __stcs((uint4*)(dst + (int64_t)a * TC_TILE_ELEMS) + lane, (&atoms[a][0][0])[lane]);
+    __syncthreads();
   }
 }
 
 // ---- the tensor-core product ----------------------------------------------------------
+// Two forms of one kernel.  Single CTAs (PAIR = false): M = 128 columns of A
+// per CTA; a cluster holds the N-tiles of one column block, which share its A
+// tiles by multicast.  CTA pairs (PAIR = true): one tcgen05 MMA of M = 256
+// (cta_group::2) covers two column blocks; each CTA of the pair holds its
+// block's A tiles and half of the N-tile's Omega rows, and the tensor cores of
+// the pair read each half once.  That halves the Omega bytes per CTA (shared
+// memory traffic bounds the single form at N = 112: the MMA's operand reads
+// plus the TMA fill exceed what the SM's shared memory delivers).
 struct TcArgs {
   int n, l2, l2p, NC, chunks_per_split, ntiles, tile_w;
-  uint32_t stage_bytes;   // bytes landing in one stage: S A tiles of 128 rows + so Omega tiles of tile_w rows
+  uint32_t stage_bytes;   // bytes landing in one CTA's stage: S A tiles + so Omega tiles
   int so;                 // Omega digits that can be non-zero (S, or fewer for a rounded Omega)
   int nstages;            // pipeline stages
   uint32_t stage_smem;    // shared memory of one stage (1024-byte multiple)
   uint32_t o_off;         // offset of the Omega tiles in a stage
-  uint32_t o_tile_smem;   // shared memory of one Omega tile (1024-byte multiple)
-  int cx, cy;             // cluster: cx N-tiles (share A tiles) x cy column blocks (share Omega tiles)
+  uint32_t o_tile_smem;   // one Omega tile: tile_w rows (single) or tile_w / 2 rows (pairs) x 64 bytes
+  int cx;                 // single CTAs: N-tiles per cluster (they share A tiles)
   int jb0;                // first column block of the launch (a column range of the sketch)
+  int64_t j_end;          // columns below this have results in the launch
+  int64_t nst;            // K stages per column block / N-tile
+  const uint16_t* a_tiles;
+  const uint16_t* om_tiles;
   const int* a_exp;
   const int* a_exp_max;
   float2* partial;
@@ -307,15 +367,15 @@ struct TcArgs {
 
 __device__ __forceinline__ int group_of(int d) { return d >= 3 ? 3 : d; }
 
-// Descriptor of a 128-row tile of TC_KS bf16 per row (swizzle matching the tensor map).
-__device__ __forceinline__ uint64_t tile_desc(const void* p) { return TC_KS == 16 ? desc_sw32(p) : desc_sw64(p); }
+// Descriptor of a tile of TC_KS bf16 per row (the swizzle of tile_offset).
+__device__ __forceinline__ uint64_t tile_desc(const void* p) { return desc_sw64(p); }
 
 // One stage's products: the slice pairs (s, t) with s < SO (the Omega digits
 // that can be non-zero), t < S and s + t <= S - 1, diagonal by diagonal from
 // the smallest (group 3 holds d >= 3), each group waiting for its flush before
 // its first product of a chunk.  Descriptor start addresses are in 16-byte
 // units (low 14 bits): a tile offset within shared memory adds without carry.
-template <int SO>
+template <int SO, bool PAIR>
 __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t db0, uint64_t o_step, uint32_t idesc,
                                           int b, int cl, int stages_per_chunk, uint64_t* acc_empty,
                                           uint64_t* acc_full) {
@@ -325,7 +385,10 @@ __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t 
     const int g = group_of(d);
     const bool group_start = (d == TC_S - 1) || (d < 3);   // first diagonal of its group
     if (b == 0 && group_start && cl > 0) {
-      if (!mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)) return false;
+      // a pair's barrier also counts the other CTA's flush warps
+      const bool ok = PAIR ? mbar_wait_cluster(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)
+                           : mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET);
+      if (!ok) return false;
       tc_fence_after();
     }
 #pragma unroll
@@ -336,52 +399,59 @@ __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t 
 #pragma unroll
       for (int kk = 0; kk < TC_KS / 16; ++kk) {   // K16 steps are 32 bytes apart in a row
         const uint32_t acc = (b == 0 && group_start && s == 0 && kk == 0) ? 0u : 1u;
-        mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+        if (PAIR) mma_bf16_pair(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+        else mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
       }
     }
     const bool group_end = (d <= 3);     // last diagonal of its group in this stage
-    if (b == stages_per_chunk - 1 && group_end) mma_commit(&acc_full[g]);
+    if (b == stages_per_chunk - 1 && group_end) {
+      if (PAIR) mma_commit_pair_multicast(&acc_full[g], 3);   // both CTAs flush their rows
+      else mma_commit(&acc_full[g]);
+    }
   }
   return true;
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 1)
-sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_om, TcArgs a) {
+template <bool PAIR>
+__global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  __shared__ uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES];
+  __shared__ uint64_t full_bar[TC_MAX_STAGES], empty_bar[TC_MAX_STAGES], peer_full[TC_MAX_STAGES];
   __shared__ uint64_t acc_full[TC_G], acc_empty[TC_G], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Grid (N-tiles, column blocks, K-splits); a cluster of cx x cy CTAs covers
-  // all N-tiles of cy column blocks.  Each A tile is loaded once per cluster
-  // row and multicast to the cx CTAs that use it; each Omega tile once per
-  // cluster column and multicast to the cy CTAs that use it.
-  const int nb = blockIdx.x, jb = blockIdx.y + a.jb0, ks = blockIdx.z;
-  const int rx = nb % a.cx, ry = jb % a.cy;
-  const uint32_t my_rank = (uint32_t)(rx + ry * a.cx);
-  const uint16_t row_mask = (uint16_t)(((1u << a.cx) - 1u) << (ry * a.cx));
-  uint16_t col_mask = 0;
-  for (int y = 0; y < a.cy; ++y) col_mask |= (uint16_t)(1u << (rx + y * a.cx));
-  const uint16_t all_mask = (uint16_t)((1u << (a.cx * a.cy)) - 1u);
+  // Single: grid (N-tiles, column blocks, K-splits), clusters of cx N-tiles.
+  // Pairs: grid (2 x N-tiles, column-block pairs, K-splits), clusters of the
+  // two CTAs of one N-tile (member 0 leads: it issues the MMAs).
+  const int member = PAIR ? (int)(blockIdx.x & 1) : 0;
+  const int nb = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int jb = a.jb0 + (PAIR ? 2 * (int)blockIdx.y + member : (int)blockIdx.y);
+  const int ks = blockIdx.z;
+  const uint32_t my_rank = PAIR ? (uint32_t)member : (uint32_t)(nb % a.cx);
+  const uint16_t all_mask = PAIR ? (uint16_t)3 : (uint16_t)((1u << a.cx) - 1u);
+  const bool leader = member == 0;
   const int c_begin = ks * a.chunks_per_split;
   const int c_end = min(a.NC, c_begin + a.chunks_per_split);
   const int nchunks = max(0, c_end - c_begin);
   const int row0 = nb * a.tile_w;
   const int n_tile = min(a.tile_w, a.l2 - row0);
-  const int n_mma = (n_tile + 15) & ~15;
+  const int n_mma = tile_mma_n(a.tile_w, a.l2, nb, PAIR);
 
-  if (warp == 13) tmem_alloc(&tmem_slot, 512);
+  if (warp == 13) {
+    if (PAIR) tmem_alloc_pair(&tmem_slot, 512);
+    else tmem_alloc(&tmem_slot, 512);
+  }
   if (threadIdx.x == 0) {
     for (int i = 0; i < a.nstages; ++i) {
       mbar_init(&full_bar[i], 1);
-      mbar_init(&empty_bar[i], a.cx * a.cy);   // every CTA of the cluster releases the slot
+      mbar_init(&empty_bar[i], PAIR ? 1 : a.cx);   // released by the MMA issuer(s) of the cluster
+      mbar_init(&peer_full[i], 1);
     }
     for (int g = 0; g < TC_G; ++g) {
       mbar_init(&acc_full[g], 1);
-      mbar_init(&acc_empty[g], TC_FLUSH_WARPS);
+      mbar_init(&acc_empty[g], PAIR ? 2 * TC_FLUSH_WARPS : TC_FLUSH_WARPS);
     }
     mbar_init(&mma_done, 1);
     fence_barrier_init();
@@ -407,52 +477,59 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
     if (warp == 12 && lane == 0) {
       // ---------------- TMA producer ----------------
-      prefetch_tensormap(&map_a);
-      prefetch_tensormap(&map_om);
-      const int iters = nchunks * (TC_KC / TC_KS);
+      // Single: this CTA loads A tiles [s0, s1) of each stage for the whole
+      // cluster.  Pairs: this CTA's own A tiles.  Then its Omega tiles.  Each
+      // is one contiguous block of the tile arrays.
+      const int s0 = PAIR ? 0 : (int)my_rank * TC_S / a.cx, s1 = PAIR ? TC_S : ((int)my_rank + 1) * TC_S / a.cx;
+      const int o_elems = (int)(a.o_tile_smem / 2);
+      const int64_t st0 = (int64_t)c_begin * TC_SPC;            // first K stage of this split
+      const uint16_t* a_src = a.a_tiles + ((jb * a.nst + st0) * TC_S + s0) * TC_TILE_ELEMS;
+      const uint16_t* o_src = PAIR ? a.om_tiles + ((nb * a.nst + st0) * 2 + member) * TC_S * o_elems
+                                   : a.om_tiles + (nb * a.nst + st0) * TC_S * o_elems;
+      const int64_t o_stride = (PAIR ? 2 : 1) * TC_S * (int64_t)o_elems;
+      const uint32_t a_bytes = (uint32_t)(s1 - s0) * TC_TILE_BYTES, o_bytes = (uint32_t)a.so * a.o_tile_smem;
+      const int iters = nchunks * TC_SPC;
       int it = 0, slot = 0, round = 0;
       for (; it < iters && !s_abort; ++it) {
         if (round > 0 && !mbar_wait(&empty_bar[slot], (round - 1) & 1, TC_WAIT_BUDGET)) {
           fail(11);
           break;
         }
-        const int c = c_begin + it / (TC_KC / TC_KS);
-        const int x = c * TC_KC + (it % (TC_KC / TC_KS)) * TC_KS;
-        if (TC_PREFETCH > 0 && it + TC_PREFETCH < iters) {
-          const int ip = it + TC_PREFETCH;
-          const int xp = (c_begin + ip / (TC_KC / TC_KS)) * TC_KC + (ip % (TC_KC / TC_KS)) * TC_KS;
-          for (int s = rx; s < TC_S; s += a.cx) tma_prefetch_3d(&map_a, xp, jb * 128, s);
-        }
         // the stage's 2S tiles arrive here whoever issued them
         mbar_arrive_expect_tx(&full_bar[slot], a.stage_bytes);
-        for (int s = rx; s < TC_S; s += a.cx)
-          tma_load_3d_multicast(&map_a, &full_bar[slot], a_tile(slot, s), x, jb * 128, s, row_mask);
-        for (int s = ry; s < a.so; s += a.cy)
-          tma_load_3d_multicast(&map_om, &full_bar[slot], o_tile(slot, s), x, row0, s, col_mask);
+        if (a_bytes) {
+          if (PAIR) bulk_load(a_tile(slot, s0), a_src, a_bytes, &full_bar[slot]);
+          else bulk_load_multicast(a_tile(slot, s0), a_src, a_bytes, &full_bar[slot], all_mask);
+        }
+        bulk_load(o_tile(slot, 0), o_src, o_bytes, &full_bar[slot]);
+        a_src += TC_S * TC_TILE_ELEMS;        // next K stage
+        o_src += o_stride;
         if (++slot == NS) {
           slot = 0;
           ++round;
         }
       }
       // tail: before the CTA may exit, every slot must have been released by
-      // every CTA of the cluster (their commits arrive here), or, after an
-      // error, every load issued into this CTA must have landed
+      // every MMA issuer of the cluster (their commits arrive here), or, after
+      // an error, every load issued into this CTA must have landed
       for (int k = max(0, it - NS); k < it; ++k) {
         const bool ok = s_abort ? mbar_wait(&full_bar[k % NS], (k / NS) & 1, TC_WAIT_BUDGET)
                                 : mbar_wait(&empty_bar[k % NS], (k / NS) & 1, TC_WAIT_BUDGET);
         if (!ok) fail(12);
       }
-    } else if (warp == 13 && lane == 0) {
+    } else if (warp == 13 && lane == 0 && leader) {
       // ---------------- MMA issuer ----------------
-      const uint32_t idesc = idesc_bf16_f32(128, n_mma);
-      const int stages_per_chunk = TC_KC / TC_KS;
+      const uint32_t idesc = idesc_bf16_f32(PAIR ? 256 : 128, n_mma);
+      const int stages_per_chunk = TC_SPC;
       // descriptor start addresses are in 16-byte units (low 14 bits): a tile
       // offset within the CTA's shared memory adds without carry
       const uint64_t o_step = a.o_tile_smem >> 4;
       int slot = 0, round = 0;
       for (int cl = 0; cl < nchunks && !s_abort; ++cl) {
         for (int b = 0; b < stages_per_chunk && !s_abort; ++b) {
-          if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET)) {
+          // this CTA's tiles, and for a pair the other CTA's (relayed)
+          if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET) ||
+              (PAIR && !mbar_wait_cluster(&peer_full[slot], round & 1, TC_WAIT_BUDGET))) {
             fail(21);
             break;
           }
@@ -461,7 +538,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
           bool ok = true;
           switch (a.so) {      // the Omega digit count picks a fully unrolled issue sequence
 #define RID_MMA_STAGE(SO) \
-            case SO: ok = mma_stage<SO>(tmem, da0, db0, o_step, idesc, b, cl, stages_per_chunk, acc_empty, acc_full); break;
+            case SO: ok = mma_stage<SO, PAIR>(tmem, da0, db0, o_step, idesc, b, cl, stages_per_chunk, acc_empty, acc_full); break;
             RID_MMA_STAGE(1) RID_MMA_STAGE(2) RID_MMA_STAGE(3) RID_MMA_STAGE(4) RID_MMA_STAGE(5) RID_MMA_STAGE(6)
             RID_MMA_STAGE(7)
 #undef RID_MMA_STAGE
@@ -471,14 +548,32 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             fail(22);
             break;
           }
-          mma_commit_multicast(&empty_bar[slot], all_mask);
+          if (PAIR) mma_commit_pair_multicast(&empty_bar[slot], all_mask);
+          else mma_commit_multicast(&empty_bar[slot], all_mask);
           if (++slot == NS) {
             slot = 0;
             ++round;
           }
         }
       }
-      mma_commit(&mma_done);
+      if (PAIR) mma_commit_pair_multicast(&mma_done, all_mask);
+      else mma_commit(&mma_done);
+    } else if (PAIR && warp == 13 && lane == 0) {
+      // ---------------- relay (odd CTA of a pair) ----------------
+      // the leader's MMAs read this CTA's tiles: tell it when each stage has landed
+      const int iters = nchunks * TC_SPC;
+      int slot = 0, round = 0;
+      for (int it = 0; it < iters && !s_abort; ++it) {
+        if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET)) {
+          fail(23);
+          break;
+        }
+        mbar_arrive_remote(&peer_full[slot], 0);
+        if (++slot == NS) {
+          slot = 0;
+          ++round;
+        }
+      }
     }
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 152;\n" ::: "memory");
@@ -489,7 +584,7 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     const int col0 = third * 48;
     const int nblk = third < 2 ? 3 : 2;              // 16-column blocks of this warp
     const int64_t j = (int64_t)jb * 128 + quarter * 32 + lane;
-    const bool j_ok = j < a.n;
+    const bool j_ok = j < a.j_end;
     const int emax = j_ok ? a.a_exp_max[j] : TC_EXP_ZERO;
     float hi[48], lo[48];
 #pragma unroll
@@ -520,7 +615,10 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
             if (h2 == nblk - 1) {        // all columns read: the group may be overwritten
               tc_fence_before();
               __syncwarp();
-              if (lane == 0) mbar_arrive(&acc_empty[g]);
+              if (lane == 0) {
+                if (leader) mbar_arrive(&acc_empty[g]);
+                else mbar_arrive_remote(&acc_empty[g], 0);   // the pair's MMAs are the leader's
+              }
             }
 #pragma unroll
             for (int q = 0; q < 16; ++q) {
@@ -552,7 +650,8 @@ sketch_tc_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constan
     if (!mbar_wait(&mma_done, 0, TC_WAIT_BUDGET)) fail(91);
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    if (PAIR) tmem_dealloc_pair(tmem, 512);
+    else tmem_dealloc(tmem, 512);
   }
 }
 
@@ -579,33 +678,6 @@ __global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit,
     if (i < ly) Y[i + j * ldy] = v;
     else X[(i - ly) + j * ldx] = v;
   }
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
-  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
-  if (!enc) {
-    cudaDriverEntryPointQueryResult q;
-    void* fn = nullptr;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
-            cudaSuccess &&
-        q == cudaDriverEntryPointSuccess)
-      enc = (PFN_cuTensorMapEncodeTiled_v12000)fn;
-  }
-  return enc;
-}
-
-// 3D bf16 tensor [slices][rows][KP] with a box of TC_KS x box_rows x 1 and the matching swizzle.
-int make_slice_map(CUtensorMap* map, const void* base, int64_t KP, int64_t rows, int slices, int box_rows) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) return -1;
-  cuuint64_t gdim[3] = {(cuuint64_t)KP, (cuuint64_t)rows, (cuuint64_t)slices};
-  cuuint64_t gstride[2] = {(cuuint64_t)KP * 2, (cuuint64_t)(KP * 2 * rows)};
-  cuuint32_t box[3] = {TC_KS, (cuuint32_t)box_rows, 1};
-  cuuint32_t es[3] = {1, 1, 1};
-  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, gdim, gstride, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, TC_KS == 16 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? 0 : (int)r;
 }
 
 // K-splits so that the clusters fill whole waves; `slots` = clusters resident at once.
@@ -658,20 +730,26 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   st->so = p->omega_bits > 0 ? (p->omega_bits + 7) / 8 : TC_S;
   st->NC = (int)((2 * p->m + TC_KC - 1) / TC_KC);
   st->KP = (int64_t)st->NC * TC_KC;
+  st->nst = st->KP / TC_KS;
   st->l2 = 2 * nrows;
   st->ntiles = (st->l2 + 127) / 128;
   st->tile_w = ((st->l2 + st->ntiles - 1) / st->ntiles + 15) / 16 * 16;
-  st->l2p = st->ntiles * st->tile_w;
   st->nblocks = (int)((p->n + 127) / 128);
+  // CTA pairs whenever there are two column blocks to pair; each CTA then
+  // holds half of an N-tile's rows (at least 16 of them)
+  st->pair = st->nblocks >= 2;
+  if (st->pair && st->tile_w < 32) st->tile_w = 32;
+  st->l2p = st->ntiles * st->tile_w;
   if (st->ntiles > 8) {
     free(st);
     return RID_EUNSUPPORTED;
   }
-  // Stage layout: S A tiles, then so Omega tiles of tile_w rows, each a
-  // multiple of 1024 bytes; as many stages as shared memory holds.
-  st->o_tile_smem = (uint32_t)((st->tile_w * TC_KS * 2 + TC_OPAD - 1) / TC_OPAD * TC_OPAD);
+  // Stage layout: S A tiles, then so Omega tiles of tile_w rows (pairs:
+  // tile_w / 2), a multiple of 8 rows, so every tile starts where its
+  // 512-byte swizzle pattern does; as many stages as shared memory holds.
+  st->o_tile_smem = (uint32_t)((st->pair ? st->tile_w / 2 : st->tile_w) * TC_KS * 2);
   st->o_off = (uint32_t)(TC_S * TC_TILE_BYTES);
-  st->stage_smem = st->o_off + (uint32_t)st->so * st->o_tile_smem;
+  st->stage_smem = (st->o_off + (uint32_t)st->so * st->o_tile_smem + 1023) / 1024 * 1024;
   st->nstages = (int)((TC_SMEM_LIMIT - 2048 - 1024) / st->stage_smem);
   if (st->nstages > TC_MAX_STAGES) st->nstages = TC_MAX_STAGES;
   if (st->nstages < 2) {
@@ -679,38 +757,40 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
     return RID_EUNSUPPORTED;
   }
   st->dyn_smem = (int)(st->nstages * st->stage_smem + 1024);
-  // Clusters span the N-tiles of one column block (they share its A tiles).
-  // Sharing Omega tiles across column blocks too (cy > 1) measured slower:
-  // larger clusters pack GPCs less densely and run in lockstep.
-  st->cx = st->ntiles;
-  st->cy = 1;
-  st->nblocks_p = (st->nblocks + st->cy - 1) / st->cy * st->cy;
+  // Single CTAs: a cluster holds the N-tiles of one column block (they share
+  // its A tiles; sharing Omega tiles across column blocks too measured
+  // slower: larger clusters pack GPCs less densely and run in lockstep).
+  // Pairs: a cluster is the pair.
+  st->cx = st->pair ? 2 : st->ntiles;
+  const int units = st->pair ? st->ntiles * ((st->nblocks + 1) / 2) : st->nblocks;   // clusters per K-split
   {
     // how many clusters of this shape are resident at once
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3(st->cx, st->nblocks_p, 1);
+    cfg.gridDim = dim3(st->pair ? 2 * st->ntiles : st->ntiles, st->pair ? (st->nblocks + 1) / 2 : st->nblocks, 1);
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = st->dyn_smem;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = st->cx;
-    attr[0].val.clusterDim.y = st->cy;
+    attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     int clusters = 0;
-    cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
-    if (cudaOccupancyMaxActiveClusters(&clusters, sketch_tc_kernel, &cfg) != cudaSuccess || clusters < 1) {
+    const void* fn = st->pair ? (const void*)sketch_tc_kernel<true> : (const void*)sketch_tc_kernel<false>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
+    if (cudaOccupancyMaxActiveClusters(&clusters, fn, &cfg) != cudaSuccess || clusters < 1) {
       cudaGetLastError();
-      clusters = p->num_sms / (st->cx * st->cy);
+      clusters = p->num_sms / st->cx;
     }
-    st->ksplit = choose_ksplit(st->nblocks_p / st->cy, st->NC, clusters > 0 ? clusters : 1);
+    st->ksplit = choose_ksplit(units, st->NC, clusters > 0 ? clusters : 1);
   }
   st->chunks_per_split = (st->NC + st->ksplit - 1) / st->ksplit;
   st->ksplit = (st->NC + st->chunks_per_split - 1) / st->chunks_per_split;
 
-  const size_t om_bytes = (size_t)TC_S * st->l2 * st->KP * 2;
-  const size_t a_bytes = (size_t)TC_S * p->n * st->KP * 2;
+  const size_t om_bytes = (size_t)TC_S * st->l2p * st->KP * 2;           // N-tiles padded to tile_w rows
+  const size_t block_bytes = (size_t)TC_S * 128 * st->KP * 2;            // one column block's tiles
+  const size_t a_bytes = block_bytes * (st->nblocks + (st->pair ? 1 : 0));
   const size_t aexp_bytes = (size_t)p->n * st->NC * 4;
   const size_t part_bytes = (size_t)st->ksplit * p->n * st->l2p * 8;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
@@ -736,12 +816,10 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   st->partial = (float2*)take(part_bytes);
   st->err = (int*)take(4);
 
-  if (make_slice_map(&st->map_a, st->a_slices, st->KP, p->n, TC_S, 128) ||
-      make_slice_map(&st->map_om, st->om_slices, st->KP, st->l2, TC_S, st->tile_w)) {
-    tc_free_state(p, st);
-    return RID_ECUDA;
-  }
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(st->om_slices, 0, om_bytes, p->stream);   // padding rows
+  if (e == cudaSuccess && st->pair)                                                     // the spare block
+    e = cudaMemsetAsync((char*)st->a_slices + block_bytes * st->nblocks, 0, block_bytes, p->stream);
   if (e == cudaSuccess) {
     omega_exp_kernel<<<nrows, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m, st->om_exp);
     e = cudaGetLastError();
@@ -750,17 +828,18 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
     int64_t blocks = ((int64_t)nrows * (st->KP / 2) + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
     omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m,
-                                                                 nrows, st->KP, st->om_exp, st->om_slices);
+                                                                 nrows, st->KP, st->tile_w, st->pair,
+                                                                 st->om_exp, st->om_slices);
     e = cudaGetLastError();
   }
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(sketch_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
+  const void* fn = st->pair ? (const void*)sketch_tc_kernel<true> : (const void*)sketch_tc_kernel<false>;
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
   if (e == cudaSuccess) {
     // setmaxnreg moves registers between warpgroups inside the launch
     // allocation; it is only safe if the kernel launches with exactly the
     // 128 registers per thread the split adds up to.
     cudaFuncAttributes fa;
-    e = cudaFuncGetAttributes(&fa, sketch_tc_kernel);
+    e = cudaFuncGetAttributes(&fa, fn);
     if (e == cudaSuccess && fa.numRegs != TC_LAUNCH_REGS) {
       tc_free_state(p, st);
       return RID_EUNSUPPORTED;
@@ -831,40 +910,43 @@ cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, in
   cudaError_t e = cudaMemsetAsync(st->a_exp_max + col0, 0x80, (size_t)ncols * 4, p->stream);
   if (e != cudaSuccess) return e;
   {
-    const int64_t tasks = ncols * (int64_t)st->NC;
-    int64_t blocks = (tasks * 32 + 255) / 256;
+    const int64_t n_pad = (ncols + 127) / 128 * 128;
+    int64_t blocks = n_pad / 8 * (int64_t)st->NC;          // a block per 8 columns of one chunk
     if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
+    uint16_t* tiles = st->a_slices + (col0 / 128) * st->nst * TC_S * TC_TILE_ELEMS;
     if (st->a_c64)
       a_slice_kernel<float2><<<(unsigned)blocks, 256, 0, p->stream>>>(
-          (const float2*)A_ + col0 * lda, lda, p->m, ncols, st->NC, st->KP, p->n * st->KP,
-          st->a_slices + col0 * st->KP, st->a_exp + col0 * st->NC, st->a_exp_max + col0);
+          (const float2*)A_ + col0 * lda, lda, p->m, ncols, n_pad, st->NC, tiles, st->a_exp + col0 * st->NC,
+          st->a_exp_max + col0);
     else
       a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
-          (const double2*)A_ + col0 * lda, lda, p->m, ncols, st->NC, st->KP, p->n * st->KP,
-          st->a_slices + col0 * st->KP, st->a_exp + col0 * st->NC, st->a_exp_max + col0);
+          (const double2*)A_ + col0 * lda, lda, p->m, ncols, n_pad, st->NC, tiles, st->a_exp + col0 * st->NC,
+          st->a_exp_max + col0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (timing) cudaEventRecord(p->ev[1], p->stream);
   const int jb0 = (int)(col0 / 128);
   const int nblocks = (int)((ncols + 127) / 128);
   TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
-              (uint32_t)(TC_S * TC_TILE_BYTES + st->so * st->tile_w * TC_KS * 2), st->so, st->nstages,
-              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, st->cy, jb0,
-              st->a_exp, st->a_exp_max, st->partial, st->err};
+              (uint32_t)(TC_S * TC_TILE_BYTES) + (uint32_t)st->so * st->o_tile_smem, st->so, st->nstages,
+              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, jb0, col0 + ncols, st->nst, st->a_slices,
+              st->om_slices, st->a_exp, st->a_exp_max, st->partial, st->err};
   {
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
-    cfg.gridDim = dim3((unsigned)st->ntiles, (unsigned)((nblocks + st->cy - 1) / st->cy * st->cy), (unsigned)st->ksplit);
+    cfg.gridDim = st->pair ? dim3((unsigned)(2 * st->ntiles), (unsigned)((nblocks + 1) / 2), (unsigned)st->ksplit)
+                           : dim3((unsigned)st->ntiles, (unsigned)nblocks, (unsigned)st->ksplit);
     cfg.blockDim = dim3(TC_THREADS);
     cfg.dynamicSmemBytes = st->dyn_smem;
     cfg.stream = p->stream;
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = st->cx;
-    attr[0].val.clusterDim.y = st->cy;
+    attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    e = cudaLaunchKernelEx(&cfg, sketch_tc_kernel, st->map_a, st->map_om, args);
+    e = st->pair ? cudaLaunchKernelEx(&cfg, sketch_tc_kernel<true>, args)
+                 : cudaLaunchKernelEx(&cfg, sketch_tc_kernel<false>, args);
     if (e != cudaSuccess) return e;
   }
   if (timing) cudaEventRecord(p->ev[2], p->stream);

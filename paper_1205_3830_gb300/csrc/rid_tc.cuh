@@ -1,5 +1,5 @@
 // Blackwell (sm_103a) building blocks written as inline PTX: mbarriers, TMA
-// tile loads, tcgen05 tensor-memory allocation, MMA, commit and loads.
+// bulk copies, tensor-map prefetch, tcgen05 tensor-memory allocation, MMA, commit and loads.
 //
 // Every wait on an mbarrier is bounded (a clock budget); when it runs out the
 // caller gets `false`, records an error and winds down instead of spinning.
@@ -42,6 +42,33 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// The same with cluster-scope acquire, for barriers that CTAs of the cluster arrive on.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_cluster(uint64_t* bar, uint32_t parity, long long budget) {
+  if (mbar_try_wait_cluster(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait_cluster(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+// Arrive (release, cluster scope) on the barrier at the offset of `bar` in the
+// cluster's CTA `rank`.
+__device__ __forceinline__ void mbar_arrive_remote(uint64_t* bar, uint32_t rank) {
+  uint32_t remote;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(bar)), "r"(rank));
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+}
 // Wait for phase `parity` of `bar` for at most `budget` clock cycles.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long budget) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -52,15 +79,26 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
   return true;
 }
 
-// ---- TMA ---------------------------------------------------------------------
-// 2D tiled load of box {x .. x+box0, y .. y+box1} into shared memory; completion
-// is counted in bytes on `bar`.  x * element size must be a multiple of 16 bytes.
-__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+// ---- bulk copies ---------------------------------------------------------------
+// Contiguous global -> shared copy of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned) into this CTA, counted in bytes on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-      ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
+// Same, delivered to the same shared-memory offset (and counted on the barrier
+// at the same offset) in every CTA of `cta_mask`.
+__device__ __forceinline__ void bulk_load_multicast(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                    uint16_t cta_mask) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, [%3], %4;"
+      ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar)), "h"(cta_mask)
+      : "memory");
+}
+
+// Bring a tensor map's descriptor into the cache before its first tensor copy.
 __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)map) : "memory");
 }
@@ -76,37 +114,22 @@ __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
   asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
+// The same for a CTA pair (cta_group::2): one warp of each of the two CTAs
+// executes it; both CTAs get the same columns.
+__device__ __forceinline__ void tmem_alloc_pair(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc_pair(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand stored with the 128-byte
-// swizzle (8-row x 128-byte atoms, 1024 bytes apart), tile base 1024-aligned.
-__device__ __forceinline__ uint64_t desc_sw128(const void* smem_ptr) {
-  const uint64_t addr = smem_u32(smem_ptr);
-  uint64_t d = 0;
-  d |= (addr & 0x3FFFFull) >> 4;           // start address (16-byte units)
-  d |= (uint64_t)1 << 16;                  // leading byte offset (unused with swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;                  // descriptor version of this architecture
-  d |= (uint64_t)2 << 61;                  // 128-byte swizzle
-  return d;
-}
-
-// Same for 32-byte rows (16 bf16 of K per row) with the 32-byte swizzle:
-// 8-row atoms of 256 bytes.  One K16 step covers the whole row.
-__device__ __forceinline__ uint64_t desc_sw32(const void* smem_ptr) {
-  const uint64_t addr = smem_u32(smem_ptr);
-  uint64_t d = 0;
-  d |= (addr & 0x3FFFFull) >> 4;
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(256 >> 4) << 32;         // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)6 << 61;                  // 32-byte swizzle
-  return d;
 }
 
 // 64-byte rows (32 bf16 of K per row) with the 64-byte swizzle: 8-row atoms of
@@ -141,6 +164,19 @@ __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64
       ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// CTA pair (cta_group::2, M = 256), issued by one thread of the even CTA:
+// rows 0-127 of A come from its shared memory, rows 128-255 from the odd CTA's
+// (same offsets); B's first N/2 rows from the even CTA, the rest from the odd
+// one; each CTA's tensor memory receives its 128 rows of D.
+__device__ __forceinline__ void mma_bf16_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
 // Arrive once on `bar` when every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
@@ -156,6 +192,15 @@ __device__ __forceinline__ void mma_commit_multicast(uint64_t* bar, uint16_t cta
       : "memory");
 }
 
+// Pair form of the multicast commit, for MMAs issued with cta_group::2.
+__device__ __forceinline__ void mma_commit_pair_multicast(uint64_t* bar, uint16_t cta_mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(cta_mask)
+      : "memory");
+}
+
 // ---- clusters ----------------------------------------------------------------------
 __device__ __forceinline__ uint32_t cluster_rank() {
   uint32_t r;
@@ -166,25 +211,6 @@ __device__ __forceinline__ uint32_t cluster_rank() {
 __device__ __forceinline__ void cluster_sync() {
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-// 3D tile load delivered to the same shared-memory offset (and the same
-// barrier offset) in every CTA of `cta_mask`.
-// Bring a 3D tile of the tensor into L2 ahead of its load (no shared memory,
-// no barrier; coordinates follow the same rules as the load).
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* map, int x, int y, int z) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"((uint64_t)map), "r"(x),
-               "r"(y), "r"(z)
-               : "memory");
-}
-
-__device__ __forceinline__ void tma_load_3d_multicast(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
-                                                      int z, uint16_t cta_mask) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster "
-      "[%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "h"(cta_mask)
-      : "memory");
-}
-
 // 32 lanes x 16 consecutive 32-bit columns: thread t of the warp gets lane
 // (warp's lane quarter) + t, columns col .. col+15.
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
@@ -202,10 +228,3 @@ __device__ __forceinline__ void tmem_ld_wait() {
 }  // namespace rid_tc
 
 #endif  // __CUDACC__
-
-// ---- host: tensor maps ---------------------------------------------------------
-// 2D row-major bf16 matrix (rows x cols, row stride ld elements) with a box of
-// box_rows x box_cols (box_cols * 2 bytes <= 128) and the 128-byte swizzle.
-// Returns 0 on success.
-int rid_make_tmap_bf16_2d(CUtensorMap* map, const void* base, uint64_t rows, uint64_t cols, uint64_t ld,
-                          uint32_t box_rows, uint32_t box_cols);
