@@ -31,8 +31,8 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
 # valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
-TC_TRAFFIC = {"bytes_per_launch": 78.4e9,   # 16 x (4.842 + 0.056) GB, profiles/sketch_tc_kernel_65536x2048.md
-              "source_sha1": "179d8f3fdf2ac9b1febe78eb2598d67572158563"}
+TC_TRAFFIC = {"bytes_per_launch": 80.4e9,   # 16 x (4.898 + 0.127) GB, profiles/sketch_tc_kernel_65536x2048.md
+              "source_sha1": "ccd55a8440f29591c5850b568ed954358f9f84d8"}
 
 
 def tc_source_unchanged():
@@ -437,6 +437,16 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     copy_stream = torch.cuda.Stream(A.device)
     landed = [torch.cuda.Event() for _ in panels]
     done = [torch.cuda.Event() for _ in panels]
+    # this machine's host->device rate: one plain copy of the first panel, timed twice
+    c0, nc = panels[0]
+    for _ in range(2):
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0.record(copy_stream)
+        with torch.cuda.stream(copy_stream):
+            A[:, c0:c0 + nc].copy_(A_host[:, c0:c0 + nc], non_blocking=True)
+        l1.record(copy_stream)
+        torch.cuda.synchronize()
+    link_gbs = A[:, c0:c0 + nc].numel() * A.element_size() / 1e9 / (l0.elapsed_time(l1) / 1e3)
 
     def copy_in():
         for i, (c0, nc) in enumerate(panels):
@@ -474,8 +484,10 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     del A_host
     h2d = cfg.a_bytes
     d2h = 4 * cfg.n + 16 * cfg.k * (cfg.n - cfg.k) + 16
-    return {"value": world * cfg.a_bytes / 1e9 / (ms / 1e3), "unit": "GB/s", "h2d_bytes_per_step": h2d,
+    value = world * cfg.a_bytes / 1e9 / (ms / 1e3)
+    return {"value": value, "unit": "GB/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": ms, "steps": args.e2e_steps,
+            "h2d_link_gbs": link_gbs, "frac_of_link": value / (world * link_gbs),
             "pipeline": (f"A in {len(panels)} column panels on a copy stream, overlapped with the sketch"
                          if pipelined else ("A copied whole; the next step's copy overlaps select, solve and "
                                             "error" if rows else "A copied whole, then the ID"))}

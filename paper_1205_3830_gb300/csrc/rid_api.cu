@@ -547,7 +547,7 @@ rid_status rid_error_sketched(rid_plan_t p, const int32_t* perm, const void* T, 
 rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   if (!p || !out) return RID_EINVAL;
   out[0] = p->mode == RID_FP64_NATIVE ? (p->split_k > 1 ? 2 : 1) : p->tc_sketch_launches;
-  out[1] = 1 + p->k;
+  out[1] = p->sel_grid > 0 ? 1 : 1 + p->k;           // one cooperative launch, or one per step
   out[2] = p->n > p->k ? 1 : 0;
   out[3] = p->n > p->k ? 6 : 5;
   out[4] = p->split_k;

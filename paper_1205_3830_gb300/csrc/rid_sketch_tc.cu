@@ -281,7 +281,25 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 // swizzled image of tile_offset.  The 8 rows of the block form one 512-byte
 // swizzle atom in each of the chunk's 8 stages x S digits: they are gathered
 // in shared memory and stored atom by atom, 512 contiguous bytes per warp
-// store.  Columns n .. n_pad - 1 (the last block's padding) get zero digits.
+// store; the next task's loads are issued before those stores.  Columns n .. n_pad - 1 (the last block's
+// padding) get zero digits.
+template <typename TA>
+__device__ __forceinline__ void slice_load(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                           int64_t groups, int64_t t, int warp, int lane, double2 (&x)[4]) {
+  const int c = (int)(t / groups);
+  const int64_t j = (t - (int64_t)c * groups) * 8 + warp;
+  const int64_t r0 = (int64_t)c * 128 + 4 * lane;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    if (j < n && r0 + u < m) {
+      const TA v = __ldcs(A + j * lda + r0 + u);
+      x[u] = make_double2((double)v.x, (double)v.y);     // exact for complex64 input
+    } else {
+      x[u] = make_double2(0.0, 0.0);
+    }
+  }
+}
+
 template <typename TA>
 __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, int64_t lda, int64_t m,
                                                       int64_t n, int64_t n_pad, int NC,
@@ -289,30 +307,21 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, 
                                                       int* __restrict__ a_exp_max) {
   // A, tiles, a_exp and a_exp_max start at the first column of the range
   // (n columns, a multiple of 128 from the matrix's first column)
-  __shared__ uint4 atoms[TC_SPC * TC_S][8][4];        // [stage x digit][row][16-byte chunk]
+  __shared__ uint4 atoms[TC_SPC * TC_S][8][4];         // [stage x digit][row][16-byte chunk]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t groups = n_pad / 8;                  // 8-column groups per chunk
   const int64_t tasks = groups * NC;
   const int64_t nst = (int64_t)NC * TC_SPC;
-  for (int64_t t = blockIdx.x; t < tasks; t += gridDim.x) {
+  double2 x[4];
+  int64_t t = blockIdx.x;
+  if (t < tasks) slice_load(A, lda, m, n, groups, t, warp, lane, x);
+  for (; t < tasks; t += gridDim.x) {
     const int c = (int)(t / groups);
     const int64_t j0 = (t - (int64_t)c * groups) * 8;
     const int64_t j = j0 + warp;
-    const bool valid = j < n;
-    const int64_t r0 = (int64_t)c * 128 + 4 * lane;
-    const TA* col = A + j * lda;
-    double2 x[4];
     int e = TC_EXP_ZERO;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      if (valid && r0 + u < m) {
-        const TA v = __ldcs(col + r0 + u);
-        x[u] = make_double2((double)v.x, (double)v.y);     // exact for complex64 input
-      } else {
-        x[u] = make_double2(0.0, 0.0);
-      }
-      e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
-    }
+    for (int u = 0; u < 4; ++u) e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
     e = __reduce_max_sync(0xffffffffu, e);
     uint32_t w[4][TC_S];
 #pragma unroll
@@ -324,11 +333,12 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, 
 #pragma unroll
     for (int s = 0; s < TC_S; ++s)
       atoms[(lane >> 2) * TC_S + s][warp][pc] = make_uint4(w[0][s], w[1][s], w[2][s], w[3][s]);
-    if (lane == 0 && valid) {
+    if (lane == 0 && j < n) {
       a_exp[j * NC + c] = e;
       atomicMax(a_exp_max + j, e);
     }
     __syncthreads();
+    if (t + gridDim.x < tasks) slice_load(A, lda, m, n, groups, t + gridDim.x, warp, lane, x);
     uint16_t* dst = tiles + ((j0 >> 7) * nst + (int64_t)c * TC_SPC) * TC_S * TC_TILE_ELEMS + (j0 & 127) * TC_KS;
     for (int a = warp; a < TC_SPC * TC_S; a += 8)       // atom a = (stage a / S, digit a % S)
       __stcs((uint4*)(dst + (int64_t)a * TC_TILE_ELEMS) + lane, (&atoms[a][0][0])[lane]);
@@ -667,10 +677,20 @@ __global__ void tc_reduce_kernel(const float2* __restrict__ partial, int ksplit,
     const int64_t j = j0 + e / l;
     const int i = (int)(e - (j - j0) * l);
     double re = 0.0, im = 0.0;
-    for (int s = 0; s < ksplit; ++s) {
-      const float2* p = partial + ((int64_t)s * n + j) * l2p + 2 * i;
-      re += (double)p[0].x + (double)p[0].y;
-      im += (double)p[1].x + (double)p[1].y;
+    const float4* p = (const float4*)(partial + j * l2p + 2 * i);   // (hi, lo) of rows 2i and 2i+1
+    const int64_t split_stride = n * l2p / 2;                       // float4 units
+    // the splits in order; their loads batched ahead of the additions
+    for (int s0 = 0; s0 < ksplit; s0 += 8) {
+      float4 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < ksplit) q[u] = __ldcs(p + (int64_t)(s0 + u) * split_stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < ksplit) {
+          re += (double)q[u].x + (double)q[u].y;
+          im += (double)q[u].z + (double)q[u].w;
+        }
     }
     const int ea = a_exp_max[j];
     const double2 v = make_double2(ea == TC_EXP_ZERO ? 0.0 : ldexp(re, om_exp[2 * i] + ea - 16),
