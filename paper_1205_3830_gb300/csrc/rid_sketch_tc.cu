@@ -755,9 +755,12 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   st->ntiles = (st->l2 + 127) / 128;
   st->tile_w = ((st->l2 + st->ntiles - 1) / st->ntiles + 15) / 16 * 16;
   st->nblocks = (int)((p->n + 127) / 128);
-  // CTA pairs whenever there are two column blocks to pair; each CTA then
-  // holds half of an N-tile's rows (at least 16 of them)
-  st->pair = st->nblocks >= 2;
+  // CTA pairs for 16 or more column blocks (an odd count multiplies one
+  // block of zeros, so small problems lose more than the pairs gain; a batch
+  // of 64..1024-column IDs ran 5 % faster on single CTAs) with at least 32
+  // rows to split between the pair (its MMA takes N >= 32; a narrower tile,
+  // e.g. the row probes alone, runs faster on single CTAs than padded)
+  st->pair = st->nblocks >= 16 && st->l2 >= 32;
   if (st->pair && st->tile_w < 32) st->tile_w = 32;
   st->l2p = st->ntiles * st->tile_w;
   if (st->ntiles > 8) {
