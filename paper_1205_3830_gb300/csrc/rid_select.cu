@@ -100,6 +100,38 @@ __device__ __forceinline__ bool zlarfg_scalars(double2 alpha, double xnorm2, dou
   return true;
 }
 
+// zlarfg_scalars by a whole warp, bit for bit the same: the divisions that do
+// not depend on one another run in different lanes (one SIMT division per
+// round), so the chain is sqrt, division, division instead of sqrt and five
+// divisions in a row.  Every lane returns the results.
+__device__ __forceinline__ bool zlarfg_scalars_warp(double2 alpha, double xnorm2, int lane, double2& tau,
+                                                    double2& scale, double& beta) {
+  tau = make_double2(0.0, 0.0);
+  scale = make_double2(0.0, 0.0);
+  beta = alpha.x;
+  if (xnorm2 == 0.0 && alpha.y == 0.0) return false;
+  const double nrm = sqrt(fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xnorm2)));
+  beta = alpha.x >= 0.0 ? -nrm : nrm;
+  // scale = cdiv((1, 0), d) with d = alpha - beta, the same steps as cdiv
+  const double2 d = make_double2(alpha.x - beta, alpha.y);
+  const bool xbig = fabs(d.x) >= fabs(d.y);
+  // round 1: lane 0 tau.x, lane 1 tau.y, lane 2 the ratio r of cdiv
+  const double num1 = lane == 0 ? beta - alpha.x : lane == 1 ? -alpha.y : (xbig ? d.y : d.x);
+  const double den1 = lane <= 1 ? beta : (xbig ? d.x : d.y);
+  const double q1 = num1 / den1;
+  tau.x = __shfl_sync(0xffffffffu, q1, 0);
+  tau.y = __shfl_sync(0xffffffffu, q1, 1);
+  const double r = __shfl_sync(0xffffffffu, q1, 2);
+  // round 2: lane 0 and lane 1 the two components of cdiv
+  const double den = xbig ? fma(d.y, r, d.x) : fma(d.x, r, d.y);
+  const double num2 = xbig ? (lane == 0 ? fma(0.0, r, 1.0) : fma(-1.0, r, 0.0))
+                           : (lane == 0 ? fma(1.0, r, 0.0) : fma(0.0, r, -1.0));
+  const double q2 = num2 / den;
+  scale.x = __shfl_sync(0xffffffffu, q2, 0);
+  scale.y = __shfl_sync(0xffffffffu, q2, 1);
+  return true;
+}
+
 // Warp sums of two values by reduce-scatter: lanes 0-15 finish the first,
 // lanes 16-31 the second (5 additions per lane instead of 10).  The result of
 // each value is the one a plain xor butterfly leaves in lane 0.
@@ -495,12 +527,23 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     if (threadIdx.x < 32) {
       ArgMax w{-1.0, INT_MAX};
       int wb = -1;
-      for (int b = lane; b < G; b += 32) {
-        const ArgMax o{__ldcg(a.val + (int64_t)buf * G + b), __ldcg(a.idx + (int64_t)buf * G + b)};
-        const ArgMax nb = better(w, o);
-        if (nb.i != w.i) {
-          w = nb;
-          wb = b;
+      constexpr int PER = 16;            // posted pairs a lane loads before reducing them
+      for (int b0 = 0; b0 < G; b0 += 32 * PER) {
+        double pv[PER];
+        int pi[PER];
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const int b = b0 + lane + 32 * u;
+          pv[u] = b < G ? __ldcg(a.val + (int64_t)buf * G + b) : -1.0;
+          pi[u] = b < G ? __ldcg(a.idx + (int64_t)buf * G + b) : INT_MAX;
+        }
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+          const ArgMax nb = better(w, ArgMax{pv[u], pi[u]});
+          if (nb.i != w.i) {
+            w = nb;
+            wb = b0 + lane + 32 * u;
+          }
         }
       }
       const ArgMax rw = warp_argmax(w);
@@ -529,13 +572,16 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     double part = 0.0;
     for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) part += cabs2(rc[i]);
     const double xnorm2 = block_sum(part);
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
       double2 tau, scale;
       double beta;
-      if (zlarfg_scalars(rc[j], xnorm2, tau, scale, beta)) rc[j] = make_double2(beta, 0.0);
-      if (blockIdx.x == 0) a.tau[j] = tau;
-      s_tau = tau;
-      s_scale = scale;
+      const bool h = zlarfg_scalars_warp(rc[j], xnorm2, lane, tau, scale, beta);
+      if (lane == 0) {
+        if (h) rc[j] = make_double2(beta, 0.0);
+        if (blockIdx.x == 0) a.tau[j] = tau;
+        s_tau = tau;
+        s_scale = scale;
+      }
     }
     __syncthreads();
     const double2 scale = s_scale;

@@ -281,8 +281,8 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 // swizzled image of tile_offset.  The 8 rows of the block form one 512-byte
 // swizzle atom in each of the chunk's 8 stages x S digits: they are gathered
 // in shared memory and stored atom by atom, 512 contiguous bytes per warp
-// store; the next task's loads are issued before those stores.  Columns n .. n_pad - 1 (the last block's
-// padding) get zero digits.
+// store; the next task's loads are issued before those stores.  Columns
+// n .. n_pad - 1 (the last block's padding) get zero digits.
 template <typename TA>
 __device__ __forceinline__ void slice_load(const TA* __restrict__ A, int64_t lda, int64_t m, int64_t n,
                                            int64_t groups, int64_t t, int warp, int lane, double2 (&x)[4]) {
@@ -292,7 +292,7 @@ __device__ __forceinline__ void slice_load(const TA* __restrict__ A, int64_t lda
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     if (j < n && r0 + u < m) {
-      const TA v = __ldcs(A + j * lda + r0 + u);
+      const TA v = __ldg(A + j * lda + r0 + u);
       x[u] = make_double2((double)v.x, (double)v.y);     // exact for complex64 input
     } else {
       x[u] = make_double2(0.0, 0.0);
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, 
     if (t + gridDim.x < tasks) slice_load(A, lda, m, n, groups, t + gridDim.x, warp, lane, x);
     uint16_t* dst = tiles + ((j0 >> 7) * nst + (int64_t)c * TC_SPC) * TC_S * TC_TILE_ELEMS + (j0 & 127) * TC_KS;
     for (int a = warp; a < TC_SPC * TC_S; a += 8)       // atom a = (stage a / S, digit a % S)
-      __stcs((uint4*)(dst + (int64_t)a * TC_TILE_ELEMS) + lane, (&atoms[a][0][0])[lane]);
+      ((uint4*)(dst + (int64_t)a * TC_TILE_ELEMS))[lane] = (&atoms[a][0][0])[lane];
     __syncthreads();
   }
 }
