@@ -210,18 +210,15 @@ __device__ int batch_select(const BatchItemDev& it, double2* tau, double* nu, do
     double part = 0.0;
     for (int i = j + 1 + threadIdx.x; i < l; i += BT_THREADS) part += cabs2(colj[i]);
     const double xnorm2 = block_sum(part, red);
-    if (threadIdx.x == 0) {
-      const double2 alpha = colj[j];
-      double2 t = make_double2(0.0, 0.0), scale = make_double2(0.0, 0.0);
-      if (!(xnorm2 == 0.0 && alpha.y == 0.0)) {
-        const double nrm = sqrt(alpha.x * alpha.x + alpha.y * alpha.y + xnorm2);
-        const double beta = alpha.x >= 0.0 ? -nrm : nrm;
-        t = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-        scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
-        colj[j] = make_double2(beta, 0.0);
+    if (warp == 0) {          // the reflector's divisions spread over the lanes
+      double2 t, scale;
+      double beta;
+      const bool h = zlarfg_scalars_warp(colj[j], xnorm2, lane, t, scale, beta);
+      if (lane == 0) {
+        if (h) colj[j] = make_double2(beta, 0.0);
+        tau[j] = t;
+        s_scale = scale;
       }
-      tau[j] = t;
-      s_scale = scale;
     }
     __syncthreads();
     const double2 scale = s_scale;
@@ -466,41 +463,43 @@ __device__ void batch_error_rows(const BatchItemDev& it, const PostItemDev& pi, 
     xj[e] = pi.X[q + (int64_t)it.perm[a] * r];          // xj[q * k + a] = X(q, perm[a])
   }
   __syncthreads();
-  // one thread per column of T (k <= 64: the sums stay in the thread)
-  double sq[RID_MAX_PROBES];
+  // one thread per column of T (k <= 64: the sums stay in the thread), the
+  // probes four at a time (few registers, so more CTAs fit on an SM); each
+  // probe's sum runs in the same order whatever the grouping
+  constexpr int QG = 4;
+  for (int q0 = 0; q0 < r; q0 += QG) {
+    double sq[QG];
 #pragma unroll
-  for (int q = 0; q < RID_MAX_PROBES; ++q) sq[q] = 0.0;
-  for (int64_t i = threadIdx.x; i < ncols; i += BT_THREADS) {
-    double2 acc[RID_MAX_PROBES];
+    for (int g = 0; g < QG; ++g) sq[g] = 0.0;
+    for (int64_t i = threadIdx.x; i < ncols; i += BT_THREADS) {
+      double2 acc[QG];
 #pragma unroll
-    for (int q = 0; q < RID_MAX_PROBES; ++q) acc[q] = make_double2(0.0, 0.0);
-    const double2* Ti = it.T + i * it.ldt;
-    for (int a = 0; a < k; ++a) {
-      const double2 t = Ti[a];
+      for (int g = 0; g < QG; ++g) acc[g] = make_double2(0.0, 0.0);
+      const double2* Ti = it.T + i * it.ldt;
+      for (int a = 0; a < k; ++a) {
+        const double2 t = Ti[a];
 #pragma unroll
-      for (int q = 0; q < RID_MAX_PROBES; ++q)
-        if (q < r) acc[q] = cfma(xj[q * k + a], t, acc[q]);
-    }
-    const int64_t col = it.perm[k + i];
+        for (int g = 0; g < QG; ++g)
+          if (q0 + g < r) acc[g] = cfma(xj[(q0 + g) * k + a], t, acc[g]);
+      }
+      const int64_t col = it.perm[k + i];
 #pragma unroll
-    for (int q = 0; q < RID_MAX_PROBES; ++q) {
-      if (q < r) {
-        const double2 x = pi.X[q + col * r];
-        sq[q] += cabs2(make_double2(x.x - acc[q].x, x.y - acc[q].y));
+      for (int g = 0; g < QG; ++g) {
+        if (q0 + g < r) {
+          const double2 x = pi.X[q0 + g + col * r];
+          sq[g] += cabs2(make_double2(x.x - acc[g].x, x.y - acc[g].y));
+        }
       }
     }
+    // fixed-order sums: over the warp, then (below) over the warps
+#pragma unroll
+    for (int g = 0; g < QG; ++g) {
+      double v = sq[g];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0 && q0 + g < r) wsum[warp][q0 + g] = v;
+    }
   }
-  // fixed-order sums: over the warp, then over the warps
-#pragma unroll
-  for (int q = 0; q < RID_MAX_PROBES; ++q) {
-    double v = sq[q];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-    sq[q] = v;
-  }
-  if (lane == 0)
-#pragma unroll
-    for (int q = 0; q < RID_MAX_PROBES; ++q) wsum[warp][q] = sq[q];
   __syncthreads();
   if (threadIdx.x == 0) {
     double est = 0.0, zmax = 0.0;
@@ -518,7 +517,7 @@ __device__ void batch_error_rows(const BatchItemDev& it, const PostItemDev& pi, 
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(BT_THREADS) batch_post_kernel(PostArgs a) {
+__global__ void __launch_bounds__(BT_THREADS, 4) batch_post_kernel(PostArgs a) {
   extern __shared__ double2 smem[];
   __shared__ double red[BT_WARPS];
   __shared__ int s_task;

@@ -82,56 +82,6 @@ __device__ double block_sum(double x) {
   return result;
 }
 
-// Reflector scalars in LAPACK zlarfg convention from alpha = Y(j, j) and
-// xnorm2 = sum_{i>j} |Y(i, j)|^2: beta = -sign(Re alpha) ||(alpha, x)||,
-// tau = (beta - alpha) / beta, scale = 1 / (alpha - beta) for v = x * scale.
-// The norm is formed with explicit fma so that every kernel rounds it alike.
-// Returns false when H = I (x = 0 and alpha real): tau = 0, nothing scaled.
-__device__ __forceinline__ bool zlarfg_scalars(double2 alpha, double xnorm2, double2& tau, double2& scale,
-                                               double& beta) {
-  tau = make_double2(0.0, 0.0);
-  scale = make_double2(0.0, 0.0);
-  beta = alpha.x;
-  if (xnorm2 == 0.0 && alpha.y == 0.0) return false;
-  const double nrm = sqrt(fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xnorm2)));
-  beta = alpha.x >= 0.0 ? -nrm : nrm;
-  tau = make_double2((beta - alpha.x) / beta, -alpha.y / beta);
-  scale = cdiv(make_double2(1.0, 0.0), make_double2(alpha.x - beta, alpha.y));
-  return true;
-}
-
-// zlarfg_scalars by a whole warp, bit for bit the same: the divisions that do
-// not depend on one another run in different lanes (one SIMT division per
-// round), so the chain is sqrt, division, division instead of sqrt and five
-// divisions in a row.  Every lane returns the results.
-__device__ __forceinline__ bool zlarfg_scalars_warp(double2 alpha, double xnorm2, int lane, double2& tau,
-                                                    double2& scale, double& beta) {
-  tau = make_double2(0.0, 0.0);
-  scale = make_double2(0.0, 0.0);
-  beta = alpha.x;
-  if (xnorm2 == 0.0 && alpha.y == 0.0) return false;
-  const double nrm = sqrt(fma(alpha.x, alpha.x, fma(alpha.y, alpha.y, xnorm2)));
-  beta = alpha.x >= 0.0 ? -nrm : nrm;
-  // scale = cdiv((1, 0), d) with d = alpha - beta, the same steps as cdiv
-  const double2 d = make_double2(alpha.x - beta, alpha.y);
-  const bool xbig = fabs(d.x) >= fabs(d.y);
-  // round 1: lane 0 tau.x, lane 1 tau.y, lane 2 the ratio r of cdiv
-  const double num1 = lane == 0 ? beta - alpha.x : lane == 1 ? -alpha.y : (xbig ? d.y : d.x);
-  const double den1 = lane <= 1 ? beta : (xbig ? d.x : d.y);
-  const double q1 = num1 / den1;
-  tau.x = __shfl_sync(0xffffffffu, q1, 0);
-  tau.y = __shfl_sync(0xffffffffu, q1, 1);
-  const double r = __shfl_sync(0xffffffffu, q1, 2);
-  // round 2: lane 0 and lane 1 the two components of cdiv
-  const double den = xbig ? fma(d.y, r, d.x) : fma(d.x, r, d.y);
-  const double num2 = xbig ? (lane == 0 ? fma(0.0, r, 1.0) : fma(-1.0, r, 0.0))
-                           : (lane == 0 ? fma(1.0, r, 0.0) : fma(0.0, r, -1.0));
-  const double q2 = num2 / den;
-  scale.x = __shfl_sync(0xffffffffu, q2, 0);
-  scale.y = __shfl_sync(0xffffffffu, q2, 1);
-  return true;
-}
-
 // Warp sums of two values by reduce-scatter: lanes 0-15 finish the first,
 // lanes 16-31 the second (5 additions per lane instead of 10).  The result of
 // each value is the one a plain xor butterfly leaves in lane 0.
