@@ -430,7 +430,7 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     T_h = torch.empty((cfg.n - cfg.k, cfg.k), dtype=torch.complex128, pin_memory=True).t()
     torch.cuda.synchronize()
     rows = args.estimator == "rows"
-    pipelined = rows and args.mode in ("fp64", "fp64_emulated")     # modes with column-range sketches
+    pipelined = rows and args.mode in ("fp64", "fp64_emulated", "bf16")     # modes with column-range sketches
     n = cfg.n
     width = max(128, (n // 8 + 127) // 128 * 128)
     panels = [(c0, min(width, n - c0)) for c0 in range(0, n, width)] if pipelined else [(0, n)]

@@ -179,9 +179,9 @@ RID_API rid_status rid_plan_round_omega(rid_plan_t plan, int32_t bits);
  * ncols a multiple of 128 unless the range ends at column n (RID_EINVAL
  * otherwise).  Each column's arithmetic is the same as in rid_sketch, so
  * covering all columns once, in any ranges, gives rid_sketch's Y and X bit for
- * bit.  Modes RID_FP64_NATIVE and RID_FP64_EMULATED (RID_EUNSUPPORTED
- * otherwise).  Ranges of one plan are sketched in stream order; the row-probe
- * error may follow once every column has been sketched. */
+ * bit.  Modes RID_FP64_NATIVE, RID_FP64_EMULATED and RID_MIXED_BF16
+ * (RID_EUNSUPPORTED otherwise).  Ranges of one plan are sketched in stream
+ * order; the row-probe error may follow once every column has been sketched. */
 RID_API rid_status rid_sketch_cols(rid_plan_t plan, const void* A, int64_t lda, void* Y, int64_t ldy,
                                    int64_t col0, int64_t ncols);
 

@@ -22,10 +22,13 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run);
 rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run);
 void rid_mx_plan_free(rid_plan_s* p);
 cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy);
+cudaError_t rid_mx_sketch_cols(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy,
+                               int64_t col0, int64_t ncols);
 int rid_mx_error_word(const rid_plan_s* p);
 rid_status rid_tc_probe_init(rid_plan_s* p);
 void rid_tc_probe_free(rid_plan_s* p);
 cudaError_t rid_tc_probe_sketch(const rid_plan_s* p, const void* A, int64_t lda);
+cudaError_t rid_tc_probe_sketch_cols(const rid_plan_s* p, const void* A, int64_t lda, int64_t col0, int64_t ncols);
 int rid_tc_probe_error_word(const rid_plan_s* p);
 
 static rid_status rid_tc_plan_init(rid_plan_s* p) {
@@ -470,14 +473,19 @@ rid_status rid_sketch_cols(rid_plan_t p, const void* A, int64_t lda, void* Y, in
   if (col0 < 0 || ncols < 0 || col0 + ncols > p->n || col0 % 128 != 0) return RID_EINVAL;
   if (ncols % 128 != 0 && col0 + ncols != p->n) return RID_EINVAL;
   if (!aligned16(Y) || ((uintptr_t)A & (p->dtype == RID_C128 ? 15u : 7u))) return RID_EINVAL;
-  if (p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED) return RID_EUNSUPPORTED;
+  if (p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED && p->mode != RID_MIXED_BF16)
+    return RID_EUNSUPPORTED;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
   cudaError_t e;
-  if (p->mode == RID_FP64_NATIVE)
+  if (p->mode == RID_FP64_NATIVE) {
     e = rid_launch_sketch_fp64(p, (const double2*)A, lda, (double2*)Y, ldy, col0, ncols);
-  else
+  } else if (p->mode == RID_MIXED_BF16) {
+    e = rid_mx_sketch_cols(p, A, lda, (double2*)Y, ldy, col0, ncols);
+    if (e == cudaSuccess && p->nrow > 0) e = rid_tc_probe_sketch_cols(p, A, lda, col0, ncols);
+  } else {
     e = rid_tc_sketch_cols_fp64(p, A, lda, (double2*)Y, ldy, col0, ncols);
+  }
   if (e == cudaSuccess && p->nrow > 0) p->x_valid = 1;
   return from_cuda(e);
 }

@@ -518,9 +518,10 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     // reflector j from the posted copy of the pivot column (zlarfg convention)
     const double2* pc = a.cand + ((int64_t)buf * G + s_b) * l;
     for (int i = threadIdx.x; i < l; i += QR_THREADS) rc[i] = __ldcg(pc + i);
-    __syncthreads();
+    // the norm below the diagonal from the same loads (block_sum's barrier
+    // also publishes rc)
     double part = 0.0;
-    for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) part += cabs2(rc[i]);
+    for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) part += cabs2(__ldcg(pc + i));
     const double xnorm2 = block_sum(part);
     if (threadIdx.x < 32) {
       double2 tau, scale;
@@ -535,13 +536,18 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     }
     __syncthreads();
     const double2 scale = s_scale;
-    if (scale.x != 0.0 || scale.y != 0.0)
-      for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) rc[i] = cmul(rc[i], scale);
-    __syncthreads();
+    const bool scaled = scale.x != 0.0 || scale.y != 0.0;
     const int rows = l - j;
     const int padded = (rows + 31) & ~31;
-    for (int i = threadIdx.x; i < padded; i += QR_THREADS)
-      v[i] = (i == 0) ? make_double2(1.0, 0.0) : (i < rows ? rc[j + i] : make_double2(0.0, 0.0));
+    // v = (1, scaled rows below the diagonal, zero padding); rc keeps the same rows
+    for (int i = threadIdx.x; i < padded; i += QR_THREADS) {
+      double2 x = make_double2(0.0, 0.0);
+      if (i > 0 && i < rows) {
+        x = scaled ? cmul(rc[j + i], scale) : rc[j + i];
+        rc[j + i] = x;
+      }
+      v[i] = (i == 0) ? make_double2(1.0, 0.0) : x;
+    }
     __syncthreads();
 
     // H_j^H on positions c > j; position p takes the column that sat at j

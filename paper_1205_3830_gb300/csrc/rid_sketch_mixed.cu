@@ -97,10 +97,12 @@ __device__ __forceinline__ void split3f(float x, uint16_t (&t)[MX_S]) {
 // to KP.  A thread takes two consecutive complex entries: two 8-byte loads and
 // one 8-byte store per term.
 __global__ void __launch_bounds__(256) mx_a_slice_kernel(const float2* __restrict__ A, int64_t lda, int64_t m,
-                                                         int64_t n, int64_t KP, uint16_t* __restrict__ slices) {
+                                                         int64_t n, int64_t KP, int64_t slice_stride,
+                                                         uint16_t* __restrict__ slices) {
+  // A and slices start at the first of the n columns of the range; the term
+  // planes of the whole matrix are slice_stride apart
   const int64_t per_col = KP / 4;                      // pairs of complex entries per column
   const int64_t total = n * per_col;
-  const int64_t slice_stride = n * KP;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = e / per_col, r = 2 * (e - j * per_col);
     const float2* col = A + j * lda;
@@ -121,6 +123,8 @@ __global__ void __launch_bounds__(256) mx_a_slice_kernel(const float2* __restric
 
 struct MxArgs {
   int n, l2, l2p, tile_w, stages_per_split, nchunk;
+  int jb0;                // first column block of the launch
+  int64_t j_end;          // columns below this have results in the launch
   uint32_t stage_bytes;
   float* partial;
   int* err;
@@ -135,7 +139,7 @@ sketch_mixed_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
   __shared__ volatile int s_abort;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nb = blockIdx.x, jb = blockIdx.y, ks = blockIdx.z;
+  const int nb = blockIdx.x, jb = a.jb0 + (int)blockIdx.y, ks = blockIdx.z;
   const int row0 = nb * a.tile_w;
   const int n_tile = min(a.tile_w, a.l2 - row0);
   const int n_mma = (n_tile + 15) & ~15;
@@ -237,7 +241,7 @@ sketch_mixed_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
         uint32_t r[16];
         tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, r);
         tmem_ld_wait();
-        if (j < a.n) {
+        if (j < a.j_end) {
           float* dst = a.partial + ((int64_t)ks * a.n + j) * a.l2p + row0 + c0;
 #pragma unroll
           for (int q = 0; q < 16; ++q)
@@ -257,12 +261,13 @@ sketch_mixed_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
   }
 }
 
+// columns j0 .. j0 + ncols - 1 of the n-column partial sums
 __global__ void mx_reduce_kernel(const float* __restrict__ partial, int ksplit, int64_t n, int l, int l2p,
-                                 double2* __restrict__ Y, int64_t ldy) {
-  const int64_t total = n * l;
+                                 double2* __restrict__ Y, int64_t ldy, int64_t j0, int64_t ncols) {
+  const int64_t total = ncols * l;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / l;
-    const int i = (int)(e - j * l);
+    const int64_t j = j0 + e / l;
+    const int i = (int)(e - (j - j0) * l);
     double re = 0.0, im = 0.0;
     for (int s = 0; s < ksplit; ++s) {
       const float* p = partial + ((int64_t)s * n + j) * l2p + 2 * i;
@@ -372,36 +377,46 @@ rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run) {
   return RID_OK;
 }
 
-cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy) {
+// Columns col0 .. col0 + ncols - 1 (col0 a multiple of 128) of Y; the
+// K-split is the plan's, so column ranges give the same Y as one call.
+cudaError_t rid_mx_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda, double2* Y, int64_t ldy,
+                               int64_t col0, int64_t ncols) {
   const MxState* st = (const MxState*)p->tc_state;
   if (!st) return cudaErrorNotSupported;
-  const float2* A = (const float2*)A_;
+  if (ncols <= 0) return cudaSuccess;
+  const float2* A = (const float2*)A_ + col0 * lda;
   if (p->timing) cudaEventRecord(p->ev[0], p->stream);
   cudaError_t e;
   {
-    const int64_t total = p->n * (st->KP / 4);
+    const int64_t total = ncols * (st->KP / 4);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, p->n, st->KP, st->a_slices);
+    mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, ncols, st->KP, p->n * st->KP,
+                                                              st->a_slices + col0 * st->KP);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p->timing) cudaEventRecord(p->ev[1], p->stream);
-  MxArgs args{(int)p->n, st->l2, st->l2p, st->tile_w, st->stages_per_split, st->nchunk,
-              (uint32_t)(MX_S * (128 + st->tile_w) * MX_KS * 2), st->partial, st->err};
+  MxArgs args{(int)p->n, st->l2, st->l2p, st->tile_w, st->stages_per_split, st->nchunk, (int)(col0 / 128),
+              col0 + ncols, (uint32_t)(MX_S * (128 + st->tile_w) * MX_KS * 2), st->partial, st->err};
   const int smem = MX_STAGES * MX_S * (128 * MX_KS * 2 + st->tile_w * MX_KS * 2) + 1024;
-  const dim3 grid((unsigned)st->ntiles, (unsigned)st->nblocks, (unsigned)st->ksplit);
+  const dim3 grid((unsigned)st->ntiles, (unsigned)((ncols + 127) / 128), (unsigned)st->ksplit);
   sketch_mixed_kernel<<<grid, MX_THREADS, smem, p->stream>>>(st->map_a, st->map_om, args);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (p->timing) cudaEventRecord(p->ev[2], p->stream);
   {
-    const int64_t total = p->n * (int64_t)p->l;
+    const int64_t total = ncols * (int64_t)p->l;
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    mx_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->l, st->l2p, Y, ldy);
+    mx_reduce_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(st->partial, st->ksplit, p->n, p->l, st->l2p, Y, ldy,
+                                                             col0, ncols);
     e = cudaGetLastError();
   }
   if (p->timing) cudaEventRecord(p->ev[3], p->stream);
   return e;
+}
+
+cudaError_t rid_mx_sketch(const rid_plan_s* p, const void* A, int64_t lda, double2* Y, int64_t ldy) {
+  return rid_mx_sketch_cols(p, A, lda, Y, ldy, 0, p->n);
 }
 
 int rid_mx_error_word(const rid_plan_s* p) {

@@ -998,9 +998,15 @@ cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda,
   return rid_tc_sketch_cols_fp64(p, A_, lda, Y, ldy, 0, p->n);
 }
 
-// X = G A for a mixed-precision plan's row probes (every row goes to X).
+// X = G A for a mixed-precision plan's row probes (every row goes to X),
+// columns col0 .. col0 + ncols - 1.
+cudaError_t rid_tc_probe_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda, int64_t col0, int64_t ncols) {
+  return tc_sketch(p, (const TcState*)p->tc_probe_state, A_, lda, nullptr, 0, 0, p->xrow, p->nrow, col0, ncols,
+                   false);
+}
+
 cudaError_t rid_tc_probe_sketch(const rid_plan_s* p, const void* A_, int64_t lda) {
-  return tc_sketch(p, (const TcState*)p->tc_probe_state, A_, lda, nullptr, 0, 0, p->xrow, p->nrow, 0, p->n, false);
+  return rid_tc_probe_sketch_cols(p, A_, lda, 0, p->n);
 }
 
 namespace {

@@ -100,3 +100,26 @@ def test_mixed_row_probe_estimate_is_fp64(rid, shape):
     assert abs(est - est_o) <= tol_est + 1e-14 * est_o
     assert abs(up - up_o) <= tol_up + 1e-14 * up_o
     assert est_o > 100 * tol_est
+
+
+@pytest.mark.parametrize("shape", [(2048, 1000, 20, 30), (700, 2100, 10, 16)], ids=str)
+def test_mixed_panels_equal_one_sketch(rid, shape):
+    """Column panels of a mixed plan (BF16x3 Y and the FP64-emulated row
+    probes), sketched out of order, give the one-call Y and estimate bit for
+    bit."""
+    m, n, k, l = shape
+    A = to_dev_colmajor(c64_lowrank(m, n, k), torch.complex64)
+    with rid.Plan(m, n, k, l, seed=9, dtype=torch.complex64, mode="bf16") as plan:
+        plan.set_probes(8, 2)
+        Y0 = plan.sketch(A).clone()
+        R = Y0.clone()
+        perm = plan.select(R)
+        T = plan.solve(R)
+        e0 = plan.error_sketched(perm, T)
+        Y1 = torch.full_like(Y0, float("nan"))
+        starts = list(range(0, n, 384))
+        for c0 in reversed(starts):
+            plan.sketch_cols(A, Y1, c0, min(384, n - c0))
+        e1 = plan.error_sketched(perm, T)
+    assert torch.equal(Y0, Y1)
+    assert e0 == e1

@@ -156,9 +156,9 @@ def test_row_probe_argument_errors(rid):
             plan.set_probes(13, 1)                   # l + nprobe > 512
     with rid.Plan(m, n, k, l, seed=1, dtype=torch.complex64, mode="bf16") as plan:
         plan.set_probes(4, 1)                        # mixed plans take FP64-grade row probes too
-        with pytest.raises(RIDError, match="EUNSUPPORTED"):
+        with pytest.raises(RIDError, match="EINVAL"):
             plan.sketch_cols(torch.zeros((n, m), dtype=torch.complex64, device="cuda").t(),
-                             rid.colmajor_empty(l, n), 0, n)
+                             rid.colmajor_empty(l, n), 64, 36)           # col0 not a multiple of 128
 
 
 @pytest.mark.parametrize("mode", MODES)
