@@ -437,16 +437,18 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     copy_stream = torch.cuda.Stream(A.device)
     landed = [torch.cuda.Event() for _ in panels]
     done = [torch.cuda.Event() for _ in panels]
-    # this machine's host->device rate: one plain copy of the first panel, timed twice
-    c0, nc = panels[0]
-    for _ in range(2):
-        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        l0.record(copy_stream)
-        with torch.cuda.stream(copy_stream):
+    # this machine's host->device rate for this buffer: the whole of A, copied
+    # panel by panel with nothing else running (the rate differs between boxes
+    # and between parts of a large pinned buffer)
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    l0.record(copy_stream)
+    with torch.cuda.stream(copy_stream):
+        for c0, nc in panels:
             A[:, c0:c0 + nc].copy_(A_host[:, c0:c0 + nc], non_blocking=True)
-        l1.record(copy_stream)
-        torch.cuda.synchronize()
-    link_gbs = A[:, c0:c0 + nc].numel() * A.element_size() / 1e9 / (l0.elapsed_time(l1) / 1e3)
+    l1.record(copy_stream)
+    torch.cuda.synchronize()
+    link_gbs = A.numel() * A.element_size() / 1e9 / (l0.elapsed_time(l1) / 1e3)
 
     def copy_in():
         for i, (c0, nc) in enumerate(panels):
