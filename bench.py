@@ -656,7 +656,7 @@ def run_batched(args, world, rank, local):
                                f"A = X Y + 1e-10 N ({a_bytes / 2**30:.1f} GiB in all)",
                    "count": len(shapes), "nprobe": r, "estimator": "rows",
                    "path": "tensor-core batch: FP64-emulated plan per problem, sketches in one CUDA graph "
-                           "(32 branches), one persistent launch of select / solve / error",
+                           "(64 branches), one persistent launch of select / solve / error",
                    "cuda_graph": True, "l2": "inputs larger than L2 (%.1f GiB)" % (a_bytes / 2**30)},
         "ids_per_s": world * len(shapes) / (ms / 1e3),
         "phase_ms": {"sketches": sketch_ms, "select_solve_error": post_ms},

@@ -304,7 +304,7 @@ RID_API rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t prob
 /* Batches on the tensor cores.  rid_batch_tc_create gives every problem its
  * own RID_FP64_EMULATED plan with nprobe row probes (probe_seed), then records,
  * once, a CUDA graph of every plan's sketch (Y = Omega A and X = G A, the
- * problems spread over 32 concurrent branch streams, largest first) followed
+ * problems spread over 64 concurrent branch streams, largest first) followed
  * by one persistent launch that runs the pivoted QR, the solve and the
  * row-probe error estimate (as rid_error_sketched) of every problem, writing
  * err_out (device, double[2 count]) and status_out (device, int32[count]) as

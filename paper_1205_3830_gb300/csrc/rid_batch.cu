@@ -846,7 +846,7 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
   }
   // branch streams and events
   if (st == RID_OK) {
-    bp->nbranch = count < 32 ? count : 32;
+    bp->nbranch = count < 64 ? count : 64;
     bp->branches = (cudaStream_t*)calloc((size_t)bp->nbranch, sizeof(cudaStream_t));
     bp->events = (cudaEvent_t*)calloc((size_t)bp->nbranch + 1, sizeof(cudaEvent_t));
     if (!bp->branches || !bp->events) st = RID_ENOMEM;
