@@ -734,7 +734,7 @@ void tc_free_state(rid_plan_s* p, TcState* st) {
 }
 
 // A tensor-core state for rows row0 .. row0 + nrows - 1 of Omega: their digit
-// planes, the A digit buffers, partial sums and tensor maps.  dry_run: only
+// tiles, the A digit tile buffer, exponents and partial sums.  dry_run: only
 // the device bytes.
 rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64, TcState** out,
                     size_t* bytes_out) {
