@@ -252,6 +252,15 @@ RID_API rid_status rid_plan_timing(rid_plan_t plan, int32_t enable, double out[3
 RID_API rid_status rid_select_noalloc(void* Y, int64_t ldy, int32_t l, int64_t n, int32_t k,
                                       int32_t* perm, int32_t* status, void* stream);
 
+/* Self-test of the bounded waits every kernel relies on (a failure detector
+ * that needs no GPU fault): on `stream`, one launch waits on an mbarrier that
+ * nothing completes (budget about 1 ms) and on a grid barrier that one CTA
+ * more than the grid must reach (budget about 10 ms).  Each gives up and
+ * records its status: out[0] (the mbarrier) and out[1] (the grid barrier)
+ * are RID_ETIMEOUT when the waits end as designed.  Synchronizes the stream;
+ * the context stays usable.  RID_EINVAL for a null out. */
+RID_API rid_status rid_selftest_timeouts(void* stream, int32_t out[2]);
+
 /* ---- Batched IDs -------------------------------------------------------------------
  * Many independent complex128 IDs of uneven sizes (e.g. the blocks of a
  * hierarchical-matrix compressor) in one persistent launch.  Each problem is

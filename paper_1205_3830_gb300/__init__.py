@@ -396,6 +396,17 @@ class BatchTC:
             pass
 
 
+def selftest_timeouts(stream=None):
+    """Run the bounded-wait self-test (rid_selftest_timeouts); returns the two
+    status names, ("RID_ETIMEOUT", "RID_ETIMEOUT") when both waits give up as
+    designed."""
+    lib = _native.load()
+    out = (ctypes.c_int32 * 2)()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    check(lib.rid_selftest_timeouts(ctypes.c_void_p(s.cuda_stream), out), "rid_selftest_timeouts")
+    return tuple(lib.rid_status_string(int(x)).decode().split(":")[0] for x in out)
+
+
 def batch_decompose(problems, nprobe=8, probe_seed=1, tile=None):
     """Run a list of (A, k, l, seed) problems as one batch; returns Batch.results()."""
     return Batch(problems, nprobe, probe_seed).run(tile).results()

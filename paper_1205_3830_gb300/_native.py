@@ -47,6 +47,7 @@ SIGNATURES = {
     "rid_batch_tc_times": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double)]),
     "rid_batch_tc_destroy": (ctypes.c_int, [_p]),
     "rid_select_noalloc": (ctypes.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p]),
+    "rid_selftest_timeouts": (ctypes.c_int, [_p, _p]),
     "rid_status_string": (ctypes.c_char_p, [ctypes.c_int]),
 }
 

@@ -15,6 +15,7 @@
 #include <climits>
 
 #include "rid_internal.cuh"
+#include "rid_tc.cuh"
 
 namespace {
 
@@ -396,22 +397,26 @@ struct CoopArgs {
   unsigned* bar;           // [0] arrivals, [1] generation
 };
 
-__device__ bool grid_sync(const CoopArgs& a) {
+// Barrier of `parties` CTAs (the grid) on a.bar: arrivals, then a generation
+// count; a CTA that waits longer than `budget` clock cycles sets the status
+// word to RID_ETIMEOUT and gets false.
+__device__ bool grid_sync(const CoopArgs& a, unsigned parties = 0, long long budget = SEL_WAIT_BUDGET) {
   __shared__ int ok;
+  if (parties == 0) parties = gridDim.x;
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned* gen = a.bar + 1;
     const unsigned g = *gen;
     __threadfence();
     int good = 1;
-    if (atomicAdd(a.bar, 1u) == gridDim.x - 1) {
+    if (atomicAdd(a.bar, 1u) == parties - 1) {
       a.bar[0] = 0u;                      // every CTA has arrived: reset, then release
       __threadfence();
       atomicAdd(a.bar + 1, 1u);
     } else {
       const long long t0 = clock64();
       while (*gen == g) {
-        if (clock64() - t0 > SEL_WAIT_BUDGET) {
+        if (clock64() - t0 > budget) {
           atomicExch(a.status, (int)RID_ETIMEOUT);
           good = 0;
           break;
@@ -642,6 +647,53 @@ cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int3
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Self-test of the bounded waits: an mbarrier that nothing completes (the
+// wait every tensor-core kernel uses) and a grid barrier that one CTA more
+// than the grid must reach (the select's).  Both must give up after their
+// budgets and report RID_ETIMEOUT, and the context stays usable.
+// ---------------------------------------------------------------------------
+namespace {
+__global__ void selftest_wait_kernel(int* status, unsigned* bar) {
+  __shared__ uint64_t never;
+  if (threadIdx.x == 0) {
+    rid_tc::mbar_init(&never, 1);
+    rid_tc::fence_barrier_init();
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0 && !rid_tc::mbar_wait(&never, 0, 2000000ll))   // ~1 ms
+    atomicExch(status, (int)RID_ETIMEOUT);
+  CoopArgs c{};
+  c.bar = bar;
+  c.status = status + 1;
+  grid_sync(c, gridDim.x + 1, 20000000ll);                                           // ~10 ms
+}
+}  // namespace
+
+extern "C" RID_API rid_status rid_selftest_timeouts(void* stream, int32_t out[2]) {
+  if (!out) return RID_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return RID_ECUDA;
+  char* buf = nullptr;
+  if (rid_dev_alloc((void**)&buf, 256, s, dev) != cudaSuccess) return RID_ENOMEM;
+  int* status = (int*)buf;
+  unsigned* bar = (unsigned*)(buf + 64);
+  cudaError_t e = cudaMemsetAsync(buf, 0, 256, s);
+  if (e == cudaSuccess) {
+    selftest_wait_kernel<<<2, 64, 0, s>>>(status, bar);
+    e = cudaGetLastError();
+  }
+  int h[2] = {-1, -1};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, status, sizeof h, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  rid_dev_free(buf, s);
+  if (e != cudaSuccess) return RID_ECUDA;
+  out[0] = h[0];
+  out[1] = h[1];
+  return RID_OK;
 }
 
 // ---------------------------------------------------------------------------
