@@ -202,14 +202,14 @@ __device__ __forceinline__ bool zlarfg_scalars_warp(double2 alpha, double xnorm2
   // scale = cdiv((1, 0), d) with d = alpha - beta, the same steps as cdiv
   const double2 d = make_double2(alpha.x - beta, alpha.y);
   const bool xbig = fabs(d.x) >= fabs(d.y);
-  // round 1: lane 0 tau.x, lane 1 tau.y, lane 2 the ratio r of cdiv
+  // first division: lane 0 tau.x, lane 1 tau.y, lane 2 the ratio r of cdiv
   const double num1 = lane == 0 ? beta - alpha.x : lane == 1 ? -alpha.y : (xbig ? d.y : d.x);
   const double den1 = lane <= 1 ? beta : (xbig ? d.x : d.y);
   const double q1 = num1 / den1;
   tau.x = __shfl_sync(0xffffffffu, q1, 0);
   tau.y = __shfl_sync(0xffffffffu, q1, 1);
   const double r = __shfl_sync(0xffffffffu, q1, 2);
-  // round 2: lane 0 and lane 1 the two components of cdiv
+  // second division: lane 0 and lane 1 the two components of cdiv
   const double den = xbig ? fma(d.y, r, d.x) : fma(d.x, r, d.y);
   const double num2 = xbig ? (lane == 0 ? fma(0.0, r, 1.0) : fma(-1.0, r, 0.0))
                            : (lane == 0 ? fma(1.0, r, 0.0) : fma(0.0, r, -1.0));
