@@ -189,7 +189,7 @@ __device__ __forceinline__ bool zlarfg_scalars(double2 alpha, double xnorm2, dou
 
 // zlarfg_scalars by a whole warp, bit for bit the same: the divisions that do
 // not depend on one another run in different lanes (one SIMT division per
-// round), so the chain is sqrt, division, division instead of sqrt and five
+// pass), so the chain is sqrt, division, division instead of sqrt and five
 // divisions in a row.  Every lane returns the results.
 __device__ __forceinline__ bool zlarfg_scalars_warp(double2 alpha, double xnorm2, int lane, double2& tau,
                                                     double2& scale, double& beta) {
