@@ -439,16 +439,21 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     done = [torch.cuda.Event() for _ in panels]
     # this machine's host->device rate for this buffer: the whole of A, copied
     # panel by panel with nothing else running (the rate differs between boxes
-    # and between parts of a large pinned buffer)
-    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    l0.record(copy_stream)
-    with torch.cuda.stream(copy_stream):
-        for c0, nc in panels:
-            A[:, c0:c0 + nc].copy_(A_host[:, c0:c0 + nc], non_blocking=True)
-    l1.record(copy_stream)
-    torch.cuda.synchronize()
-    link_gbs = A.numel() * A.element_size() / 1e9 / (l0.elapsed_time(l1) / 1e3)
+    # and between parts of a large pinned buffer); the better of a copy before
+    # and one after the untimed pass, so first-touch costs of the pinned
+    # buffer do not lower it
+    def link_rate():
+        l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        l0.record(copy_stream)
+        with torch.cuda.stream(copy_stream):
+            for c0, nc in panels:
+                A[:, c0:c0 + nc].copy_(A_host[:, c0:c0 + nc], non_blocking=True)
+        l1.record(copy_stream)
+        torch.cuda.synchronize()
+        return A.numel() * A.element_size() / 1e9 / (l0.elapsed_time(l1) / 1e3)
+
+    link_first = link_rate()
 
     def copy_in():
         for i, (c0, nc) in enumerate(panels):
@@ -481,6 +486,7 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
 
     passes(1)                                        # untimed: the first pass of this pattern
     torch.cuda.synchronize()
+    link_gbs = max(link_first, link_rate())
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier(world)
     start.record(stream)
