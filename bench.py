@@ -702,7 +702,8 @@ def run_serving(args, world, rank, local):
     serve.run_one(mats[0], specs[0][3], specs[0][4], 1, args.nprobe, 1, args.mode)
     sweep = []
     for rate in rates:
-        srv = serve.Server(slots=args.slots, mode=args.mode)
+        opts = {} if args.select_ctas is None else {"select_ctas": args.select_ctas}
+        srv = serve.Server(slots=args.slots, mode=args.mode, **opts)
         t0 = time.perf_counter()
         due = 0.0
         for i, (_, m, n, k, l) in enumerate(specs):
@@ -720,6 +721,9 @@ def run_serving(args, world, rank, local):
                       "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"), "peak_concurrent": srv.peak_running,
                       "peak_hbm_gb": srv.peak_used / 1e9, "errors": errs})
     best = max(sweep, key=lambda x: x["served_per_s"])
+    ctas = srv.select_ctas
+    select_shape = ("the plan's default (one cooperative launch)" if ctas is None or ctas < 0 else
+                    "one launch per step" if ctas == 0 else f"one cooperative launch of at most {ctas} CTAs")
     line = {
         "metric": METRIC, "value": best["served_per_s"], "unit": "IDs/s", "n_gpus": world, "steps": len(rates),
         "warmup": 1, "ms_per_step": 1e3 / best["served_per_s"], "higher_is_better": True, "scaling": "weak",
@@ -727,7 +731,8 @@ def run_serving(args, world, rank, local):
         "data": "synthetic (seeded, generated on the device)",
         "config": {"workload": f"serving: {len(specs)} complex128 ID requests, Poisson arrivals, m, n log-uniform "
                                f"[256, 16384], k log-uniform [8, 256], l = k + 10",
-                   "mode": args.mode, "slots": args.slots, "rates": rates},
+                   "mode": args.mode, "slots": args.slots, "rates": rates,
+                   "select": select_shape},
         "p50_ms": best["p50_ms"], "p99_ms": best["p99_ms"], "sweep": sweep,
     }
     if rank == 0:
@@ -759,6 +764,10 @@ def main():
     ap.add_argument("--requests", type=int, default=64, help="requests per rate (--config serving)")
     ap.add_argument("--rates", default="5,20,80,320", help="offered request rates per second (--config serving)")
     ap.add_argument("--slots", type=int, default=8, help="concurrent requests (--config serving)")
+    ap.add_argument("--select-ctas", type=int, default=None,
+                    help="launch shape of each served request's select: 0 one launch per step, N > 0 one "
+                         "cooperative launch of at most N CTAs, -1 the plan's default (--config serving; "
+                         "default: the server's, one launch per step)")
     ap.add_argument("--m", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()

@@ -134,6 +134,19 @@ RID_API rid_status rid_sketch(rid_plan_t plan, const void* A, int64_t lda, void*
  *   becomes RID_ERANK and later steps of this call are skipped. */
 RID_API rid_status rid_select(rid_plan_t plan, void* Y, int64_t ldy, int32_t* perm);
 
+/* Launch shape of rid_select.  The results are bitwise the same for every
+ * shape: each column's arithmetic, the pivot rule and the reflector do not
+ * depend on which CTA or warp handles a column.
+ *   ctas > 0: all k steps in one cooperative launch of min(ctas, the plan's
+ *   default) CTAs, each step ending in a grid barrier;
+ *   ctas == 0: one launch per step, and no CTA ever waits on another, so
+ *   kernels of other streams can share the GPU with it;
+ *   ctas < 0: back to the plan's default (chosen at rid_plan_create: one
+ *   cooperative launch filling the GPU, where the device supports it).
+ * RID_EUNSUPPORTED for ctas > 0 when the device has no cooperative launch.
+ * No device work; takes effect at the next rid_select. */
+RID_API rid_status rid_plan_set_select_grid(rid_plan_t plan, int32_t ctas);
+
 /* Factorization of R, Sec. 2 "R2 = R1 T":  T = R1^-1 R2 by back substitution,
  * every right-hand side column independent (Sec. 3.2).
  *   Y: the output of rid_select (R1 = Y[0:k, 0:k] upper triangular,

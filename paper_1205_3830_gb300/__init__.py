@@ -201,6 +201,12 @@ class Plan:
                                            max(_ld(T), self.k), out), "rid_error_sketched")
         return float(out[0]), float(out[1])
 
+    def set_select_grid(self, ctas):
+        """Launch shape of select (same results for every shape): ctas > 0
+        one cooperative launch of at most that many CTAs, 0 one launch per
+        step (no CTA waits on another), < 0 the plan's default."""
+        check(self._lib.rid_plan_set_select_grid(self._h, int(ctas)), "rid_plan_set_select_grid")
+
     def stats(self):
         """Launch counts per call, K-splits and device bytes of the plan."""
         out = (ctypes.c_int64 * 8)()

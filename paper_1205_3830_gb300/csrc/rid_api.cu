@@ -142,9 +142,9 @@ Layout plan_layout(const rid_plan_s* p) {
   L.qr_idx = take((size_t)p->qr_grid * sizeof(int));
   L.qr_counter = take(sizeof(unsigned));
   L.tau = take((size_t)p->k * sizeof(double2));
-  L.sel_cand = take((size_t)2 * p->sel_grid * p->l * sizeof(double2));
-  L.sel_val = take((size_t)2 * p->sel_grid * sizeof(double));
-  L.sel_idx = take((size_t)2 * p->sel_grid * sizeof(int));
+  L.sel_cand = take((size_t)2 * p->sel_grid_max * p->l * sizeof(double2));
+  L.sel_val = take((size_t)2 * p->sel_grid_max * sizeof(double));
+  L.sel_idx = take((size_t)2 * p->sel_grid_max * sizeof(int));
   L.sel_bar = take(2 * sizeof(unsigned));
   L.probes = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
   L.wtilde = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
@@ -174,6 +174,7 @@ void choose_launch_shapes(rid_plan_s* p) {
   if (g > 4 * sms) g = 4 * sms;
   p->qr_grid = (int)(g < 1 ? 1 : g);
   p->sel_grid = rid_select_coop_grid(p->device, p->num_sms, p->n, p->l);
+  p->sel_grid_max = p->sel_grid;
   // error
   const int64_t ncols = p->n - p->k;
   int64_t wg = (ncols + 63) / 64;
@@ -550,6 +551,19 @@ rid_status rid_error_sketched(rid_plan_t p, const int32_t* perm, const void* T, 
   out[1] = host[1];
   if (p->mode != RID_FP64_NATIVE && rid_tc_error_word(p) != 0) return RID_ETIMEOUT;
   return status == RID_OK ? RID_OK : (rid_status)status;
+}
+
+rid_status rid_plan_set_select_grid(rid_plan_t p, int32_t ctas) {
+  if (!p) return RID_EINVAL;
+  if (ctas < 0) {
+    p->sel_grid = p->sel_grid_max;
+  } else if (ctas == 0) {
+    p->sel_grid = 0;
+  } else {
+    if (p->sel_grid_max == 0) return RID_EUNSUPPORTED;      // no cooperative launch here
+    p->sel_grid = ctas < p->sel_grid_max ? ctas : p->sel_grid_max;
+  }
+  return RID_OK;
 }
 
 rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {

@@ -39,9 +39,10 @@ struct rid_plan_s {
   double2* tau;            // k
   // select in one cooperative launch (sel_grid CTAs; 0: one launch per step)
   int sel_grid;
-  double2* sel_cand;       // 2 x sel_grid x l posted columns
-  double* sel_val;         // 2 x sel_grid
-  int* sel_idx;            // 2 x sel_grid
+  int sel_grid_max;        // the default sel_grid; the posted buffers are sized for it
+  double2* sel_cand;       // 2 x sel_grid_max x l posted columns
+  double* sel_val;         // 2 x sel_grid_max
+  int* sel_idx;            // 2 x sel_grid_max
   unsigned* sel_bar;       // grid barrier: arrivals, generation
 
   // error: probes, modified probes, partial sums, result

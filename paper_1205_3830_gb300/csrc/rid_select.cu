@@ -293,12 +293,15 @@ __device__ void pivot_and_reflect(const SelectArgs& a, int j) {
   double part = 0.0;
   for (int i = j + 1 + threadIdx.x; i < a.l; i += blockDim.x) part += cabs2(__ldcg(colj + i));
   const double xnorm2 = block_sum(part);
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {              // the divisions spread over warp 0 (same bits as one thread)
     double2 tau, scale;
     double beta;
-    if (zlarfg_scalars(__ldcg(colj + j), xnorm2, tau, scale, beta)) colj[j] = make_double2(beta, 0.0);
-    a.tau[j] = tau;
-    s_scale = scale;
+    const bool h = zlarfg_scalars_warp(__ldcg(colj + j), xnorm2, threadIdx.x, tau, scale, beta);
+    if (threadIdx.x == 0) {
+      if (h) colj[j] = make_double2(beta, 0.0);
+      a.tau[j] = tau;
+      s_scale = scale;
+    }
   }
   __syncthreads();
   const double2 scale = s_scale;

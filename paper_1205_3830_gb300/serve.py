@@ -64,13 +64,18 @@ class Request:
 class Server:
     """slots concurrent IDs, admitted by an HBM budget (bytes)."""
 
-    def __init__(self, slots=8, hbm_budget=None, mode="fp64_emulated", device=None):
+    def __init__(self, slots=8, hbm_budget=None, mode="fp64_emulated", device=None, select_ctas=0):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
             hbm_budget = int(0.8 * free)
         self.budget = int(hbm_budget)
         self.mode = mode
+        # launch shape of each request's select (None: the plan's default).  One
+        # launch per step (0) lets the other requests' kernels share the GPU
+        # with a select; a cooperative launch holds every SM it spans for all
+        # k steps.  The results are the same either way.
+        self.select_ctas = select_ctas
         self.used = 0
         self.peak_used = 0
         self.running = 0
@@ -139,7 +144,8 @@ class Server:
                 return
             try:
                 with torch.cuda.stream(stream):
-                    req.result = run_one(req.A, req.k, req.l, req.seed, req.nprobe, req.probe_seed, self.mode, stream)
+                    req.result = run_one(req.A, req.k, req.l, req.seed, req.nprobe, req.probe_seed, self.mode, stream,
+                                         self.select_ctas)
             except Exception as exc:        # reported with the request, the server keeps running
                 req.error = exc
             req.t_done = time.perf_counter()
@@ -150,13 +156,17 @@ class Server:
                 self.cv.notify_all()
 
 
-def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None):
+def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None, select_ctas=None):
     """One whole ID on `stream`; returns host copies of J, T and the estimate.
     In the FP64 modes the error comes from row probes that the sketch
-    multiplies in its one pass over A; the mixed mode takes column probes."""
+    multiplies in its one pass over A; the mixed mode takes column probes.
+    select_ctas (None: the plan's default) sets the select's launch shape;
+    the results do not depend on it."""
     m, n = A.shape
     stream = stream or torch.cuda.current_stream(A.device)
     with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream) as plan:
+        if select_ctas is not None:
+            plan.set_select_grid(select_ctas)
         rows = mode in ROW_PROBE_MODES
         if rows:
             plan.set_probes(nprobe, probe_seed)

@@ -86,4 +86,5 @@ def test_calls_reject_null_plan(lib):
     assert lib.rid_error(None, None, 1, None, None, 1, 8, 1, out) == E
     assert lib.rid_sync_status(None) == E
     assert lib.rid_plan_set_omega(None, None, 1) == E
+    assert lib.rid_plan_set_select_grid(None, 0) == E
     assert lib.rid_plan_destroy(None) == _native.RID_OK

@@ -32,14 +32,16 @@ def make_requests(count, seed):
     return reqs
 
 
-@pytest.mark.parametrize("mode", ["fp64_emulated", "fp64"])
-def test_served_results_equal_solo_results(serve, mode):
+@pytest.mark.parametrize("mode,select_ctas", [("fp64_emulated", None), ("fp64", None), ("fp64_emulated", 0)])
+def test_served_results_equal_solo_results(serve, mode, select_ctas):
+    # select_ctas = 0: the served selects run one launch per step; the solo
+    # runs keep the default cooperative launch, and the bits must not change
     reqs = make_requests(10, seed=1)
     dev = {i: to_dev_colmajor(A) for (i, A, k, l, s) in reqs}
     solo = {i: serve.run_one(dev[i], k, l, s, mode=mode) for (i, A, k, l, s) in reqs}
     torch.cuda.synchronize()
     budget = 3 * max(serve.footprint(*A.shape, k, l, mode=mode) for (i, A, k, l, s) in reqs)
-    srv = serve.Server(slots=4, hbm_budget=budget, mode=mode)
+    srv = serve.Server(slots=4, hbm_budget=budget, mode=mode, select_ctas=select_ctas)
     try:
         handles = [srv.submit(i, dev[i], k, l, s) for (i, A, k, l, s) in reqs]
         done = srv.drain(timeout=300)
