@@ -207,7 +207,7 @@ const char* rid_status_string(rid_status s) {
 static rid_status check_plan_args(int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype, rid_mode mode) {
   if (m < 1 || n < 1 || k < 1 || l < k || k > m || k > n) return RID_EINVAL;
   if (n > 0x7fffffffLL || m > ((int64_t)1 << 40)) return RID_EINVAL;
-  if (l > 512) return RID_EUNSUPPORTED;
+  if (l > 512) return RID_EUNSUPPORTED;   // the QR keeps a column's l entries in one warp's registers
   if (dtype != RID_C128 && dtype != RID_C64) return RID_EINVAL;
   if (mode < RID_FP64_NATIVE || mode > RID_MIXED_3XTF32) return RID_EINVAL;
   if (dtype == RID_C128 && (mode == RID_MIXED_BF16 || mode == RID_MIXED_3XTF32)) return RID_EUNSUPPORTED;
@@ -247,15 +247,8 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
                            rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream) {
   if (!plan) return RID_EINVAL;
   *plan = nullptr;
-  if (m < 1 || n < 1 || k < 1 || l < k || k > m || k > n) return RID_EINVAL;
-  if (n > 0x7fffffffLL || m > ((int64_t)1 << 40)) return RID_EINVAL;
-  if (l > 512) return RID_EUNSUPPORTED;   // the QR keeps a column's l entries in one warp's registers
-  if (dtype != RID_C128 && dtype != RID_C64) return RID_EINVAL;
-  if (mode < RID_FP64_NATIVE || mode > RID_MIXED_3XTF32) return RID_EINVAL;
-  if (dtype == RID_C128 && (mode == RID_MIXED_BF16 || mode == RID_MIXED_3XTF32)) return RID_EUNSUPPORTED;
-  if (dtype == RID_C64 && (mode == RID_FP64_NATIVE || mode == RID_FP64_EMULATED)) return RID_EUNSUPPORTED;
-  int nr = 0;
-  if (rid_solve_smem_bytes(k, &nr) > 200 * 1024) return RID_EUNSUPPORTED;
+  const rid_status chk = check_plan_args(m, n, k, l, dtype, mode);
+  if (chk != RID_OK) return chk;
 
   rid_plan_s* p = (rid_plan_s*)calloc(1, sizeof(rid_plan_s));
   if (!p) return RID_ENOMEM;
