@@ -8,7 +8,11 @@ matrix m = 262144, n = 8192 (k = 200, l = 208), inputs resident in HBM.
 Prints one JSON line (rank 0).  With N > 1 (torchrun) every rank decomposes
 its own matrix (independent problems, no collective on the data path) and
 the value is the total over ranks (weak scaling).  --impl reference times
-the CPU oracle on a bounded column slab of the same workload.
+the CPU oracle on a bounded column slab of the same workload.  At N = 1 the
+line also carries, after the timed region, the end-to-end figure from host
+buffers (`e2e`), the 24-bit test matrix variant, the CPU oracle and a
+serving sample (`serving`: served IDs/s with p50 / p99 latency); the other
+workloads run with --config (mixed_c64, batched, serving, ...).
 """
 from __future__ import annotations
 
