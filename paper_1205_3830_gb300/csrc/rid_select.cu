@@ -6,12 +6,13 @@
 // between the dot product and the update, and recomputes its remaining norm
 // sum_{i>j} |Y_ic|^2 exactly.  Ties of the pivot norms go to the lowest column
 // index; reflectors follow LAPACK's zlarfg convention.
-//   - Plans: all k steps in one cooperative launch with a bounded grid
-//     barrier per step (select_coop_kernel, below).
-//   - The allocation-free entry: one launch per step; the last CTA to finish
-//     (a fence and an atomic ticket, so no CTA waits on another) reduces the
-//     posted (norm, column) pairs, swaps the pivot column into place and forms
-//     the next reflector.
+//   - Plans by default: all k steps in one cooperative launch with a bounded
+//     grid barrier per step (select_coop_kernel, below).
+//   - The allocation-free entry, plans set to it (rid_plan_set_select_grid
+//     with 0) and devices without cooperative launch: one launch per step;
+//     the last CTA to finish (a fence and an atomic ticket, so no CTA waits on
+//     another) reduces the posted (norm, column) pairs, swaps the pivot column
+//     into place and forms the next reflector.
 #include <climits>
 
 #include "rid_internal.cuh"
