@@ -7,7 +7,10 @@ the outputs Y, perm, T) fits in the HBM budget next to the requests already
 running; otherwise it waits, first come first served.  Each slot is a worker
 thread with its own CUDA stream, so admitted requests run concurrently on the
 device; a request's whole ID runs on its slot's stream, its memory is freed
-when it completes and the next request is admitted at once.
+when it completes and the next request is admitted at once.  By default a
+request's pivoted QR runs as one launch per step rather than one cooperative
+launch, so it never holds the whole GPU while the other slots wait (the
+results are the same bits).
 
 Latency is measured from submit() to the moment the result (J, T, the error
 estimate) is available on the host side of the worker.
