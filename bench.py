@@ -35,7 +35,7 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
 # valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
-TC_TRAFFIC = {"bytes_per_launch": 80.4e9,   # 16 x (4.898 + 0.127) GB, profiles/sketch_tc_kernel_65536x2048.md
+TC_TRAFFIC = {"bytes_per_launch": 80.4e9,   # 16 x (4.898 + 0.127) GB: the 65536 x 2048 capture, scaled by A's entries
               "source_sha1": "b2f7ed03c64df6320efa7a71b04e096a46b9a50a"}
 
 
