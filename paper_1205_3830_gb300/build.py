@@ -1,7 +1,8 @@
 """Build the native library librid.so for sm_103a (GB300) with nvcc.
 
 Each .cu file under csrc/ is compiled in parallel to an object, then linked
-into _build/librid.so.  A source newer than the library triggers a rebuild.
+into _build/librid.so.  A source or header newer than the library triggers a
+rebuild.
 """
 from __future__ import annotations
 
