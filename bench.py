@@ -725,7 +725,7 @@ def serve_sweep(args, rates, requests, rank, local):
             if wait > 0:
                 time.sleep(wait)
             srv.submit(i, mats[i], k, l, 2000 + i, args.nprobe, 1)
-        done = srv.drain()
+        done = srv.drain(timeout=600)            # a stuck request ends the sweep with an error, not a hang
         wall = time.perf_counter() - t0
         srv.close()
         errs = sum(1 for r in done if r.error is not None)
