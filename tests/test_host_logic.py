@@ -26,17 +26,26 @@ class _FakeProc:
         return 0
 
 
-def _sampler_with(bench, tmp_path, lines):
-    path = tmp_path / "clocks.csv"
-    path.write_text("\n".join(lines) + "\n")
+@pytest.fixture
+def scratch():
+    # inside the package's git-ignored build folder, so the test writes nothing outside the repository
+    d = os.path.join(ROOT, "paper_1205_3830_gb300", "_build", "host_logic_tests")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def _sampler_with(bench, scratch, lines):
+    path = os.path.join(scratch, "clocks.csv")
+    with open(path, "w") as f:
+        f.write("\n".join(lines) + "\n")
     s = bench.ClockSampler(0)
-    s.path = str(path)
+    s.path = path
     s.f = open(os.devnull, "w")
     s.proc = _FakeProc()
     return s
 
 
-def test_clock_sampler_median_and_reasons(bench, tmp_path):
+def test_clock_sampler_median_and_reasons(bench, scratch):
     # fields: index, clocks.sm, clocks.max.sm, power, active mask, hw_slowdown,
     # hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap
     lines = ["0, 2070, 2070, 1210.5, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
@@ -44,19 +53,19 @@ def test_clock_sampler_median_and_reasons(bench, tmp_path):
              "0, 2010, 2070, 1390.0, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
              "garbage line",
              "0, [N/A], 2070, 1390.0, 0x0, Not Active, Not Active, Not Active, Not Active"]
-    out = _sampler_with(bench, tmp_path, lines).stop()
+    out = _sampler_with(bench, scratch, lines).stop()
     assert out == {"sm_mhz": 2010.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
-    assert not os.path.exists(tmp_path / "clocks.csv")       # the sample file is removed
+    assert not os.path.exists(os.path.join(scratch, "clocks.csv"))     # the sample file is removed
 
 
-def test_clock_sampler_reports_thermal_slowdown(bench, tmp_path):
+def test_clock_sampler_reports_thermal_slowdown(bench, scratch):
     lines = ["0, 1500, 2070, 900.0, 0x0000000000000040, Active, Active, Not Active, Not Active"]
-    out = _sampler_with(bench, tmp_path, lines).stop()
+    out = _sampler_with(bench, scratch, lines).stop()
     assert out["reasons"] == ["hw_slowdown", "hw_thermal_slowdown"]
 
 
-def test_clock_sampler_without_samples(bench, tmp_path):
-    assert _sampler_with(bench, tmp_path, ["only garbage"]).stop() is None
+def test_clock_sampler_without_samples(bench, scratch):
+    assert _sampler_with(bench, scratch, ["only garbage"]).stop() is None
     s = bench.ClockSampler(0)                 # never started (no nvidia-smi)
     assert s.stop() is None
 
