@@ -88,3 +88,22 @@ def test_calls_reject_null_plan(lib):
     assert lib.rid_plan_set_omega(None, None, 1) == E
     assert lib.rid_plan_set_select_grid(None, 0) == E
     assert lib.rid_plan_destroy(None) == _native.RID_OK
+
+
+def test_plain_c99_consumer_compiles_links_and_runs(lib):
+    """include/rid.h is a C header: a C99 program compiles against it with
+    -pedantic -Werror, links librid.so and gets the documented statuses from
+    the calls that need no GPU (tests/c/abi_consumer.c)."""
+    import shutil
+    from paper_1205_3830_gb300 import _native
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    libdir = os.path.dirname(_native.LIB_PATH)
+    exe = os.path.join(libdir, "abi_consumer")
+    subprocess.run([gcc, "-std=c99", "-pedantic", "-Wall", "-Wextra", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    os.path.join(ROOT, "tests", "c", "abi_consumer.c"), "-L", libdir, "-lrid",
+                    "-Wl,-rpath," + libdir, "-o", exe], check=True, capture_output=True, text=True)
+    r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == "ok"
