@@ -141,10 +141,13 @@ RID_API rid_status rid_select(rid_plan_t plan, void* Y, int64_t ldy, int32_t* pe
  *   default) CTAs, each step ending in a grid barrier;
  *   ctas == 0: one launch per step, and no CTA ever waits on another, so
  *   kernels of other streams can share the GPU with it;
- *   ctas < 0: back to the plan's default (chosen at rid_plan_create: one
- *   cooperative launch filling the GPU, where the device supports it).
- * RID_EUNSUPPORTED for ctas > 0 when the device has no cooperative launch.
- * No device work; takes effect at the next rid_select. */
+ *   ctas < 0: back to the plan's default, chosen at rid_plan_create: one
+ *   cooperative launch of as many CTAs as the GPU holds at once, but no more
+ *   than one per 16 columns, where the device supports cooperative launch;
+ *   otherwise one launch per step.
+ * RID_EINVAL for a null plan; RID_EUNSUPPORTED for ctas > 0 when the device
+ * has no cooperative launch.  No device work; takes effect at the next
+ * rid_select. */
 RID_API rid_status rid_plan_set_select_grid(rid_plan_t plan, int32_t ctas);
 
 /* Factorization of R, Sec. 2 "R2 = R1 T":  T = R1^-1 R2 by back substitution,
