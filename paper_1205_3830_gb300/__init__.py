@@ -46,6 +46,33 @@ def as_colmajor(x):
     return x.t().contiguous().t()
 
 
+def _need(cond, msg):
+    """Argument check that survives python -O: the kernels trust these shapes."""
+    if not cond:
+        raise ValueError(msg)
+
+
+def _check_matrix(x, name, rows, cols, dtype, exact=False):
+    """x: a column-major CUDA tensor of `dtype` with at least (exactly, if
+    `exact`) rows x cols entries; the kernels read and write rows x cols."""
+    _need(isinstance(x, torch.Tensor) and x.is_cuda, f"{name} must be a CUDA tensor")
+    _need(x.dtype == dtype, f"{name} must be {dtype}, got {x.dtype}")
+    _need(x.dim() == 2, f"{name} must be a matrix")
+    if exact:
+        _need(tuple(x.shape) == (rows, cols), f"{name} must be {rows} x {cols}, got {tuple(x.shape)}")
+    else:
+        _need(x.shape[0] >= rows and x.shape[1] >= cols,
+              f"{name} must hold at least {rows} x {cols}, got {tuple(x.shape)}")
+    _need(x.numel() == 0 or x.stride(0) == 1, f"{name} must be column-major (use as_colmajor)")
+
+
+def _check_perm(perm, n):
+    _need(isinstance(perm, torch.Tensor) and perm.is_cuda and perm.dtype == torch.int32,
+          "perm must be an int32 CUDA tensor")
+    _need(perm.numel() >= n and (perm.dim() == 1 and perm.stride(0) == 1),
+          f"perm must be a contiguous vector of at least {n} entries")
+
+
 def _ld(x):
     if x.dim() < 2:
         return max(int(x.shape[0]) if x.dim() else 1, 1)
@@ -119,7 +146,7 @@ class Plan:
         omega = omega.to(device=self.device, dtype=torch.complex128)
         if omega.stride(1) != 1:
             omega = omega.contiguous()
-        assert tuple(omega.shape) == (self.l, self.m)
+        _need(tuple(omega.shape) == (self.l, self.m), f"omega must be {self.l} x {self.m}")
         check(self._lib.rid_plan_set_omega(self._h, ctypes.c_void_p(omega.data_ptr()), omega.stride(0)),
               "rid_plan_set_omega")
         self._keep = omega
@@ -131,10 +158,10 @@ class Plan:
     # -- the four steps --------------------------------------------------------
     def sketch(self, A, Y=None):
         """Y = Omega A (l x n complex128, column-major)."""
-        assert A.is_cuda and A.dtype == self.dtype and tuple(A.shape) == (self.m, self.n)
-        assert A.stride(0) == 1, "A must be column-major (use as_colmajor)"
+        _check_matrix(A, "A", self.m, self.n, self.dtype, exact=True)
         if Y is None:
             Y = colmajor_empty(self.l, self.n, torch.complex128, self.device)
+        _check_matrix(Y, "Y", self.l, self.n, torch.complex128)
         check(self._lib.rid_sketch(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
                                    ctypes.c_void_p(Y.data_ptr()), _ld(Y)), "rid_sketch")
         return Y
@@ -142,7 +169,8 @@ class Plan:
     def sketch_cols(self, A, Y, col0, ncols):
         """Columns col0 .. col0 + ncols - 1 of Y = Omega A (A, Y: the whole
         matrices); panels covering every column give sketch()'s Y bit for bit."""
-        assert A.is_cuda and A.dtype == self.dtype and tuple(A.shape) == (self.m, self.n) and A.stride(0) == 1
+        _check_matrix(A, "A", self.m, self.n, self.dtype, exact=True)
+        _check_matrix(Y, "Y", self.l, self.n, torch.complex128)
         check(self._lib.rid_sketch_cols(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
                                         ctypes.c_void_p(Y.data_ptr()), _ld(Y), int(col0), int(ncols)),
               "rid_sketch_cols")
@@ -150,18 +178,20 @@ class Plan:
 
     def select(self, Y, perm=None):
         """Pivoted QR of Y in place; returns perm (int32[n], J = perm[:k])."""
-        assert Y.is_cuda and Y.dtype == torch.complex128 and Y.stride(0) == 1
+        _check_matrix(Y, "Y", self.l, self.n, torch.complex128)
         if perm is None:
             perm = torch.empty(self.n, dtype=torch.int32, device=self.device)
+        _check_perm(perm, self.n)
         check(self._lib.rid_select(self._h, ctypes.c_void_p(Y.data_ptr()), _ld(Y),
                                    ctypes.c_void_p(perm.data_ptr())), "rid_select")
         return perm
 
     def solve(self, Y, T=None):
         """T = R1^-1 R2 (k x (n-k) complex128, column-major)."""
-        assert Y.is_cuda and Y.dtype == torch.complex128 and Y.stride(0) == 1
+        _check_matrix(Y, "Y", self.k, self.n, torch.complex128)
         if T is None:
             T = colmajor_empty(self.k, self.n - self.k, torch.complex128, self.device)
+        _check_matrix(T, "T", self.k, self.n - self.k, torch.complex128)
         ptr = T.data_ptr() if T.numel() else 0
         check(self._lib.rid_solve(self._h, ctypes.c_void_p(Y.data_ptr()), _ld(Y), ctypes.c_void_p(ptr),
                                   max(_ld(T), self.k)), "rid_solve")
@@ -169,7 +199,9 @@ class Plan:
 
     def error(self, A, perm, T, nprobe=8, probe_seed=1):
         """(est, upper) of ||A - A(:, J) P||_2 by nprobe Gaussian probes (synchronizes)."""
-        assert A.is_cuda and A.stride(0) == 1
+        _check_matrix(A, "A", self.m, self.n, self.dtype, exact=True)
+        _check_perm(perm, self.n)
+        _check_matrix(T, "T", self.k, self.n - self.k, torch.complex128)
         out = (ctypes.c_double * 2)()
         ptr = T.data_ptr() if T.numel() else 0
         check(self._lib.rid_error(self._h, ctypes.c_void_p(A.data_ptr()), _ld(A),
@@ -195,6 +227,8 @@ class Plan:
     def error_sketched(self, perm, T):
         """(est, upper) of ||A - A(:, J) P||_2 from the row probes of the last
         sketch: no pass over A (synchronizes)."""
+        _check_perm(perm, self.n)
+        _check_matrix(T, "T", self.k, self.n - self.k, torch.complex128)
         out = (ctypes.c_double * 2)()
         ptr = T.data_ptr() if T.numel() else 0
         check(self._lib.rid_error_sketched(self._h, ctypes.c_void_p(perm.data_ptr()), ctypes.c_void_p(ptr),
@@ -249,7 +283,7 @@ class Batch:
         self.Y, self.perm, self.T, self.A = [], [], [], []
         items = (_native.BatchItem * len(problems))()
         for i, (A, k, l, seed) in enumerate(problems):
-            assert A.is_cuda and A.dtype == torch.complex128 and A.stride(0) == 1
+            _check_matrix(A, f"problem {i}: A", 1, 1, torch.complex128)
             m, n = A.shape
             Y = colmajor_empty(l, n, device=self.device)
             perm = torch.empty(n, dtype=torch.int32, device=self.device)
@@ -352,7 +386,7 @@ class BatchTC:
         self.Y, self.perm, self.T, self.A = [], [], [], []
         items = (_native.BatchItem * len(problems))()
         for i, (A, k, l, seed) in enumerate(problems):
-            assert A.is_cuda and A.dtype == torch.complex128 and A.stride(0) == 1
+            _check_matrix(A, f"problem {i}: A", 1, 1, torch.complex128)
             m, n = A.shape
             Y = colmajor_empty(l, n, device=self.device)
             perm = torch.empty(n, dtype=torch.int32, device=self.device)

@@ -101,3 +101,19 @@ def test_workload_config_names_the_workload(bench):
     args.omega, args.omega_bits = "srft", 24
     c = bench.workload_config(cfg, args)
     assert c["omega"].startswith("subsampled randomized Fourier transform") and "24 bits" in c["omega"]
+
+
+def test_binding_argument_checks_raise_value_errors():
+    """The binding's checks raise (they do not vanish under python -O like
+    asserts would): host tensors, non-tensors and wrong perm types."""
+    import torch
+    import paper_1205_3830_gb300 as rid
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        rid._check_matrix(torch.zeros((4, 3), dtype=torch.complex128).t(), "Y", 3, 4, torch.complex128)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        rid._check_matrix([[0j]], "A", 1, 1, torch.complex128)
+    with pytest.raises(ValueError, match="int32 CUDA tensor"):
+        rid._check_perm(torch.arange(5, dtype=torch.int32), 5)
+    with pytest.raises(ValueError, match="omega"):
+        rid._need(False, "omega must be 2 x 3")
+    rid._need(True, "never raised")
