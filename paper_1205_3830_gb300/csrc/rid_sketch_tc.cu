@@ -32,9 +32,8 @@
 // holds S A-slice tiles and S Omega-slice tiles.  The slicers write the digits
 // in exactly that shared-memory image, tile after tile, so a stage's A tiles
 // are one contiguous block in memory and arrive by one bulk copy (rather than
-// a tensor copy of 64-byte rows per tile).  The N-tiles of one column block
-// form a cluster: each A tile is loaded once and multicast to them, and a
-// stage is released by a multicast commit.  A K-split over CTAs balances
+// a tensor copy of 64-byte rows per tile).  Every CTA loads its own tiles:
+// nothing is multicast between CTAs.  A K-split over CTAs balances
 // the waves; partial sums are reduced in a fixed order, so results are
 // deterministic.  Row probes (rows l.. of Omega) are sliced and multiplied
 // like the test matrix's rows and reduced into X instead of Y.
@@ -348,8 +347,8 @@ __global__ void __launch_bounds__(256) a_slice_kernel(const TA* __restrict__ A, 
 
 // ---- the tensor-core product ----------------------------------------------------------
 // Two forms of one kernel.  Single CTAs (PAIR = false): M = 128 columns of A
-// per CTA; a cluster holds the N-tiles of one column block, which share its A
-// tiles by multicast.  CTA pairs (PAIR = true): one tcgen05 MMA of M = 256
+// per CTA, each CTA loading its own A and Omega tiles (clusters of 1).  CTA
+// pairs (PAIR = true): one tcgen05 MMA of M = 256
 // (cta_group::2) covers two column blocks; each CTA of the pair holds its
 // block's A tiles and half of the N-tile's Omega rows, and the tensor cores of
 // the pair read each half once.  That halves the Omega bytes per CTA (shared
@@ -469,7 +468,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
     if (s_abort) atomicCAS(a.err, 0, 1);
   }
   tc_fence_before();
-  cluster_sync();          // barriers of every CTA initialised before any multicast
+  cluster_sync();          // a pair's barriers initialised before the other CTA signals them
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
 
@@ -487,10 +486,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
     asm volatile("setmaxnreg.dec.sync.aligned.u32 56;\n" ::: "memory");
     if (warp == 12 && lane == 0) {
       // ---------------- TMA producer ----------------
-      // Single: this CTA loads A tiles [s0, s1) of each stage for the whole
-      // cluster.  Pairs: this CTA's own A tiles.  Then its Omega tiles.  Each
-      // is one contiguous block of the tile arrays.
-      const int s0 = PAIR ? 0 : (int)my_rank * TC_S / a.cx, s1 = PAIR ? TC_S : ((int)my_rank + 1) * TC_S / a.cx;
+      // This CTA's A tiles of each stage (a cluster of one, or its half of a
+      // pair), then its Omega tiles; each is one contiguous block of the tile
+      // arrays.
+      const int s0 = 0, s1 = TC_S;
       const int o_elems = (int)(a.o_tile_smem / 2);
       const int64_t st0 = (int64_t)c_begin * TC_SPC;            // first K stage of this split
       const uint16_t* a_src = a.a_tiles + ((jb * a.nst + st0) * TC_S + s0) * TC_TILE_ELEMS;
@@ -508,8 +507,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
         // the stage's 2S tiles arrive here whoever issued them
         mbar_arrive_expect_tx(&full_bar[slot], a.stage_bytes);
         if (a_bytes) {
-          if (PAIR) bulk_load(a_tile(slot, s0), a_src, a_bytes, &full_bar[slot]);
-          else bulk_load_multicast(a_tile(slot, s0), a_src, a_bytes, &full_bar[slot], all_mask);
+          bulk_load(a_tile(slot, s0), a_src, a_bytes, &full_bar[slot]);
         }
         bulk_load(o_tile(slot, 0), o_src, o_bytes, &full_bar[slot]);
         a_src += TC_S * TC_TILE_ELEMS;        // next K stage
@@ -559,7 +557,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
             break;
           }
           if (PAIR) mma_commit_pair_multicast(&empty_bar[slot], all_mask);
-          else mma_commit_multicast(&empty_bar[slot], all_mask);
+          else mma_commit(&empty_bar[slot]);
           if (++slot == NS) {
             slot = 0;
             ++round;
@@ -780,11 +778,10 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
     return RID_EUNSUPPORTED;
   }
   st->dyn_smem = (int)(st->nstages * st->stage_smem + 1024);
-  // Single CTAs: a cluster holds the N-tiles of one column block (they share
-  // its A tiles; sharing Omega tiles across column blocks too measured
-  // slower: larger clusters pack GPCs less densely and run in lockstep).
+  // Single CTAs: clusters of one (each CTA loads its own A tiles; sharing
+  // them across the N-tiles of a column block by multicast bought about 1 %).
   // Pairs: a cluster is the pair.
-  st->cx = st->pair ? 2 : st->ntiles;
+  st->cx = st->pair ? 2 : 1;
   const int units = st->pair ? st->ntiles * ((st->nblocks + 1) / 2) : st->nblocks;   // clusters per K-split
   {
     // how many clusters of this shape are resident at once
