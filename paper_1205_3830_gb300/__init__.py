@@ -56,6 +56,13 @@ def _check_matrix(x, name, rows, cols, dtype, exact=False):
     """x: a column-major CUDA tensor of `dtype` with at least (exactly, if
     `exact`) rows x cols entries; the kernels read and write rows x cols."""
     _need(isinstance(x, torch.Tensor) and x.is_cuda, f"{name} must be a CUDA tensor")
+    _check_layout(x, name, rows, cols, dtype, exact)
+
+
+def _check_layout(x, name, rows, cols, dtype, exact=False):
+    """The device-independent part of _check_matrix: dtype, shape and a
+    column-major layout whose columns do not overlap."""
+    _need(isinstance(x, torch.Tensor), f"{name} must be a tensor")
     _need(x.dtype == dtype, f"{name} must be {dtype}, got {x.dtype}")
     _need(x.dim() == 2, f"{name} must be a matrix")
     if exact:
@@ -63,7 +70,13 @@ def _check_matrix(x, name, rows, cols, dtype, exact=False):
     else:
         _need(x.shape[0] >= rows and x.shape[1] >= cols,
               f"{name} must hold at least {rows} x {cols}, got {tuple(x.shape)}")
-    _need(x.numel() == 0 or x.stride(0) == 1, f"{name} must be column-major (use as_colmajor)")
+    # the row stride of a one-row matrix and the column stride of a
+    # one-column matrix are never used; every other column must start at
+    # least `rows` entries after the previous one (no overlapping views)
+    _need(x.numel() == 0 or x.shape[0] <= 1 or x.stride(0) == 1,
+          f"{name} must be column-major (use as_colmajor)")
+    _need(x.numel() == 0 or x.shape[1] <= 1 or x.stride(1) >= max(1, x.shape[0]),
+          f"{name} has overlapping columns (stride(1) = {x.stride(1)} < {x.shape[0]} rows)")
 
 
 def _check_perm(perm, n):
@@ -74,8 +87,12 @@ def _check_perm(perm, n):
 
 
 def _ld(x):
+    """Leading dimension of a column-major matrix view: its column stride, at
+    least its row count (a one-column view's stride(1) is arbitrary)."""
     if x.dim() < 2:
         return max(int(x.shape[0]) if x.dim() else 1, 1)
+    if x.shape[1] <= 1:
+        return max(int(x.shape[0]), 1)
     return max(int(x.stride(1)), int(x.shape[0]), 1)
 
 

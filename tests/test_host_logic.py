@@ -117,3 +117,66 @@ def test_binding_argument_checks_raise_value_errors():
     with pytest.raises(ValueError, match="omega"):
         rid._need(False, "omega must be 2 x 3")
     rid._need(True, "never raised")
+
+
+# ---- the binding's layout checks (CPU tensors; the device check is separate) ----
+
+def _layout(x, rows, cols, exact=False):
+    import torch
+    import paper_1205_3830_gb300 as rid
+    rid._check_layout(x, "x", rows, cols, torch.complex128, exact)
+    return rid._ld(x)
+
+
+def test_layout_accepts_one_row_views_of_any_row_stride():
+    import torch
+    import paper_1205_3830_gb300 as rid
+    # a k = 1 interpolation matrix: 1 x (n - k); torch treats the size-1 dim as
+    # contiguous, so as_colmajor may leave stride(0) = n - k
+    T = torch.zeros(1, 333 - 1, dtype=torch.complex128)
+    assert T.stride() == (332, 1)
+    assert _layout(T, 1, 332, exact=True) == 1
+    assert _layout(rid.as_colmajor(T), 1, 332, exact=True) == 1
+    Tc = torch.zeros(332, 1, dtype=torch.complex128).t()          # (1, 332) with strides (1, 1)
+    assert _layout(Tc, 1, 332) == 1
+
+
+def test_layout_accepts_one_column_views_of_any_column_stride():
+    import torch
+    x = torch.zeros(7, 1, dtype=torch.complex128)                   # strides (1, 1)
+    assert _layout(x, 7, 1) == 7
+    y = torch.zeros(5, 7, dtype=torch.complex128).t()[:, :1]        # (7, 1) with strides (1, 7)
+    assert _layout(y, 7, 1) == 7
+
+
+def test_layout_ld_is_the_column_stride_of_a_submatrix():
+    import torch
+    big = torch.zeros(10, 12, dtype=torch.complex128).t()           # 12 x 10, ld 12
+    sub = big[:5, :4]
+    assert _layout(sub, 5, 4) == 12
+
+
+def test_layout_rejects_row_major_and_overlapping_views():
+    import torch
+    rowmajor = torch.zeros(4, 6, dtype=torch.complex128)
+    with pytest.raises(ValueError, match="column-major"):
+        _layout(rowmajor, 4, 6)
+    col = torch.zeros(4, 1, dtype=torch.complex128)
+    expanded = col.expand(4, 6)                                     # stride(1) = 0: every column the same memory
+    assert expanded.stride() == (1, 0)
+    with pytest.raises(ValueError, match="overlapping"):
+        _layout(expanded, 4, 6)
+    overlap = torch.zeros(20, dtype=torch.complex128).as_strided((4, 3), (1, 2))
+    with pytest.raises(ValueError, match="overlapping"):
+        _layout(overlap, 4, 3)
+
+
+def test_layout_rejects_wrong_shape_and_dtype():
+    import torch
+    x = torch.zeros(3, 4, dtype=torch.complex128).t()
+    with pytest.raises(ValueError, match="must be 3 x 4"):
+        _layout(x, 3, 4, exact=True)
+    with pytest.raises(ValueError, match="at least"):
+        _layout(x, 5, 3)
+    with pytest.raises(ValueError, match="complex128"):
+        _layout(x.to(torch.complex64), 4, 3)
