@@ -323,8 +323,33 @@ def pin_srft(o):
     assert np.abs(Y - Yf).max() <= 1e-12 * np.abs(Yf).max()
 
 
+def pin_srft_distribution(o):
+    """The SRFT's random parts (Sec. 2): phases phi uniform on [0, 1), row
+    samples s uniform on {0..m-1}, drawn independently of Omega's stream and of
+    each other."""
+    m = 20000
+    phi, _ = o.srft_parameters(4, m, seed=9)
+    assert phi.min() >= 0.0 and phi.max() < 1.0
+    assert scipy.stats.kstest(phi, "uniform").pvalue > 1e-4
+    assert abs(np.corrcoef(phi[:-1], phi[1:])[0, 1]) < 0.03        # no serial dependence
+    # independent of the Gaussian test matrix drawn under the same seed: the
+    # angle of Omega's row-0 entries is that stream's uniform at the same counter
+    om = o.gaussian_test_matrix(1, m, seed=9)[0]
+    u_om = np.mod(np.angle(om) / (2.0 * np.pi), 1.0)
+    assert abs(np.corrcoef(phi, u_om)[0, 1]) < 0.03
+    assert np.mean(np.abs(phi - u_om) < 1e-12) < 0.01
+    for m_s, l_s in ((16, 16000), (1000, 50000)):
+        _, s = o.srft_parameters(l_s, m_s, seed=4)
+        assert s.dtype.kind == "i" and s.min() >= 0 and s.max() < m_s
+        counts = np.bincount(s, minlength=m_s)
+        assert scipy.stats.chisquare(counts).pvalue > 1e-4, m_s
+    phi2, s2 = o.srft_parameters(20000, 20000, seed=4)
+    assert abs(np.corrcoef(phi2, s2 / 20000.0)[0, 1]) < 0.03       # phases and samples independent
+
+
 ALL_PINS = [
     pin_philox_kat, pin_uniform53, pin_gaussian_distribution, pin_randomize_exact,
     pin_qr_lapack, pin_qr_pivot_rule, pin_rank_deficient, pin_factor_r, pin_exact_rank,
     pin_spectrum_bound, pin_brute_force, pin_error_estimate, pin_error_estimate_left, pin_round_test_matrix, pin_srft,
+    pin_srft_distribution,
 ]

@@ -54,6 +54,13 @@ MUTATIONS = [
      [pins.pin_srft]),
     ("srft_dft_sign", "F_rows = np.exp(-2j * np.pi * (jk / m))", "F_rows = np.exp(2j * np.pi * (jk / m))",
      [pins.pin_srft]),
+    ("srft_phase_half_range", "    return phi, s\n", "    return phi * 0.5, s\n", [pins.pin_srft_distribution]),
+    ("srft_sample_biased", "s = np.minimum(np.floor(u * m)", "s = np.minimum(np.floor(u * u * m)",
+     [pins.pin_srft_distribution]),
+    ("srft_sample_drops_last", "s = np.minimum(np.floor(u * m)", "s = np.minimum(np.floor(u * (m - 1))",
+     [pins.pin_srft_distribution]),
+    ("srft_phase_omega_stream", "    ctr[:, 2] = 0\n    ctr[:, 3] = STREAM_SRFT", "    ctr[:, 2] = 0\n    ctr[:, 3] = STREAM_OMEGA",
+     [pins.pin_srft_distribution]),
 ]
 
 
