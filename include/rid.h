@@ -141,10 +141,13 @@ RID_API rid_status rid_select(rid_plan_t plan, void* Y, int64_t ldy, int32_t* pe
  *   default) CTAs, each step ending in a grid barrier;
  *   ctas == 0: one launch per step, and no CTA ever waits on another, so
  *   kernels of other streams can share the GPU with it;
- *   ctas < 0: back to the plan's default, chosen at rid_plan_create: one
- *   cooperative launch of as many CTAs as the GPU holds at once, but no more
- *   than one per 16 columns, where the device supports cooperative launch;
- *   otherwise one launch per step.
+ *   ctas < 0: back to the plan's default, chosen at rid_plan_create, where
+ *   the device supports cooperative launch: for l <= 256, when Y's columns
+ *   fit in the shared memory of one CTA per SM, one cooperative launch that
+ *   keeps them there for all k steps (no column crosses L2 between steps);
+ *   otherwise one cooperative launch of as many CTAs as the GPU holds at
+ *   once, but no more than one per 16 columns.  Without cooperative launch:
+ *   one launch per step.
  * RID_EINVAL for a null plan; RID_EUNSUPPORTED for ctas > 0 when the device
  * has no cooperative launch.  No device work; takes effect at the next
  * rid_select. */
@@ -247,9 +250,33 @@ RID_API rid_status rid_plan_stats(rid_plan_t plan, int64_t out[8]);
  *   records them on the plan's stream around its kernels.  If out (HOST,
  *   double[3]) is not NULL, waits for the last rid_sketch and returns its
  *   times in ms: out[0] = digit slicing of A (0 in the native mode),
- *   out[1] = the product kernel, out[2] = the split-K reduction.
+ *   out[1] = the product kernel, out[2] = the split-K reduction.  In the
+ *   FP64-emulated mode a wide A is sliced and multiplied in up to four
+ *   column panels (the plan's digit tiles hold one panel); out[0] and out[1]
+ *   are then the sums over the panels.
  *   RID_EINVAL if out is given before timing was enabled. */
 RID_API rid_status rid_plan_timing(rid_plan_t plan, int32_t enable, double out[3]);
+
+/* The sketch's accuracy against the plan's mode, read after rid_select.  The
+ * ID's error is governed by sigma_{k+1} (Sec. 2, Eq. 1); a sketch computed in
+ * low precision resolves only a spectrum that decays less than its own noise.
+ *   Y: the rid_select output of this plan (DEVICE, l x n, ldy >= l): R in rows
+ *   0..k-1, and in rows k..l-1 of columns k..n-1 what the k reflectors left.
+ *   out (HOST, double[3]):
+ *     out[0] = rho = max_{c >= k} ||Y(k:l-1, c)|| / |R(0, 0)|, the largest
+ *              remaining column norm of the pivoted QR relative to the first
+ *              pivot (the pivoted QR's estimate of sigma_{k+1} / sigma_1 of
+ *              the sketch; 0 when k = n or k = l);
+ *     out[1] = the floor of the plan's mode: rho above which that mode was
+ *              measured to return the FP64 path's J and an ID error within
+ *              twice the FP64 path's (0 for the FP64 modes; 2e-6 for
+ *              RID_MIXED_BF16);
+ *     out[2] = 1.0 if rho >= out[1] (the result is accepted), else 0.0: the
+ *              spectrum decays below what the mode resolves, and the ID should
+ *              be recomputed in an FP64 mode.
+ *   Synchronizes the stream.  RID_EINVAL for a null plan, Y or out, or
+ *   ldy < l. */
+RID_API rid_status rid_plan_accuracy(rid_plan_t plan, const void* Y, int64_t ldy, double out[3]);
 
 /* Allocation-free pivoted QR (the paper has no counterpart: this is a service
  * for callers that cannot call cudaMalloc, e.g. code running under another

@@ -258,6 +258,16 @@ class Plan:
         step (no CTA waits on another), < 0 the plan's default."""
         check(self._lib.rid_plan_set_select_grid(self._h, int(ctas)), "rid_plan_set_select_grid")
 
+    def accuracy(self, Y):
+        """After select(Y): (rho, floor, accepted) with rho the pivoted QR's
+        estimate of sigma_{k+1} / sigma_1 of the sketch and floor the smallest
+        rho at which this plan's mode was measured to match the FP64 path
+        (0 for FP64 modes); accepted is rho >= floor (synchronizes)."""
+        _check_matrix(Y, "Y", self.l, self.n, torch.complex128)
+        out = (ctypes.c_double * 3)()
+        check(self._lib.rid_plan_accuracy(self._h, ctypes.c_void_p(Y.data_ptr()), _ld(Y), out), "rid_plan_accuracy")
+        return float(out[0]), float(out[1]), bool(out[2] != 0.0)
+
     def stats(self):
         """Launch counts per call, K-splits and device bytes of the plan."""
         out = (ctypes.c_int64 * 8)()

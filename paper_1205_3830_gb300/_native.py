@@ -39,6 +39,7 @@ SIGNATURES = {
     "rid_plan_stats": (ctypes.c_int, [_c_plan, ctypes.POINTER(_i64)]),
     "rid_plan_set_select_grid": (ctypes.c_int, [_c_plan, _i32]),
     "rid_plan_timing": (ctypes.c_int, [_c_plan, _i32, ctypes.POINTER(ctypes.c_double)]),
+    "rid_plan_accuracy": (ctypes.c_int, [_c_plan, _p, _i64, ctypes.POINTER(ctypes.c_double)]),
     "rid_batch_workspace": (ctypes.c_int, [_i32, ctypes.POINTER(ctypes.c_size_t)]),
     "rid_batch_run": (ctypes.c_int, [ctypes.c_void_p, _i32, _i32, _u64, _i32, _p, _p, _p, ctypes.c_size_t, _p]),
     "rid_batch_prepare": (ctypes.c_int, [ctypes.c_void_p, _i32, _i32, _p, ctypes.c_size_t, _p]),

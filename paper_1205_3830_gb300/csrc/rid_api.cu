@@ -128,7 +128,7 @@ rid_status from_cuda(cudaError_t e) {
 // Workspace layout of a plan: one allocation, carved into 256-byte aligned pieces.
 struct Layout {
   size_t omega, status, sk_partial, qr_val, qr_idx, qr_counter, tau, sel_cand, sel_val, sel_idx, sel_bar,
-      probes, wtilde, wj_part, ew_part, norm_part, err_out, total;
+      res_cand, res_val, res_pos, res_col, res_flag, probes, wtilde, wj_part, ew_part, norm_part, err_out, total;
 };
 
 Layout plan_layout(const rid_plan_s* p) {
@@ -146,6 +146,11 @@ Layout plan_layout(const rid_plan_s* p) {
   L.sel_val = take((size_t)2 * p->sel_grid_max * sizeof(double));
   L.sel_idx = take((size_t)2 * p->sel_grid_max * sizeof(int));
   L.sel_bar = take(2 * sizeof(unsigned));
+  L.res_cand = take((size_t)2 * p->res_grid * p->l * sizeof(double2));
+  L.res_val = take((size_t)2 * p->res_grid * sizeof(double));
+  L.res_pos = take((size_t)2 * p->res_grid * sizeof(int));
+  L.res_col = take((size_t)2 * p->res_grid * sizeof(int));
+  L.res_flag = take((size_t)p->res_grid * sizeof(unsigned));
   L.probes = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
   L.wtilde = take((size_t)p->n * RID_MAX_PROBES * sizeof(double2));
   L.wj_part = take((size_t)p->err_wj_grid * p->k * RID_MAX_PROBES * sizeof(double2));
@@ -175,6 +180,8 @@ void choose_launch_shapes(rid_plan_s* p) {
   p->qr_grid = (int)(g < 1 ? 1 : g);
   p->sel_grid = rid_select_coop_grid(p->device, p->num_sms, p->n, p->l);
   p->sel_grid_max = p->sel_grid;
+  p->res_grid = p->sel_grid > 0 ? rid_select_resident_grid(p->device, p->num_sms, p->n, p->l, &p->res_cpc, &p->res_smem)
+                                : 0;
   // error
   const int64_t ncols = p->n - p->k;
   int64_t wg = (ncols + 63) / 64;
@@ -279,6 +286,11 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   p->sel_val = (double*)(base + L.sel_val);
   p->sel_idx = (int*)(base + L.sel_idx);
   p->sel_bar = (unsigned*)(base + L.sel_bar);
+  p->res_cand = (double2*)(base + L.res_cand);
+  p->res_val = (double*)(base + L.res_val);
+  p->res_pos = (int*)(base + L.res_pos);
+  p->res_col = (int*)(base + L.res_col);
+  p->res_flag = (unsigned*)(base + L.res_flag);
   p->probes = (double2*)(base + L.probes);
   p->wtilde = (double2*)(base + L.wtilde);
   p->wj_part = (double2*)(base + L.wj_part);
@@ -313,7 +325,7 @@ rid_status rid_plan_destroy(rid_plan_t p) {
   DeviceGuard g(p->device);
   cudaStreamSynchronize(p->stream);
   if (p->timing)
-    for (int i = 0; i < 4; ++i) cudaEventDestroy(p->ev[i]);
+    for (int i = 0; i < RID_TIMING_EVENTS; ++i) cudaEventDestroy(p->ev[i]);
   rid_tc_plan_free(p);
   rid_tc_probe_free(p);
   rid_dev_free(p->probe_base, p->stream);
@@ -572,20 +584,57 @@ rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   return RID_OK;
 }
 
+// The floor of the mixed-precision sketch (BF16x3 splits, FP32 sums over at
+// most 2048 reals), on rho = the pivoted QR's estimate of sigma_{k+1}/sigma_1.
+// Measured on complex64 matrices with a prescribed gap: the mixed ID's error
+// equals the FP64 path's down to a gap of 1e-5 and is 1.17x it at 1e-6
+// (rho = 1.07e-6); below that it stays near 3e-6 sigma_1 (5.6x the FP64
+// path's error at a gap of 1e-7, where rho reads 7.3e-7).  The floor is set a
+// factor 2 above that crossing.
+constexpr double RID_MIXED_BF16_FLOOR = 2e-6;
+
+rid_status rid_plan_accuracy(rid_plan_t p, const void* Y, int64_t ldy, double out[3]) {
+  if (!p || !Y || !out || ldy < p->l) return RID_EINVAL;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  double h[2] = {0.0, 0.0};
+  cudaError_t e = rid_launch_tail_ratio(p, (const double2*)Y, ldy, p->err_out);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, p->err_out, sizeof h, cudaMemcpyDeviceToHost, p->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+  if (e != cudaSuccess) return from_cuda(e);
+  const double rho = h[0] > 0.0 ? h[1] / h[0] : 0.0;
+  const double floor_ = p->mode == RID_MIXED_BF16 ? RID_MIXED_BF16_FLOOR : 0.0;
+  out[0] = rho;
+  out[1] = floor_;
+  out[2] = rho >= floor_ ? 1.0 : 0.0;
+  return RID_OK;
+}
+
 rid_status rid_plan_timing(rid_plan_t p, int32_t enable, double out[3]) {
   if (!p) return RID_EINVAL;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
   if (out) {
     if (!p->timing) return RID_EINVAL;
-    float ms[3] = {0.f, 0.f, 0.f};
-    cudaError_t e = cudaEventSynchronize(p->ev[3]);
-    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaEventElapsedTime(&ms[i], p->ev[i], p->ev[i + 1]);
+    // first passes and products summed over the panels of the last sketch
+    const int np = p->ev_panels > 0 ? p->ev_panels : 1;
+    double sum[3] = {0.0, 0.0, 0.0};
+    cudaError_t e = cudaEventSynchronize(p->ev[1 + 2 * np]);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+      float a = 0.f, b = 0.f;
+      e = cudaEventElapsedTime(&a, p->ev[2 * i], p->ev[1 + 2 * i]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&b, p->ev[1 + 2 * i], p->ev[2 + 2 * i]);
+      sum[0] += a;
+      sum[1] += b;
+    }
+    float c = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&c, p->ev[2 * np], p->ev[1 + 2 * np]);
     if (e != cudaSuccess) return from_cuda(e);
-    for (int i = 0; i < 3; ++i) out[i] = ms[i];
+    sum[2] = c;
+    for (int i = 0; i < 3; ++i) out[i] = sum[i];
   }
   if (enable && !p->timing) {
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < RID_TIMING_EVENTS; ++i)
       if (cudaEventCreate(&p->ev[i]) != cudaSuccess) return RID_ECUDA;
     p->timing = 1;
   }

@@ -9,6 +9,10 @@
 // ---------------------------------------------------------------------------
 // Plan: sizes, the test matrix Omega and all device workspace of one ID shape.
 // ---------------------------------------------------------------------------
+// Column panels of the emulated sketch a plan times at most (rid_plan_timing).
+#define RID_MAX_PANELS 8
+#define RID_TIMING_EVENTS (2 + 2 * RID_MAX_PANELS)
+
 struct rid_plan_s {
   int64_t m, n;
   int32_t k, l;
@@ -44,6 +48,15 @@ struct rid_plan_s {
   double* sel_val;         // 2 x sel_grid_max
   int* sel_idx;            // 2 x sel_grid_max
   unsigned* sel_bar;       // grid barrier: arrivals, generation
+  // select with Y resident in shared memory (res_grid CTAs of res_cpc columns; 0: not possible)
+  int res_grid;
+  int res_cpc;
+  size_t res_smem;         // dynamic shared memory of one CTA
+  double2* res_cand;       // 2 x res_grid x l posted columns
+  double* res_val;         // 2 x res_grid
+  int* res_pos;            // 2 x res_grid
+  int* res_col;            // 2 x res_grid
+  unsigned* res_flag;      // res_grid
 
   // error: probes, modified probes, partial sums, result
   int err_wj_grid;         // CTAs over the columns of T
@@ -69,9 +82,13 @@ struct rid_plan_s {
   void* probe_base;        // allocation of Omega + G, X, norms, partials (null: none)
   size_t probe_bytes;
 
-  // optional per-kernel timing of rid_sketch (CUDA events on the plan's stream)
+  // optional per-kernel timing of rid_sketch (CUDA events on the plan's stream):
+  // ev[0] before the sketch; per panel i (ev_panels of them) ev[1 + 2i] after
+  // its first pass (slicing) and ev[2 + 2i] after its product; ev[1 + 2 ev_panels]
+  // after the reduction
   int timing;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[RID_TIMING_EVENTS];
+  mutable int ev_panels;
 
   // emulated / mixed sketch state (owned by the tensor-core path)
   void* tc_state;
@@ -117,6 +134,10 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
 cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm);
 // CTAs of the cooperative select for n columns on this device (0: not available).
 int rid_select_coop_grid(int device, int num_sms, int64_t n, int l);
+// Shape of the select with Y resident in shared memory: CTAs (0 when the
+// columns do not fit, l > 256 or no cooperative launch), columns per CTA and
+// the dynamic shared memory of a CTA.
+int rid_select_resident_grid(int device, int num_sms, int64_t n, int l, int* cpc, size_t* smem);
 
 cudaError_t rid_launch_solve(const rid_plan_s* p, const double2* Y, int64_t ldy, double2* T,
                              int64_t ldt);
@@ -128,6 +149,9 @@ cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
 
 // ||g_q||^2 of the row probes (rows l..ls-1 of Omega), once per rid_plan_set_probes.
 cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p);
+
+// out[0] = |R(0,0)|, out[1] = max_{c >= k} ||Y(k:l-1, c)|| of a selected Y (device doubles).
+cudaError_t rid_launch_tail_ratio(const rid_plan_s* p, const double2* Y, int64_t ldy, double* out);
 // est / upper from X of the last sketch, perm and T, into p->err_out.
 cudaError_t rid_launch_error_sketched(const rid_plan_s* p, const int32_t* perm, const double2* T, int64_t ldt);
 

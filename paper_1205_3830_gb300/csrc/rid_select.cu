@@ -140,7 +140,15 @@ __device__ __forceinline__ void column_update(double2 (&x)[R], const double2* __
   }
 }
 
-template <int R>
+// A column entry: an L2 load (global columns that other CTAs write) or a
+// plain load (columns resident in this CTA's shared memory).
+template <bool GLB>
+__device__ __forceinline__ double2 ld_entry(const double2* p) {
+  if (GLB) return __ldcg(p);
+  return *p;
+}
+
+template <int R, bool GLB = true>
 __device__ __forceinline__ double reflect_column(const double2* __restrict__ in, double2* __restrict__ out,
                                                  const double2* __restrict__ v, double2 ctau, int rows, int lane,
                                                  bool norm) {
@@ -149,7 +157,7 @@ __device__ __forceinline__ double reflect_column(const double2* __restrict__ in,
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int i = lane + 32 * u;
-    x[u] = (i < rows) ? __ldcg(in + i) : make_double2(0.0, 0.0);
+    x[u] = (i < rows) ? ld_entry<GLB>(in + i) : make_double2(0.0, 0.0);
     w = cfma_conj(v[i], x[u], w);
   }
   warp_sum2(w.x, w.y, lane);
@@ -164,7 +172,7 @@ __device__ __forceinline__ double reflect_column(const double2* __restrict__ in,
 
 // Two columns at once: independent chains for the FP64 pipe and shared
 // reduce-scatter sums.
-template <int R>
+template <int R, bool GLB = true>
 __device__ __forceinline__ void reflect_pair(const double2* __restrict__ in0, double2* __restrict__ out0,
                                              const double2* __restrict__ in1, double2* __restrict__ out1,
                                              const double2* __restrict__ v, double2 ctau, int rows, int lane,
@@ -174,8 +182,8 @@ __device__ __forceinline__ void reflect_pair(const double2* __restrict__ in0, do
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int i = lane + 32 * u;
-    x[u] = (i < rows) ? __ldcg(in0 + i) : make_double2(0.0, 0.0);
-    y[u] = (i < rows) ? __ldcg(in1 + i) : make_double2(0.0, 0.0);
+    x[u] = (i < rows) ? ld_entry<GLB>(in0 + i) : make_double2(0.0, 0.0);
+    y[u] = (i < rows) ? ld_entry<GLB>(in1 + i) : make_double2(0.0, 0.0);
     const double2 vi = v[i];
     w0 = cfma_conj(vi, x[u], w0);
     w1 = cfma_conj(vi, y[u], w1);
@@ -191,12 +199,12 @@ __device__ __forceinline__ void reflect_pair(const double2* __restrict__ in0, do
 
 // RMAX: the largest chunk count a kernel instantiation handles (8: l <= 256,
 // two CTAs of 128 registers per SM; 16: l <= 512, one CTA per SM).
-template <int RMAX>
+template <int RMAX, bool GLB = true>
 __device__ __forceinline__ double reflect_any(const double2* in, double2* out, const double2* v, double2 ctau,
                                               int rows, int lane, bool norm) {
   switch ((rows + 31) >> 5) {
 #define RID_REFLECT_CASE(R) \
-    case R: if (R <= RMAX) return reflect_column<(R <= RMAX ? R : 1)>(in, out, v, ctau, rows, lane, norm); break;
+    case R: if (R <= RMAX) return reflect_column<(R <= RMAX ? R : 1), GLB>(in, out, v, ctau, rows, lane, norm); break;
     RID_REFLECT_CASE(1) RID_REFLECT_CASE(2) RID_REFLECT_CASE(3) RID_REFLECT_CASE(4)
     RID_REFLECT_CASE(5) RID_REFLECT_CASE(6) RID_REFLECT_CASE(7) RID_REFLECT_CASE(8)
     RID_REFLECT_CASE(9) RID_REFLECT_CASE(10) RID_REFLECT_CASE(11) RID_REFLECT_CASE(12)
@@ -213,14 +221,14 @@ __device__ __forceinline__ double reflect_any(const double2* in, double2* out, c
 #ifndef RID_SEL_PAIR_MAX
 #define RID_SEL_PAIR_MAX 6
 #endif
-template <int RMAX>
+template <int RMAX, bool GLB = true>
 __device__ __forceinline__ bool reflect_any_pair(const double2* in0, double2* out0, const double2* in1, double2* out1,
                                                  const double2* v, double2 ctau, int rows, int lane, bool norm,
                                                  double& nu0, double& nu1) {
   if (RMAX > 8) return false;
   switch ((rows + 31) >> 5) {
 #define RID_PAIR_CASE(R) \
-    case R: reflect_pair<(R <= 8 ? R : 1)>(in0, out0, in1, out1, v, ctau, rows, lane, norm, nu0, nu1); return true;
+    case R: reflect_pair<(R <= 8 ? R : 1), GLB>(in0, out0, in1, out1, v, ctau, rows, lane, norm, nu0, nu1); return true;
     RID_PAIR_CASE(1) RID_PAIR_CASE(2) RID_PAIR_CASE(3) RID_PAIR_CASE(4) RID_PAIR_CASE(5) RID_PAIR_CASE(6)
 #if RID_SEL_PAIR_MAX >= 7
     RID_PAIR_CASE(7)
@@ -602,6 +610,346 @@ __global__ void __launch_bounds__(QR_THREADS, rid_min_blocks(RMAX)) select_coop_
     for (int i = threadIdx.x; i < l; i += QR_THREADS) a.Y[(int64_t)(a.k - 1) * a.ldy + i] = rc[i];
 }
 
+
+// ---------------------------------------------------------------------------
+// All k steps with Y resident in shared memory (the plan path when the
+// columns fit and l <= 256).
+//
+// One CTA of 512 threads per SM, a cooperative launch.  CTA b owns the
+// columns b cpc .. b cpc + cpc - 1 of Y and keeps them in shared memory from
+// the first load to the final store: no column crosses L2 between steps.
+// Columns never move; the pivoting is bookkept instead.  Every CTA tracks the
+// position of each of its columns (ties of the pivot norms still go to the
+// lowest position), and all CTAs record the pivot positions p_0 .. p_j and
+// the column X_j that sat at position j before swap j (the latest earlier
+// step whose pivot position was j left it there, or none did and it is
+// column j), so each can apply swap j to its own columns.  At the end every
+// column is stored at its final position and perm is written from the
+// positions.  The arithmetic of a step is that of the other select paths
+// (the same column update, the same order in the pivot's norm, the same
+// reflector scalars), so the results agree with them bit for bit.
+//
+// Exchange: after its update a CTA posts its best (norm, position, column)
+// and a copy of that column into the buffer of the next step's parity, then
+// raises its flag to the number of steps posted (release).  A step starts
+// once every flag has reached it (acquire); a flag wait has a clock budget,
+// after which the status word becomes RID_ETIMEOUT and the CTA returns.
+// ---------------------------------------------------------------------------
+constexpr int RES_THREADS = 512;
+constexpr int RES_WARPS = RES_THREADS / 32;
+constexpr int RES_MAX_L = 256;
+constexpr size_t RES_SMEM_LIMIT = 232448;   // shared memory of one CTA (static + dynamic)
+
+struct ResArgs {
+  double2* Y;
+  int64_t ldy;
+  int l, k;
+  int64_t n;
+  int32_t* perm;
+  double2* tau;
+  int* status;
+  double2* cand;           // [2][G][l] posted columns
+  double* val;             // [2][G] posted norms
+  int* pos;                // [2][G] posted positions
+  int* col;                // [2][G] posted column indices
+  unsigned* flag;          // [G] steps posted by each CTA
+  int cpc;                 // columns per CTA
+};
+
+struct Best {
+  double v;
+  int pos;                 // position (the tie key)
+  int c;                   // local column
+};
+
+__device__ __forceinline__ Best better_res(Best a, Best b) {
+  return (b.v > a.v || (b.v == a.v && b.pos < a.pos)) ? b : a;
+}
+
+// Block-wide best of 16 warps; result valid in every thread.
+__device__ Best block_best(Best a) {
+  __shared__ Best red[RES_WARPS];
+  __shared__ Best result;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    Best o;
+    o.v = __shfl_xor_sync(0xffffffffu, a.v, off);
+    o.pos = __shfl_xor_sync(0xffffffffu, a.pos, off);
+    o.c = __shfl_xor_sync(0xffffffffu, a.c, off);
+    a = better_res(a, o);
+  }
+  if (lane == 0) red[warp] = a;
+  __syncthreads();
+  if (warp == 0) {
+    Best b = lane < RES_WARPS ? red[lane] : Best{-1.0, INT_MAX, -1};
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      Best o;
+      o.v = __shfl_xor_sync(0xffffffffu, b.v, off);
+      o.pos = __shfl_xor_sync(0xffffffffu, b.pos, off);
+      o.c = __shfl_xor_sync(0xffffffffu, b.c, off);
+      b = better_res(b, o);
+    }
+    if (lane == 0) result = b;
+  }
+  __syncthreads();
+  return result;
+}
+
+// Post this CTA's best column for step `step` (buffer step & 1), then raise
+// the flag to step + 1.
+__device__ void res_post(const ResArgs& a, const double2* cols, int l, Best best, int c_lo, int step) {
+  const Best r = block_best(best);
+  const int64_t slot = (int64_t)(step & 1) * gridDim.x + blockIdx.x;
+  if (r.c >= 0) {
+    double2* dst = a.cand + slot * l;
+    for (int i = threadIdx.x; i < l; i += RES_THREADS) dst[i] = cols[(int64_t)r.c * l + i];
+  }
+  if (threadIdx.x == 0) {
+    a.val[slot] = r.v;
+    a.pos[slot] = r.pos;
+    a.col[slot] = r.c >= 0 ? c_lo + r.c : -1;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) atomicExch(a.flag + blockIdx.x, (unsigned)(step + 1));
+}
+
+// Wait until every CTA has posted step `step`; false after the clock budget.
+// A lane polls its flags (lane, lane + 32, ...) together, one round trip per poll.
+constexpr int RES_FLAGS_PER_LANE = 8;                 // grids of up to 256 CTAs
+__device__ bool res_wait(const ResArgs& a, int step) {
+  __shared__ int ok;
+  if (threadIdx.x < 32) {
+    const long long t0 = clock64();
+    bool good = true;
+    unsigned pending = 0;
+#pragma unroll
+    for (int u = 0; u < RES_FLAGS_PER_LANE; ++u)
+      if (threadIdx.x + 32 * u < (int)gridDim.x) pending |= 1u << u;
+    while (__any_sync(0xffffffffu, pending != 0)) {
+      unsigned f[RES_FLAGS_PER_LANE];
+#pragma unroll
+      for (int u = 0; u < RES_FLAGS_PER_LANE; ++u)
+        if (pending & (1u << u))
+          asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f[u]) : "l"(a.flag + threadIdx.x + 32 * u) : "memory");
+#pragma unroll
+      for (int u = 0; u < RES_FLAGS_PER_LANE; ++u)
+        if ((pending & (1u << u)) && f[u] >= (unsigned)(step + 1)) pending &= ~(1u << u);
+      if (pending && clock64() - t0 > SEL_WAIT_BUDGET) {
+        atomicExch(a.status, (int)RID_ETIMEOUT);
+        good = false;
+        pending = 0;
+      }
+    }
+    good = __all_sync(0xffffffffu, good);
+    if (threadIdx.x == 0) ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <int RMAX>
+__global__ void __launch_bounds__(RES_THREADS, 1) select_resident_kernel(ResArgs a) {
+  extern __shared__ double2 res_cols[];      // cpc columns of l entries, then positions and done marks
+  __shared__ double2 v[RES_MAX_L];           // reflector j: v[0] = 1, v[i] = row j + i
+  __shared__ double2 rc[RES_MAX_L];          // the pivot column: R above, reflector below
+  __shared__ int hp[RES_MAX_L], hx[RES_MAX_L];   // pivot positions and the columns they displaced
+  __shared__ double red[QR_WARPS];
+  __shared__ double2 s_tau, s_scale;
+  __shared__ int s_b, s_x;
+  __shared__ ArgMax s_win;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int G = gridDim.x;
+  const int l = a.l;
+  const int64_t c_lo = (int64_t)blockIdx.x * a.cpc;
+  const int64_t c_hi = a.n < c_lo + a.cpc ? a.n : c_lo + a.cpc;
+  const int nc = c_hi > c_lo ? (int)(c_hi - c_lo) : 0;
+  double2* cols = res_cols;
+  int* cpos = (int*)(res_cols + (int64_t)a.cpc * l);
+  int* done = cpos + a.cpc;
+
+  // load the CTA's columns; full norms; the first posting
+  for (int64_t e = threadIdx.x; e < (int64_t)nc * l; e += RES_THREADS) {
+    const int64_t c = e / l, i = e - c * l;
+    cols[e] = __ldcg(a.Y + (c_lo + c) * a.ldy + i);
+  }
+  for (int c = threadIdx.x; c < nc; c += RES_THREADS) {
+    cpos[c] = (int)(c_lo + c);
+    done[c] = 0;
+  }
+  __syncthreads();
+  {
+    Best best{-1.0, INT_MAX, -1};
+    for (int c = wid; c < nc; c += RES_WARPS) {
+      double sq = 0.0;
+      for (int i = lane; i < l; i += 32) sq += cabs2(cols[(int64_t)c * l + i]);
+      sq = warp_sum(sq);
+      best = better_res(best, Best{sq, cpos[c], c});
+    }
+    res_post(a, cols, l, best, (int)c_lo, 0);
+  }
+
+  int j = 0;
+  bool rank_ok = true;
+  for (; j < a.k; ++j) {
+    if (!res_wait(a, j)) return;
+    const int buf = j & 1;
+    // pivot j: the best posted pair (ties to the lowest position), by warp 0;
+    // warp 1 finds the column at position j before the swap
+    if (wid == 0) {
+      // the posted pairs of all CTAs, loaded before they are reduced
+      ArgMax w{-1.0, INT_MAX};
+      int wb = -1;
+      double pv[RES_FLAGS_PER_LANE];
+      int pp[RES_FLAGS_PER_LANE];
+#pragma unroll
+      for (int u = 0; u < RES_FLAGS_PER_LANE; ++u) {
+        const int b = lane + 32 * u;
+        pv[u] = b < G ? __ldcg(a.val + (int64_t)buf * G + b) : -1.0;
+        pp[u] = b < G ? __ldcg(a.pos + (int64_t)buf * G + b) : INT_MAX;
+      }
+#pragma unroll
+      for (int u = 0; u < RES_FLAGS_PER_LANE; ++u) {
+        const ArgMax nb = better(w, ArgMax{pv[u], pp[u]});
+        if (nb.i != w.i) {
+          w = nb;
+          wb = lane + 32 * u;
+        }
+      }
+      const ArgMax rw = warp_argmax(w);
+      if (wb >= 0 && w.i == rw.i) s_b = wb;
+      if (lane == 0) s_win = rw;
+    } else if (wid == 1) {
+      int last = -1;
+      for (int jj = lane; jj < j; jj += 32)
+        if (hp[jj] == j) last = max(last, jj);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) last = max(last, __shfl_xor_sync(0xffffffffu, last, off));
+      if (lane == 0) s_x = last >= 0 ? hx[last] : j;
+    }
+    __syncthreads();
+    const ArgMax r = s_win;
+    if (!(r.v > 0.0)) {                                  // rank(Y) = j < k (Sec. 2)
+      if (blockIdx.x == 0 && threadIdx.x == 0) *a.status = RID_ERANK;
+      rank_ok = false;
+      break;
+    }
+    const int p = r.i;
+    const int wbuf = s_b;
+    const int q = __ldcg(a.col + (int64_t)buf * G + wbuf);
+    const int xj = s_x;
+    // reflector j from the posted copy of the pivot column (zlarfg convention);
+    // the norm below the diagonal in the order of the 256-thread select CTAs
+    const double2* pc = a.cand + ((int64_t)buf * G + wbuf) * l;
+    for (int i = threadIdx.x; i < l; i += RES_THREADS) rc[i] = __ldcg(pc + i);
+    double part = 0.0;
+    if (threadIdx.x < QR_THREADS)
+      for (int i = j + 1 + threadIdx.x; i < l; i += QR_THREADS) part += cabs2(__ldcg(pc + i));
+    part = warp_sum(part);
+    if (lane == 0 && wid < QR_WARPS) red[wid] = part;
+    __syncthreads();
+    if (wid == 0) {
+      double y = lane < QR_WARPS ? red[lane] : 0.0;
+      const double xnorm2 = warp_sum(y);
+      double2 tau, scale;
+      double beta;
+      const bool h = zlarfg_scalars_warp(rc[j], xnorm2, lane, tau, scale, beta);
+      if (lane == 0) {
+        if (h) rc[j] = make_double2(beta, 0.0);
+        if (blockIdx.x == 0) a.tau[j] = tau;
+        s_tau = tau;
+        s_scale = scale;
+        hp[j] = p;
+        hx[j] = xj;
+      }
+    }
+    __syncthreads();
+    const double2 scale = s_scale;
+    const bool scaled = scale.x != 0.0 || scale.y != 0.0;
+    const int rows = l - j;
+    const int padded = (rows + 31) & ~31;
+    for (int i = threadIdx.x; i < padded; i += RES_THREADS) {
+      double2 x = make_double2(0.0, 0.0);
+      if (i > 0 && i < rows) {
+        x = scaled ? cmul(rc[j + i], scale) : rc[j + i];
+        rc[j + i] = x;
+      }
+      v[i] = (i == 0) ? make_double2(1.0, 0.0) : x;
+    }
+    // swap j: the pivot settles at position j, the column from j moves to p
+    if (threadIdx.x == 0) {
+      if (q >= c_lo && q < c_lo + nc) {
+        done[q - c_lo] = 1;
+        cpos[q - c_lo] = j;
+      }
+      if (xj != q && xj >= c_lo && xj < c_lo + nc) cpos[xj - c_lo] = p;
+    }
+    __syncthreads();
+    if (q >= c_lo && q < c_lo + nc)                      // the pivot column: R above, reflector below
+      for (int i = j + threadIdx.x; i < l; i += RES_THREADS) cols[(q - c_lo) * (int64_t)l + i] = rc[i];
+
+    // H_j^H on this CTA's remaining columns (rows j..l-1), new norms below row j
+    const double2 ctau = make_double2(s_tau.x, -s_tau.y);
+    const bool more = j + 1 < a.k;
+    Best best{-1.0, INT_MAX, -1};
+    for (int c = wid; c < nc; c += 2 * RES_WARPS) {
+      const int c2 = c + RES_WARPS;
+      const bool l0 = !done[c], l1 = c2 < nc && !done[c2];
+      double2* x0 = cols + (int64_t)c * l + j;
+      double2* x1 = cols + (int64_t)c2 * l + j;
+      double nu0 = 0.0, nu1 = 0.0;
+      if (l0 && l1 && reflect_any_pair<RMAX, false>(x0, x0, x1, x1, v, ctau, rows, lane, more, nu0, nu1)) {
+        if (more) {
+          best = better_res(best, Best{nu0, cpos[c], c});
+          best = better_res(best, Best{nu1, cpos[c2], c2});
+        }
+        continue;
+      }
+      if (l0) {
+        nu0 = reflect_any<RMAX, false>(x0, x0, v, ctau, rows, lane, more);
+        if (more) best = better_res(best, Best{nu0, cpos[c], c});
+      }
+      if (l1) {
+        nu1 = reflect_any<RMAX, false>(x1, x1, v, ctau, rows, lane, more);
+        if (more) best = better_res(best, Best{nu1, cpos[c2], c2});
+      }
+    }
+    if (more) res_post(a, cols, l, best, (int)c_lo, j + 1);
+    __syncthreads();
+  }
+  (void)rank_ok;
+  // every column to its final position (after a rank failure: the state reached)
+  for (int64_t e = threadIdx.x; e < (int64_t)nc * l; e += RES_THREADS) {
+    const int64_t c = e / l, i = e - c * l;
+    a.Y[(int64_t)cpos[c] * a.ldy + i] = cols[e];
+  }
+  for (int c = threadIdx.x; c < nc; c += RES_THREADS) a.perm[cpos[c]] = (int32_t)(c_lo + c);
+}
+
+
+// |R(0,0)| and the largest column norm of rows k..l-1 over columns k..n-1 of
+// a selected Y: one CTA, a warp per column, sums in a fixed order.
+__global__ void __launch_bounds__(QR_THREADS) tail_ratio_kernel(const double2* __restrict__ Y, int64_t ldy, int l,
+                                                                int k, int64_t n, double* __restrict__ out) {
+  __shared__ double red[QR_WARPS];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double best = 0.0;
+  for (int64_t c = k + wid; c < n; c += QR_WARPS) {
+    double sq = 0.0;
+    for (int i = k + lane; i < l; i += 32) sq += cabs2(__ldg(Y + c * ldy + i));
+    best = fmax(best, warp_sum(sq));
+  }
+  if (lane == 0) red[wid] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int w = 0; w < QR_WARPS; ++w) m = fmax(m, red[w]);
+    out[0] = sqrt(cabs2(Y[0]));
+    out[1] = sqrt(m);
+  }
+}
 }  // namespace
 
 // CTAs of the cooperative select for n columns (0: use one launch per step).
@@ -624,10 +972,66 @@ int rid_select_coop_grid(int device, int num_sms, int64_t n, int l) {
   return (int)(g < 1 ? 1 : g);
 }
 
+int rid_select_resident_grid(int device, int num_sms, int64_t n, int l, int* cpc_out, size_t* smem_out) {
+  *cpc_out = 0;
+  *smem_out = 0;
+  if (l < 1 || l > RES_MAX_L || n < 1) return 0;
+  int coop = 0;
+  if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device) != cudaSuccess || !coop) {
+    cudaGetLastError();
+    return 0;
+  }
+  // the attribute is process-wide: always the largest bound, which every shape fits under
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, select_resident_kernel<8>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const size_t dyn_max = RES_SMEM_LIMIT - fa.sharedSizeBytes - 1024;
+  if (cudaFuncSetAttribute(select_resident_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int64_t g = num_sms < 32 * RES_FLAGS_PER_LANE ? num_sms : 32 * RES_FLAGS_PER_LANE;
+  const int64_t by_work = (n + 3) / 4;                 // at least four columns a CTA
+  if (g > by_work) g = by_work;
+  const int64_t cpc = (n + g - 1) / g;
+  const size_t smem = (size_t)cpc * l * sizeof(double2) + (size_t)cpc * 2 * sizeof(int);
+  if (smem > dyn_max) return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_resident_kernel<8>, RES_THREADS, smem) !=
+          cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    return 0;
+  }
+  g = (n + cpc - 1) / cpc;
+  if (g > (int64_t)per_sm * num_sms) return 0;
+  *cpc_out = (int)cpc;
+  *smem_out = smem;
+  return (int)g;
+}
+
+cudaError_t rid_launch_tail_ratio(const rid_plan_s* p, const double2* Y, int64_t ldy, double* out) {
+  tail_ratio_kernel<<<1, QR_THREADS, 0, p->stream>>>(Y, ldy, p->l, p->k, p->n, out);
+  return cudaGetLastError();
+}
+
 cudaError_t rid_launch_select(const rid_plan_s* p, double2* Y, int64_t ldy, int32_t* perm) {
   if (p->l > 32 * QR_PER_LANE) return cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
   if (e != cudaSuccess) return e;
+  if (p->sel_grid > 0 && p->sel_grid == p->sel_grid_max && p->res_grid > 0) {
+    // the default launch shape: Y resident in shared memory
+    ResArgs r{Y, ldy, p->l, p->k, p->n, perm, p->tau, p->status, p->res_cand, p->res_val, p->res_pos, p->res_col,
+              p->res_flag, p->res_cpc};
+    e = cudaMemsetAsync(p->res_flag, 0, (size_t)p->res_grid * sizeof(unsigned), p->stream);
+    if (e != cudaSuccess) return e;
+    void* args[] = {&r};
+    return cudaLaunchCooperativeKernel((const void*)select_resident_kernel<8>, dim3(p->res_grid), dim3(RES_THREADS),
+                                       args, p->res_smem, p->stream);
+  }
   if (p->sel_grid > 0) {
     CoopArgs c{Y, ldy, p->l, p->k, p->n, perm, p->tau, p->status, p->sel_cand, p->sel_val, p->sel_idx,
                p->sel_bar};

@@ -106,6 +106,7 @@ cudaError_t rid_launch_sketch_fp64(const rid_plan_s* p, const double2* A, int64_
   const dim3 grid((unsigned)((ls + BL - 1) / BL), (unsigned)((n + BN - 1) / BN),
                   (unsigned)p->split_k);
   if (p->timing) {
+    p->ev_panels = 1;
     cudaEventRecord(p->ev[0], p->stream);
     cudaEventRecord(p->ev[1], p->stream);
   }

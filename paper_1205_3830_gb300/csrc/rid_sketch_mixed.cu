@@ -7,10 +7,11 @@
 // three BF16 terms, hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid),
 // which carry about 24 bits of x.  The product keeps the six term pairs with
 // s + t <= 2 (the others are below 2^-24 of the leading term) and sums them,
-// over the CTA's whole K range, in one FP32 TMEM accumulator.  The same real
-// view as the FP64-emulated path is used (Omega' of 2l x 2m real rows, A' =
-// A's floats read as 2m x n), N-tiles of up to 256 rows of Omega', 64-byte
-// rows of K = 32 per stage.  K-split partials are summed in FP64.
+// over the CTA's K range of at most 2048 reals, in one FP32 TMEM accumulator.
+// The same real view as the FP64-emulated path is used (Omega' of 2l x 2m
+// real rows, A' = A's floats read as 2m x n), N-tiles of up to 256 rows of
+// Omega', 64-byte rows of K = 32 per stage.  K-split partials are summed in
+// FP64.
 #include <cudaTypedefs.h>
 
 #include "rid_internal.cuh"
@@ -25,6 +26,10 @@ constexpr int MX_PAIRS = 6;                // (s, t) with s + t <= 2
 constexpr int MX_KS = 32;                  // K per stage (64-byte rows)
 constexpr int MX_STAGES = 3;
 constexpr int MX_THREADS = 192;            // warp 0 TMA, 1 MMA + TMEM, 2-5 epilogue
+// K stages one FP32 accumulator sums at most (2048 reals): the rounding of the
+// FP32 sums grows with the square root of their length, so the K-split is
+// raised until every split is this short; the splits are summed in FP64.
+constexpr int MX_MAX_STAGES_PER_SPLIT = 64;
 constexpr long long MX_WAIT_BUDGET = 4000000000ll;
 constexpr int MX_SMEM_MAX = MX_STAGES * MX_S * (128 + 256) * MX_KS * 2 + 1024;   // 222208 bytes
 static_assert(MX_SMEM_MAX <= 232448 - 1024, "mixed stages exceed shared memory");
@@ -326,6 +331,8 @@ rid_status rid_mx_plan_setup(rid_plan_s* p, int dry_run) {
     int ks = (2 * p->num_sms + units - 1) / units;
     const int max_ks = st->nchunk / 16 > 0 ? st->nchunk / 16 : 1;   // at least 16 stages per split
     if (ks > max_ks) ks = max_ks;
+    const int min_ks = (st->nchunk + MX_MAX_STAGES_PER_SPLIT - 1) / MX_MAX_STAGES_PER_SPLIT;
+    if (ks < min_ks) ks = min_ks;
     if (ks < 1) ks = 1;
     st->stages_per_split = (st->nchunk + ks - 1) / ks;
     st->ksplit = (st->nchunk + st->stages_per_split - 1) / st->stages_per_split;
@@ -385,7 +392,10 @@ cudaError_t rid_mx_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda,
   if (!st) return cudaErrorNotSupported;
   if (ncols <= 0) return cudaSuccess;
   const float2* A = (const float2*)A_ + col0 * lda;
-  if (p->timing) cudaEventRecord(p->ev[0], p->stream);
+  if (p->timing) {
+    p->ev_panels = 1;
+    cudaEventRecord(p->ev[0], p->stream);
+  }
   cudaError_t e;
   {
     const int64_t total = ncols * (st->KP / 4);

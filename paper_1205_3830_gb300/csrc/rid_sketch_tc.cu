@@ -86,8 +86,8 @@ struct TcState {
   int cx;                 // single CTAs: N-tiles per cluster
   uint16_t* om_slices;    // tiles [N-tile][K stage][S][tile_w x TC_KS] bf16 (see omega_slice_kernel)
   int* om_exp;            // [l2]
-  uint16_t* a_slices;     // tiles [column block][K stage][S][128 x TC_KS] bf16 (see a_slice_kernel);
-                          // pairs: one zero block past the last, the partner of an odd last block
+  uint16_t* a_slices;     // tiles [column block of the panel][K stage][S][128 x TC_KS] bf16 (see a_slice_kernel)
+  int panel_blocks;       // column blocks of one panel: the digit tiles hold one panel at a time
   int* a_exp;             // [n][NC]
   int* a_exp_max;         // [n]
   float2* partial;        // [ksplit][n][l2p]: (hi, lo) of each running sum
@@ -364,6 +364,7 @@ struct TcArgs {
   uint32_t o_tile_smem;   // one Omega tile: tile_w rows (single) or tile_w / 2 rows (pairs) x 64 bytes
   int cx;                 // single CTAs: N-tiles per cluster (they share A tiles)
   int jb0;                // first column block of the launch (a column range of the sketch)
+  int tile_jb0;           // the column block whose digit tiles start a_tiles
   int64_t j_end;          // columns below this have results in the launch
   int64_t nst;            // K stages per column block / N-tile
   const uint16_t* a_tiles;
@@ -492,7 +493,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
       const int s0 = 0, s1 = TC_S;
       const int o_elems = (int)(a.o_tile_smem / 2);
       const int64_t st0 = (int64_t)c_begin * TC_SPC;            // first K stage of this split
-      const uint16_t* a_src = a.a_tiles + ((jb * a.nst + st0) * TC_S + s0) * TC_TILE_ELEMS;
+      const uint16_t* a_src = a.a_tiles + (((int64_t)(jb - a.tile_jb0) * a.nst + st0) * TC_S + s0) * TC_TILE_ELEMS;
       const uint16_t* o_src = PAIR ? a.om_tiles + ((nb * a.nst + st0) * 2 + member) * TC_S * o_elems
                                    : a.om_tiles + (nb * a.nst + st0) * TC_S * o_elems;
       const int64_t o_stride = (PAIR ? 2 : 1) * TC_S * (int64_t)o_elems;
@@ -761,6 +762,16 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   st->pair = st->nblocks >= 16 && st->l2 >= 32;
   if (st->pair && st->tile_w < 32) st->tile_w = 32;
   st->l2p = st->ntiles * st->tile_w;
+  // Column panels: the digit tiles of A take 7/4 of A's bytes, so a matrix of
+  // more than 32 column blocks is sliced and multiplied in at most 4 panels
+  // (even block counts, so CTA pairs never straddle two panels): the plan's
+  // digit tiles stay below half of A's bytes.
+  {
+    const int np = st->nblocks > 32 ? 4 : 1;
+    int pb = (st->nblocks + np - 1) / np;
+    if (st->pair) pb = (pb + 1) & ~1;
+    st->panel_blocks = pb;
+  }
   if (st->ntiles > 8) {
     free(st);
     return RID_EUNSUPPORTED;
@@ -782,7 +793,8 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   // them across the N-tiles of a column block by multicast bought about 1 %).
   // Pairs: a cluster is the pair.
   st->cx = st->pair ? 2 : 1;
-  const int units = st->pair ? st->ntiles * ((st->nblocks + 1) / 2) : st->nblocks;   // clusters per K-split
+  // clusters per K-split of one panel
+  const int units = st->pair ? st->ntiles * (st->panel_blocks / 2) : st->ntiles * st->panel_blocks;
   {
     // how many clusters of this shape are resident at once
     cudaLaunchConfig_t cfg = {};
@@ -810,7 +822,7 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
 
   const size_t om_bytes = (size_t)TC_S * st->l2p * st->KP * 2;           // N-tiles padded to tile_w rows
   const size_t block_bytes = (size_t)TC_S * 128 * st->KP * 2;            // one column block's tiles
-  const size_t a_bytes = block_bytes * (st->nblocks + (st->pair ? 1 : 0));
+  const size_t a_bytes = block_bytes * st->panel_blocks;
   const size_t aexp_bytes = (size_t)p->n * st->NC * 4;
   const size_t part_bytes = (size_t)st->ksplit * p->n * st->l2p * 8;
   auto al = [](size_t x) { return (x + 1023) & ~(size_t)1023; };
@@ -838,8 +850,6 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
 
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st->om_slices, 0, om_bytes, p->stream);   // padding rows
-  if (e == cudaSuccess && st->pair)                                                     // the spare block
-    e = cudaMemsetAsync((char*)st->a_slices + block_bytes * st->nblocks, 0, block_bytes, p->stream);
   if (e == cudaSuccess) {
     omega_exp_kernel<<<nrows, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m, st->om_exp);
     e = cudaGetLastError();
@@ -925,33 +935,42 @@ cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, in
   if (!st) return cudaErrorNotSupported;
   if (ncols <= 0) return cudaSuccess;
   timing = timing && p->timing;
-  if (timing) cudaEventRecord(p->ev[0], p->stream);
+  // the range's column blocks, a panel of at most panel_blocks at a time: its
+  // digits are cut into the plan's tiles, then multiplied
+  const int jb_begin = (int)(col0 / 128), jb_end = (int)((col0 + ncols + 127) / 128);
+  const int npanels = (jb_end - jb_begin + st->panel_blocks - 1) / st->panel_blocks;
+  if (timing) {
+    p->ev_panels = npanels <= RID_MAX_PANELS ? npanels : 0;
+    cudaEventRecord(p->ev[0], p->stream);
+  }
   // 0x80808080 is below every exponent: the running maximum starts there
   cudaError_t e = cudaMemsetAsync(st->a_exp_max + col0, 0x80, (size_t)ncols * 4, p->stream);
   if (e != cudaSuccess) return e;
-  {
-    const int64_t n_pad = (ncols + 127) / 128 * 128;
-    int64_t blocks = n_pad / 8 * (int64_t)st->NC;          // a block per 8 columns of one chunk
-    if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
-    uint16_t* tiles = st->a_slices + (col0 / 128) * st->nst * TC_S * TC_TILE_ELEMS;
-    if (st->a_c64)
-      a_slice_kernel<float2><<<(unsigned)blocks, 256, 0, p->stream>>>(
-          (const float2*)A_ + col0 * lda, lda, p->m, ncols, n_pad, st->NC, tiles, st->a_exp + col0 * st->NC,
-          st->a_exp_max + col0);
-    else
-      a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
-          (const double2*)A_ + col0 * lda, lda, p->m, ncols, n_pad, st->NC, tiles, st->a_exp + col0 * st->NC,
-          st->a_exp_max + col0);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (timing) cudaEventRecord(p->ev[1], p->stream);
-  const int jb0 = (int)(col0 / 128);
-  const int nblocks = (int)((ncols + 127) / 128);
-  TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
-              (uint32_t)(TC_S * TC_TILE_BYTES) + (uint32_t)st->so * st->o_tile_smem, st->so, st->nstages,
-              st->stage_smem, st->o_off, st->o_tile_smem, st->cx, jb0, col0 + ncols, st->nst, st->a_slices,
-              st->om_slices, st->a_exp, st->a_exp_max, st->partial, st->err};
-  {
+  for (int pi = 0; pi < npanels; ++pi) {
+    const int jb0 = jb_begin + pi * st->panel_blocks;
+    const int nblocks = jb_end - jb0 < st->panel_blocks ? jb_end - jb0 : st->panel_blocks;
+    const int64_t c0 = (int64_t)jb0 * 128;                      // the panel's first column
+    const int64_t pcols = (col0 + ncols < c0 + (int64_t)nblocks * 128 ? col0 + ncols : c0 + (int64_t)nblocks * 128) - c0;
+    {
+      // a CTA pair's partner of an odd last block gets zero digits
+      const int64_t n_pad = st->pair ? (pcols + 255) / 256 * 256 : (pcols + 127) / 128 * 128;
+      int64_t blocks = n_pad / 8 * (int64_t)st->NC;          // a block per 8 columns of one chunk
+      if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
+      if (st->a_c64)
+        a_slice_kernel<float2><<<(unsigned)blocks, 256, 0, p->stream>>>(
+            (const float2*)A_ + c0 * lda, lda, p->m, pcols, n_pad, st->NC, st->a_slices, st->a_exp + c0 * st->NC,
+            st->a_exp_max + c0);
+      else
+        a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
+            (const double2*)A_ + c0 * lda, lda, p->m, pcols, n_pad, st->NC, st->a_slices, st->a_exp + c0 * st->NC,
+            st->a_exp_max + c0);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (timing && pi < RID_MAX_PANELS && p->ev_panels) cudaEventRecord(p->ev[1 + 2 * pi], p->stream);
+    TcArgs args{(int)p->n, st->l2, st->l2p, st->NC, st->chunks_per_split, st->ntiles, st->tile_w,
+                (uint32_t)(TC_S * TC_TILE_BYTES) + (uint32_t)st->so * st->o_tile_smem, st->so, st->nstages,
+                st->stage_smem, st->o_off, st->o_tile_smem, st->cx, jb0, jb0, c0 + pcols, st->nst, st->a_slices,
+                st->om_slices, st->a_exp, st->a_exp_max, st->partial, st->err};
     cudaLaunchConfig_t cfg = {};
     cudaLaunchAttribute attr[1];
     cfg.gridDim = st->pair ? dim3((unsigned)(2 * st->ntiles), (unsigned)((nblocks + 1) / 2), (unsigned)st->ksplit)
@@ -968,8 +987,13 @@ cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, in
     e = st->pair ? cudaLaunchKernelEx(&cfg, sketch_tc_kernel<true>, args)
                  : cudaLaunchKernelEx(&cfg, sketch_tc_kernel<false>, args);
     if (e != cudaSuccess) return e;
+    if (timing && pi < RID_MAX_PANELS && p->ev_panels) cudaEventRecord(p->ev[2 + 2 * pi], p->stream);
   }
-  if (timing) cudaEventRecord(p->ev[2], p->stream);
+  if (timing && !p->ev_panels) {        // more panels than timed: the whole sketch counts as its first pass
+    p->ev_panels = 1;
+    cudaEventRecord(p->ev[1], p->stream);
+    cudaEventRecord(p->ev[2], p->stream);
+  }
   {
     const int64_t total = ncols * (int64_t)st->nrows;
     int64_t blocks = (total + 255) / 256;
@@ -979,7 +1003,7 @@ cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, in
                                                                ncols);
     e = cudaGetLastError();
   }
-  if (timing) cudaEventRecord(p->ev[3], p->stream);
+  if (timing) cudaEventRecord(p->ev[1 + 2 * p->ev_panels], p->stream);
   return e;
 }
 

@@ -123,3 +123,50 @@ def test_mixed_panels_equal_one_sketch(rid, shape):
         e1 = plan.error_sketched(perm, T)
     assert torch.equal(Y0, Y1)
     assert e0 == e1
+
+
+# ---- the accuracy floor of the mixed mode ---------------------------------------
+# A sweep of the spectral gap sigma_{k+1} / sigma_1 from 1e-2 to 1e-9 on a
+# complex64 A with a prescribed spectrum.  At every point the mixed ID is
+# compared with the FP64 oracle on the same (upcast) A: J, T and the exact
+# error ||A - A(:, J) P||_2 of both.  The plan's own accuracy check
+# (rid_plan_accuracy) must accept exactly where the mixed result is as good as
+# the FP64 path's: J equal and an ID error within twice the FP64 path's.
+FLOOR_RATIOS = [1e-2, 1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8, 1e-9]
+
+
+def gap_matrix_c64(m, n, k, ratio, seed):
+    r = min(m, n)
+    sigma = np.concatenate([np.ones(k), ratio * 0.95 ** np.arange(r - k)])
+    return np.asfortranarray(synth.prescribed_spectrum(m, n, sigma, seed).astype(np.complex64))
+
+
+@pytest.mark.parametrize("ratio", FLOOR_RATIOS, ids=lambda r: f"{r:.0e}")
+def test_mixed_accuracy_floor_sweep(rid, ratio):
+    m, n, k, l = 4096, 1024, 20, 30
+    A = gap_matrix_c64(m, n, k, ratio, seed=17)
+    A64 = A.astype(np.complex128)
+    want = oracle.rid(A64, k, l, seed=23)
+    err_fp64 = oracle.exact_error(A64, want["perm"], want["T"])
+    with rid.Plan(m, n, k, l, seed=23, dtype=torch.complex64, mode="bf16") as plan:
+        Y = plan.sketch(to_dev_colmajor(A, torch.complex64))
+        perm_d = plan.select(Y)
+        T_d = plan.solve(Y)
+        rho, floor, accepted = plan.accuracy(Y)
+        plan.sync_status()
+    perm, T = to_host(perm_d), to_host(T_d)
+    j_equal = bool(np.array_equal(perm[:k], want["J"]))
+    err_mixed = oracle.exact_error(A64, perm, T)
+    dT = np.abs(T - want["T"]).max() / np.abs(want["T"]).max() if j_equal else float("inf")
+    print(f"mixed floor sweep: sigma_k+1/sigma_1 = {ratio:.0e}  rho = {rho:.2e}  J equal = {j_equal}  "
+          f"max|dT|/max|T| = {dT:.2e}  error mixed / FP64 = {err_mixed:.2e} / {err_fp64:.2e}  "
+          f"floor = {floor:.0e}  accepted = {accepted}")
+    # rho estimates the gap of the sketch: within a factor 30 of sigma_{k+1} / sigma_1
+    assert ratio / 30 <= rho <= ratio * 30 or (ratio < 1e-7 and rho <= 1e-5)
+    if accepted:
+        assert j_equal, "accepted above the floor, but J differs from the FP64 path's"
+        assert err_mixed <= 2.0 * err_fp64 + 1e-12, (err_mixed, err_fp64)
+    if ratio <= 1e-8:
+        # far below the floor the mixed sketch's own noise sets the error: the
+        # plan must not accept it
+        assert not accepted
