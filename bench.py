@@ -377,12 +377,15 @@ def run_ours(args, cfg, world, rank, local):
         del A, Y, perm, T
         torch.cuda.empty_cache()
         try:
-            sweep, select_shape = serve_sweep(args, [2560.0], args.serving_requests, rank, local)
-            s = sweep[0]
+            rates = [float(x) for x in args.serving_rates.split(",")]
+            sweep, select_shape = serve_sweep(args, rates, args.serving_requests, rank, local, args.pool)
+            s = max(sweep, key=lambda x: x["served_per_s"])     # saturation: the highest served rate
             line["serving"] = {"value": s["served_per_s"], "unit": "IDs/s", "p50_ms": s["p50_ms"],
                                "p99_ms": s["p99_ms"], "gb_per_s": s["gb_per_s"], "offered_per_s": s["offered_per_s"],
-                               "errors": s["errors"], "slots": args.slots, "select": select_shape,
-                               "workload": f"{args.serving_requests} {SERVING_WORKLOAD}, FP64-emulated"}
+                               "errors": sum(x["errors"] for x in sweep), "slots": args.slots,
+                               "select": select_shape, "sweep": sweep,
+                               "workload": f"{args.serving_requests} requests per rate, {SERVING_WORKLOAD}, "
+                                           f"cycling through {args.pool} device-resident matrices, FP64-emulated"}
         except Exception as exc:            # reported in the line; the headline above stands
             line["serving"] = {"error": f"{type(exc).__name__}: {exc}"}
     if rank == 0:
@@ -433,6 +436,42 @@ def time_rounded_omega(args, cfg, A, stream, world, rank):
             "omega": "complex Gaussian rounded to 24 bits below each row's maximum (ties to even)"}
 
 
+def run_select_phase(args, cfg, world, rank, local):
+    """The pivoted QR alone on a seeded random l x n complex Y (the sketch's
+    shape for the config), with the plan's default launch shape; one JSON
+    line with the per-call time (CUDA events).  For profiling the select
+    without the config's A on the device."""
+    import torch
+    import synth
+    import paper_1205_3830_gb300 as rid
+    from paper_1205_3830_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.MASTER_SEED + 11 + rank)
+    Y0 = torch.randn((cfg.n, cfg.l), dtype=torch.complex128, device=dev, generator=gen).t()
+    plan = rid.Plan(cfg.m, cfg.n, cfg.k, cfg.l, seed=cfg.seed + rank, mode=args.mode)
+    Y = rid.colmajor_empty(cfg.l, cfg.n, device=dev)
+    perm = torch.empty(cfg.n, dtype=torch.int32, device=dev)
+    times = []
+    for s in range(args.warmup + args.steps):
+        Y.copy_(Y0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.select(Y, perm)
+        e1.record()
+        torch.cuda.synchronize()
+        if s >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+    plan.sync_status()
+    if rank == 0:
+        print(json.dumps({"phase": "select", "config": cfg.name, "l": cfg.l, "n": cfg.n, "k": cfg.k,
+                          "select_ms": statistics.mean(times), "select_ms_min": min(times),
+                          "launches": plan.stats()["select_launches"]}), flush=True)
+    plan.close()
+
+
 def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     """Same metric with host buffers: every step copies A in from pinned host
     memory and reads perm, T and the estimate back.  With the row-probe
@@ -441,8 +480,12 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     and the next step's copy of a panel starts as soon as this step's sketch
     of it is done (the host->device link, about 211 GB/s, is the bound)."""
     import torch
+    allowed = os.sched_getaffinity(0)
+    placement = pin_near_gpu(A.device)          # before the pinned buffer is allocated and first touched
     A_host = torch.empty((cfg.n, cfg.m), dtype=A.dtype, pin_memory=True).t()
     A_host.copy_(A)
+    torch.cuda.synchronize()
+    os.sched_setaffinity(0, allowed)
     perm_h = torch.empty(cfg.n, dtype=torch.int32, pin_memory=True)
     T_h = torch.empty((cfg.n - cfg.k, cfg.k), dtype=torch.complex128, pin_memory=True).t()
     torch.cuda.synchronize()
@@ -472,26 +515,42 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
 
     link_first = link_rate()
 
-    def copy_in():
+    # optional trace of the timed passes: per step and panel, the copy's start
+    # and end (copy stream) and the sketch's start and end (compute stream)
+    trace = []
+
+    def timed_event(stream_):
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream_)
+        return ev
+
+    def copy_in(rec=None):
         for i, (c0, nc) in enumerate(panels):
             copy_stream.wait_event(done[i])          # this panel's previous sketch has read A
+            t0 = timed_event(copy_stream) if rec is not None else None
             with torch.cuda.stream(copy_stream):
                 A[:, c0:c0 + nc].copy_(A_host[:, c0:c0 + nc], non_blocking=True)
             landed[i].record(copy_stream)
+            if rec is not None:
+                rec.append({"panel": i, "copy": (t0, timed_event(copy_stream))})
 
-    def passes(steps):
+    def passes(steps, traced=False):
         copy_stream.wait_stream(stream)
-        copy_in()
+        recs = [[] for _ in range(steps)] if traced else None
+        copy_in(recs[0] if traced else None)
         for step in range(steps):
             for i, (c0, nc) in enumerate(panels):
                 stream.wait_event(landed[i])
+                s0 = timed_event(stream) if traced else None
                 if pipelined:
                     plan.sketch_cols(A, Y, c0, nc)
                 else:
                     plan.sketch(A, Y)
                 done[i].record(stream)
+                if traced and i < len(recs[step]):
+                    recs[step][i]["sketch"] = (s0, timed_event(stream))
             if rows and step + 1 < steps:
-                copy_in()                            # the next step's A, behind this step's sketch
+                copy_in(recs[step + 1] if traced else None)   # the next step's A, behind this step's sketch
             plan.select(Y, perm)
             plan.solve(Y, T)
             if rows:
@@ -500,6 +559,10 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
                 plan.error(A, perm, T, args.nprobe, 1)
             perm_h.copy_(perm, non_blocking=True)
             T_h.copy_(T, non_blocking=True)
+            if not rows and step + 1 < steps:
+                copy_stream.wait_stream(stream)     # the column-probe error read A: the next copy follows it
+                copy_in(recs[step + 1] if traced else None)
+        return recs
 
     passes(1)                                        # untimed: the first pass of this pattern
     torch.cuda.synchronize()
@@ -511,6 +574,11 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
     stop.record(stream)
     torch.cuda.synchronize()
     ms = max_over_ranks(start.elapsed_time(stop), world) / args.e2e_steps
+    # a traced pass after the timed region (events add little, but none sit in it)
+    t_start = timed_event(copy_stream)
+    recs = passes(max(2, args.e2e_steps), traced=True)
+    torch.cuda.synchronize()
+    trace = e2e_trace_summary(recs, t_start, [nc for _, nc in panels], cfg.m, A.element_size())
     del A_host
     h2d = cfg.a_bytes
     d2h = 4 * cfg.n + 16 * cfg.k * (cfg.n - cfg.k) + 16
@@ -520,7 +588,62 @@ def run_e2e(args, cfg, plan, A, Y, perm, T, stream, world):
             "h2d_link_gbs": link_gbs, "frac_of_link": value / (world * link_gbs),
             "pipeline": (f"A in {len(panels)} column panels on a copy stream, overlapped with the sketch"
                          if pipelined else ("A copied whole; the next step's copy overlaps select, solve and "
-                                            "error" if rows else "A copied whole, then the ID"))}
+                                            "error" if rows else "A copied whole, then the ID")),
+            "trace": trace, "host_placement": placement}
+
+
+def pin_near_gpu(device):
+    """Run this process on the CPUs that sysfs lists as local to the GPU's PCI
+    device, so the pinned host buffer allocated next lands in that node's
+    memory; returns what was found (the bus id, the NUMA node, the CPU list)."""
+    import torch
+    out = {"affinity_set": False}
+    try:
+        p = torch.cuda.get_device_properties(device)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        out["pci"] = bus
+        base = f"/sys/bus/pci/devices/{bus}"
+        with open(f"{base}/numa_node") as f:
+            out["numa_node"] = int(f.read().strip())
+        with open(f"{base}/local_cpulist") as f:
+            cpulist = f.read().strip()
+        out["local_cpus"] = cpulist
+        cpus = set()
+        for part in cpulist.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        allowed = os.sched_getaffinity(0)
+        if cpus and cpus & allowed and cpus & allowed != allowed:
+            os.sched_setaffinity(0, cpus & allowed)
+            out["affinity_set"] = True
+    except (OSError, ValueError, AttributeError) as exc:
+        out["note"] = f"{type(exc).__name__}: {exc}"
+    return out
+
+
+def e2e_trace_summary(recs, t_start, widths, m, esize):
+    """Per-panel copy and sketch intervals of a traced end-to-end pass: the
+    copy rate of each panel, the copy engine's busy share, the time the
+    sketch of a panel waited for its copy and the copy for the sketch."""
+    steps = []
+    for rec in recs:
+        t = [(r["copy"][0], r["copy"][1], r["sketch"][0], r["sketch"][1]) for r in rec if "sketch" in r]
+        if not t:
+            continue
+        c_ms = [a.elapsed_time(b) for a, b, _, _ in t]
+        s_ms = [c.elapsed_time(d) for _, _, c, d in t]
+        span = t[0][0].elapsed_time(t[-1][3])
+        rates = [w * m * esize / 1e9 / (ms / 1e3) for w, ms in zip(widths, c_ms) if ms > 0]
+        # idle gaps of the copy engine between consecutive panels' copies
+        gaps = [t[i][1].elapsed_time(t[i + 1][0]) for i in range(len(t) - 1)]
+        steps.append({"span_ms": span, "copy_ms": sum(c_ms), "sketch_ms": sum(s_ms),
+                      "copy_busy_frac": sum(c_ms) / span if span > 0 else None,
+                      "copy_gbs_min": min(rates) if rates else None, "copy_gbs_max": max(rates) if rates else None,
+                      "copy_gap_ms_max": max(gaps) if gaps else 0.0})
+    return {"steps": steps}
 
 
 def compare_with_fp64(args, cfg, A, perm, T, stream, rank):
@@ -697,41 +820,49 @@ def run_batched(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
-def serve_sweep(args, rates, requests, rank, local):
-    """Serve `requests` seeded requests at each offered rate; returns the
-    sweep (served IDs/s, GB of A/s, p50 / p99 ms per rate) and the server's
-    select launch shape."""
+def serve_sweep(args, rates, requests, rank, local, pool=64):
+    """Serve `requests` seeded requests at each offered rate (Poisson arrivals)
+    and return the sweep (served IDs/s, GB of A/s, p50 / p99 ms, the plans'
+    share per rate) and the server's select launch shape.  The requests cycle
+    through `pool` distinct device matrices drawn from the workload's shape
+    distribution (request i: matrix i % pool, its own seed 2000 + i), so a
+    thousand requests per rate fit beside the server's memory."""
+    import numpy as np
     import torch
     import synth
     from paper_1205_3830_gb300 import serve
     dev = torch.device("cuda", local)
     gen = torch.Generator(device=dev)
     gen.manual_seed(synth.MASTER_SEED + 5 + rank)
-    specs = synth.serving_requests(requests, 1.0, synth.MASTER_SEED + 5 + rank)   # shapes; times rescaled per rate
+    pool = max(1, min(pool, requests))
+    specs = synth.serving_requests(pool, 1.0, synth.MASTER_SEED + 5 + rank)      # shapes of the pool
     mats = [device_lowrank(m, n, k, 1e-10, gen, dev) for (_, m, n, k, l) in specs]
-    gaps = [specs[0][0]] + [specs[i][0] - specs[i - 1][0] for i in range(1, len(specs))]
-    a_bytes = sum(16.0 * m * n for (_, m, n, k, l) in specs)
+    a_bytes = sum(16.0 * specs[i % pool][1] * specs[i % pool][2] for i in range(requests))
     # warm-up: every kernel once
     serve.run_one(mats[0], specs[0][3], specs[0][4], 1, args.nprobe, 1, args.mode)
     sweep = []
     for rate in rates:
         opts = {} if args.select_ctas is None else {"select_ctas": args.select_ctas}
         srv = serve.Server(slots=args.slots, mode=args.mode, **opts)
+        gaps = np.random.default_rng(synth.MASTER_SEED + 7 + rank).exponential(1.0 / rate, size=requests)
         t0 = time.perf_counter()
         due = 0.0
-        for i, (_, m, n, k, l) in enumerate(specs):
-            due += gaps[i] / rate
+        for i in range(requests):
+            _, m, n, k, l = specs[i % pool]
+            due += gaps[i]
             wait = t0 + due - time.perf_counter()
             if wait > 0:
                 time.sleep(wait)
-            srv.submit(i, mats[i], k, l, 2000 + i, args.nprobe, 1)
-        done = srv.drain(timeout=600)            # a stuck request ends the sweep with an error, not a hang
+            srv.submit(i, mats[i % pool], k, l, 2000 + i, args.nprobe, 1)
+        done = srv.drain(timeout=900)            # a stuck request ends the sweep with an error, not a hang
         wall = time.perf_counter() - t0
         srv.close()
         errs = sum(1 for r in done if r.error is not None)
         st = serve.latency_stats(done)
-        sweep.append({"offered_per_s": rate, "served_per_s": len(done) / wall, "gb_per_s": a_bytes / 1e9 / wall,
-                      "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"), "peak_concurrent": srv.peak_running,
+        sweep.append({"offered_per_s": rate, "requests": len(done), "served_per_s": len(done) / wall,
+                      "gb_per_s": a_bytes / 1e9 / wall, "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"),
+                      "plan_dev_p50_ms": st.get("plan_dev_p50_ms"), "plan_host_p50_ms": st.get("plan_host_p50_ms"),
+                      "id_dev_p50_ms": st.get("id_dev_p50_ms"), "peak_concurrent": srv.peak_running,
                       "peak_hbm_gb": srv.peak_used / 1e9, "errors": errs})
     ctas = srv.select_ctas
     select_shape = ("the plan's default (one cooperative launch)" if ctas is None or ctas < 0 else
@@ -754,7 +885,7 @@ def run_serving(args, world, rank, local):
     build.build()
     torch.cuda.set_device(local)
     rates = [float(x) for x in args.rates.split(",")]
-    sweep, select_shape = serve_sweep(args, rates, args.requests, rank, local)
+    sweep, select_shape = serve_sweep(args, rates, args.requests, rank, local, args.pool)
     best = max(sweep, key=lambda x: x["served_per_s"])
     line = {
         "metric": METRIC, "value": best["served_per_s"], "unit": "IDs/s", "n_gpus": world, "steps": len(rates),
@@ -792,15 +923,23 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="problems per batch (--config batched)")
-    ap.add_argument("--requests", type=int, default=64, help="requests per rate (--config serving)")
-    ap.add_argument("--rates", default="5,20,80,320", help="offered request rates per second (--config serving)")
+    ap.add_argument("--requests", type=int, default=1000, help="requests per rate (--config serving)")
+    ap.add_argument("--rates", default="40,160,320,640,1280,2560",
+                    help="offered request rates per second (--config serving)")
+    ap.add_argument("--pool", type=int, default=64,
+                    help="distinct request matrices the requests cycle through (serving)")
     ap.add_argument("--slots", type=int, default=8, help="concurrent requests (--config serving)")
-    ap.add_argument("--serving-requests", type=int, default=48,
-                    help="requests of the serving sample added to the headline line (0: none)")
+    ap.add_argument("--serving-requests", type=int, default=1000,
+                    help="requests per rate of the serving sweep added to the headline line (0: none)")
+    ap.add_argument("--serving-rates", default="160,320,640,1280,2560",
+                    help="offered rates per second of the serving sweep added to the headline line")
     ap.add_argument("--select-ctas", type=int, default=None,
                     help="launch shape of each served request's select: 0 one launch per step, N > 0 one "
                          "cooperative launch of at most N CTAs, -1 the plan's default (--config serving; "
                          "default: the server's, one launch per step)")
+    ap.add_argument("--phase", choices=("id", "select"), default="id",
+                    help="select: time the pivoted QR alone on a random sketch-shaped Y (l x n of the config; "
+                         "profiling without the config's A on the device)")
     ap.add_argument("--m", type=int, default=0, help="override m (profiling of smaller cases)")
     ap.add_argument("--n", type=int, default=0, help="override n (profiling of smaller cases)")
     args = ap.parse_args()
@@ -824,6 +963,8 @@ def main():
         cfg = dataclasses.replace(cfg, m=args.m or cfg.m, n=args.n or cfg.n)
     if args.impl == "reference":
         run_reference(args, cfg, world, rank)
+    elif args.phase == "select":
+        run_select_phase(args, cfg, world, rank, local)
     else:
         run_ours(args, cfg, world, rank, local)
     if world > 1:

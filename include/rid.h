@@ -219,6 +219,16 @@ RID_API rid_status rid_sketch_cols(rid_plan_t plan, const void* A, int64_t lda, 
  *   the stream.  rid_plan_omega still returns the l rows of the test matrix. */
 RID_API rid_status rid_plan_set_probes(rid_plan_t plan, int32_t nprobe, uint64_t probe_seed);
 
+/* rid_plan_create and rid_plan_set_probes(plan, nprobe, probe_seed) in one
+ * call: the plan is built with its nprobe row probes (0 <= nprobe <= 16) from
+ * the start, so the tensor-core modes cut the digits of the test matrix and
+ * the probe rows once, and nothing synchronizes (all work is ordered on
+ * stream).  The results are those of the two calls.  Errors as for
+ * rid_plan_create and rid_plan_set_probes; *plan is NULL on failure. */
+RID_API rid_status rid_plan_create_probes(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
+                                          rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream,
+                                          int32_t nprobe, uint64_t probe_seed);
+
 /* Error of the ID from the row probes of the last rid_sketch, without reading
  * A.  E = A - A(:, J) P has E(:, J) = 0 and E(:, perm[k+i]) =
  * A(:, perm[k+i]) - A(:, J) T(:, i), so

@@ -110,7 +110,9 @@ class Plan:
     """One ID shape (m, n, k, l) with its seeded Gaussian test matrix Omega."""
 
     def __init__(self, m, n, k, l, seed=0, dtype=torch.complex128, mode="fp64", stream=None,
-                 device=None):
+                 device=None, nprobe=0, probe_seed=1):
+        """nprobe > 0 builds the plan with row probes from the start (as
+        set_probes(nprobe, probe_seed) after it, without its synchronization)."""
         self._lib = _native.load()
         self.m, self.n, self.k, self.l = int(m), int(n), int(k), int(l)
         self.seed = int(seed)
@@ -125,11 +127,18 @@ class Plan:
         self.stream = stream
         handle = ctypes.c_void_p()
         with torch.cuda.device(self.device):
-            st = self._lib.rid_plan_create(ctypes.byref(handle), self.m, self.n, self.k, self.l,
-                                           _DTYPES[dtype], MODES[mode], self.seed & (2 ** 64 - 1),
-                                           ctypes.c_void_p(stream.cuda_stream))
-        check(st, "rid_plan_create")
+            if nprobe:
+                st = self._lib.rid_plan_create_probes(ctypes.byref(handle), self.m, self.n, self.k, self.l,
+                                                      _DTYPES[dtype], MODES[mode], self.seed & (2 ** 64 - 1),
+                                                      ctypes.c_void_p(stream.cuda_stream), int(nprobe),
+                                                      int(probe_seed) & (2 ** 64 - 1))
+            else:
+                st = self._lib.rid_plan_create(ctypes.byref(handle), self.m, self.n, self.k, self.l,
+                                               _DTYPES[dtype], MODES[mode], self.seed & (2 ** 64 - 1),
+                                               ctypes.c_void_p(stream.cuda_stream))
+        check(st, "rid_plan_create_probes" if nprobe else "rid_plan_create")
         self._h = handle
+        self.nrow = int(nprobe)
 
     # -- lifetime --------------------------------------------------------
     def close(self):

@@ -20,6 +20,8 @@ _u64 = ctypes.c_uint64
 SIGNATURES = {
     "rid_plan_create": (ctypes.c_int, [ctypes.POINTER(_c_plan), _i64, _i64, _i32, _i32, ctypes.c_int,
                                        ctypes.c_int, _u64, _p]),
+    "rid_plan_create_probes": (ctypes.c_int, [ctypes.POINTER(_c_plan), _i64, _i64, _i32, _i32, ctypes.c_int,
+                                              ctypes.c_int, _u64, _p, _i32, _u64]),
     "rid_plan_destroy": (ctypes.c_int, [_c_plan]),
     "rid_plan_footprint": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]),

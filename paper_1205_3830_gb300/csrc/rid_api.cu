@@ -250,8 +250,8 @@ rid_status rid_plan_footprint(int64_t m, int64_t n, int32_t k, int32_t l, rid_dt
   return RID_OK;
 }
 
-rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
-                           rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream) {
+static rid_status plan_create_impl(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype,
+                                   rid_mode mode, uint64_t seed, void* stream, bool init_tc) {
   if (!plan) return RID_EINVAL;
   *plan = nullptr;
   const rid_status chk = check_plan_args(m, n, k, l, dtype, mode);
@@ -307,7 +307,7 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
     free(p);
     return RID_ECUDA;
   }
-  if (mode != RID_FP64_NATIVE) {
+  if (mode != RID_FP64_NATIVE && init_tc) {
     const rid_status s = rid_tc_plan_init(p);
     if (s != RID_OK) {
       rid_dev_free(base, p->stream);
@@ -318,6 +318,11 @@ rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, in
   }
   *plan = p;
   return RID_OK;
+}
+
+rid_status rid_plan_create(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l,
+                           rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream) {
+  return plan_create_impl(plan, m, n, k, l, dtype, mode, seed, stream, true);
 }
 
 rid_status rid_plan_destroy(rid_plan_t p) {
@@ -390,14 +395,17 @@ rid_status rid_plan_round_omega(rid_plan_t p, int32_t bits) {
   return from_cuda(cudaStreamSynchronize(p->stream));
 }
 
-rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
+// sync: the public call synchronizes the plan's stream before and after; a
+// plan being created has nothing in flight, and everything below is ordered
+// on its stream, so creation skips the waits.
+static rid_status set_probes_impl(rid_plan_t p, int32_t nprobe, uint64_t probe_seed, bool sync) {
   if (!p || nprobe < 0 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
   if (nprobe > 0 && p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED && p->mode != RID_MIXED_BF16)
     return RID_EUNSUPPORTED;
   if (p->l + nprobe > 512) return RID_EUNSUPPORTED;
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
-  cudaError_t e = cudaStreamSynchronize(p->stream);
+  cudaError_t e = sync ? cudaStreamSynchronize(p->stream) : cudaSuccess;
   if (e != cudaSuccess) return from_cuda(e);
   const int32_t ls = p->l + nprobe;
   char* base = nullptr;
@@ -422,7 +430,7 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
     if (e == cudaSuccess && p->omega_bits > 0)
       e = rid_launch_round_rows((double2*)base + (int64_t)p->l * p->ldo, nprobe, p->m, p->ldo, p->omega_bits,
                                 p->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(p->stream);
+    if (e == cudaSuccess && sync) e = cudaStreamSynchronize(p->stream);
     if (e != cudaSuccess) {
       rid_dev_free(base, p->stream);
       return from_cuda(e);
@@ -455,7 +463,30 @@ rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed
   }
   const rid_status ps = rid_probe_state_reset(p);
   if (ps != RID_OK) return ps;
-  return from_cuda(cudaStreamSynchronize(p->stream));
+  return sync ? from_cuda(cudaStreamSynchronize(p->stream)) : RID_OK;
+}
+
+rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
+  return set_probes_impl(p, nprobe, probe_seed, true);
+}
+
+rid_status rid_plan_create_probes(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype,
+                                  rid_mode mode, uint64_t seed, void* stream, int32_t nprobe, uint64_t probe_seed) {
+  if (!plan) return RID_EINVAL;
+  *plan = nullptr;
+  if (nprobe < 0 || nprobe > RID_MAX_PROBES) return RID_EINVAL;
+  rid_plan_t p = nullptr;
+  const rid_status s = plan_create_impl(&p, m, n, k, l, dtype, mode, seed, stream, nprobe == 0);
+  if (s != RID_OK) return s;
+  if (nprobe > 0) {
+    const rid_status t = set_probes_impl(p, nprobe, probe_seed, false);
+    if (t != RID_OK) {
+      rid_plan_destroy(p);
+      return t;
+    }
+  }
+  *plan = p;
+  return RID_OK;
 }
 
 rid_status rid_sketch(rid_plan_t p, const void* A, int64_t lda, void* Y, int64_t ldy) {

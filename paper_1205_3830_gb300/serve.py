@@ -13,7 +13,12 @@ launch, so it never holds the whole GPU while the other slots wait (the
 results are the same bits).
 
 Latency is measured from submit() to the moment the result (J, T, the error
-estimate) is available on the host side of the worker.
+estimate) is available on the host side of the worker.  A request's matrix A
+is on the device when it is submitted (the caller owns it); no host-device
+copy of A is part of the latency.  Every request builds its own plan (the
+test matrix Omega of its seed, its digit tiles and workspace) from the
+library's stream-ordered memory pool; the plan's share of the work is
+reported per request (plan_host_ms, plan_dev_ms beside id_dev_ms).
 """
 from __future__ import annotations
 
@@ -167,16 +172,20 @@ def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=
     the results do not depend on it."""
     m, n = A.shape
     stream = stream or torch.cuda.current_stream(A.device)
-    with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream) as plan:
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t0 = time.perf_counter()
+    ev[0].record(stream)
+    rows = mode in ROW_PROBE_MODES
+    with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream, nprobe=nprobe if rows else 0,
+              probe_seed=probe_seed) as plan:
         if select_ctas is not None:
             plan.set_select_grid(select_ctas)
-        rows = mode in ROW_PROBE_MODES
-        if rows:
-            plan.set_probes(nprobe, probe_seed)
         with torch.cuda.stream(stream):
             Y = colmajor_empty(l, n, device=A.device)
             perm = torch.empty(n, dtype=torch.int32, device=A.device)
             T = colmajor_empty(k, n - k, device=A.device)
+        ev[1].record(stream)
+        plan_host_ms = 1e3 * (time.perf_counter() - t0)
         plan.sketch(A, Y)
         plan.select(Y, perm)
         plan.solve(Y, T)
@@ -184,8 +193,10 @@ def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=
             est, upper = plan.error_sketched(perm, T)                # synchronizes the stream
         else:
             est, upper = plan.error(A, perm, T, nprobe, probe_seed)
+        ev[2].record(stream)
         plan.sync_status()
-        return {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper}
+        return {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper, "plan_host_ms": plan_host_ms,
+                "plan_dev_ms": ev[0].elapsed_time(ev[1]), "id_dev_ms": ev[1].elapsed_time(ev[2])}
 
 
 def latency_stats(reqs):
@@ -196,4 +207,10 @@ def latency_stats(reqs):
     def pct(p):
         return lat[min(len(lat) - 1, int(round(p / 100.0 * (len(lat) - 1))))]
 
-    return {"p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "max_ms": 1e3 * lat[-1], "count": len(lat)}
+    out = {"p50_ms": 1e3 * pct(50), "p99_ms": 1e3 * pct(99), "max_ms": 1e3 * lat[-1], "count": len(lat)}
+    parts = [r.result for r in reqs if isinstance(getattr(r, "result", None), dict) and "plan_dev_ms" in r.result]
+    if parts:
+        for key in ("plan_host_ms", "plan_dev_ms", "id_dev_ms"):
+            vals = sorted(p[key] for p in parts)
+            out[key.replace("_ms", "_p50_ms")] = vals[len(vals) // 2]
+    return out

@@ -195,3 +195,30 @@ def test_sketch_cols_argument_errors(rid):
             with pytest.raises(RIDError, match="EINVAL"):
                 plan.sketch_cols(A, Y, c0, nc)
         plan.sketch_cols(A, Y, 256, 144)                  # the last, ragged panel
+
+
+@pytest.mark.parametrize("mode", MODES + ["bf16"])
+def test_plan_created_with_probes_matches_set_probes(rid, mode):
+    """rid_plan_create_probes gives the bits of rid_plan_create + rid_plan_set_probes:
+    the sketch Y (and the probe products behind the estimate), J, T and the estimate."""
+    m, n, k, l = 3000, 2200, 24, 34            # 18 column blocks: the CTA-pair product in the emulated mode
+    A = lowrank(m, n, k, seed=8)
+    dtype = torch.complex64 if mode == "bf16" else torch.complex128
+    Ad = to_dev_colmajor(A.astype(np.complex64) if mode == "bf16" else A, dtype)
+    outs = []
+    for built_in in (False, True):
+        kw = {"nprobe": 8, "probe_seed": 4} if built_in else {}
+        with rid.Plan(m, n, k, l, seed=6, dtype=dtype, mode=mode, **kw) as plan:
+            if not built_in:
+                plan.set_probes(8, 4)
+            assert plan.nrow == 8
+            Y = plan.sketch(Ad)
+            Y0 = Y.clone()
+            perm = plan.select(Y)
+            T = plan.solve(Y)
+            est = plan.error_sketched(perm, T)
+            plan.sync_status()
+            outs.append((to_host(Y0), to_host(perm), to_host(T), est))
+    (Ya, pa, Ta, ea), (Yb, pb, Tb, eb) = outs
+    assert np.array_equal(Ya, Yb) and np.array_equal(pa, pb) and np.array_equal(Ta, Tb)
+    assert ea == eb

@@ -82,6 +82,15 @@ def test_latency_percentiles():
     assert serve.latency_stats([]) == {}
 
 
+def test_latency_stats_report_the_plans_share():
+    from paper_1205_3830_gb300 import serve
+    reqs = [types.SimpleNamespace(latency=0.01 * (i + 1),
+                                  result={"plan_host_ms": 1.0 + i, "plan_dev_ms": 0.5 * i, "id_dev_ms": 10.0 + i})
+            for i in range(5)]
+    st = serve.latency_stats(reqs)
+    assert st["plan_host_p50_ms"] == 3.0 and st["plan_dev_p50_ms"] == 1.0 and st["id_dev_p50_ms"] == 12.0
+
+
 def test_traffic_figure_follows_the_kernel_source(bench, monkeypatch):
     """The ncu traffic of the product kernel is reported only for the source
     it was measured on: any other hash turns it off."""
