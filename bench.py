@@ -35,8 +35,12 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
 # valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
-TC_TRAFFIC = {"bytes_per_launch": 80.4e9,   # 16 x (4.898 + 0.127) GB: the 65536 x 2048 capture, scaled by A's entries
-              "source_sha1": "b2f7ed03c64df6320efa7a71b04e096a46b9a50a"}
+# DRAM bytes of one product launch of the 32 GiB workload (one column panel of
+# 2048 columns): the 65536 x 2048 capture of profiles/sketch_tc_kernel_65536x2048.md,
+# 4 x (4.896 + 0.127) GB, scaled by the panel's 4x rows; reported only for the
+# source it was measured on
+TC_TRAFFIC = {"bytes_per_launch": 20.09e9,
+              "source_sha1": "578149bc5400b51fcb31d8cf494e45bf5e468de8"}
 
 
 def tc_source_unchanged():
@@ -237,11 +241,11 @@ def run_ours(args, cfg, world, rank, local):
     A = synth.device.device_matrix(cfg, device=dev)
     stream = torch.cuda.current_stream(dev)
     a_dtype = torch.complex64 if cfg.dtype == "c64" else torch.complex128
-    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, dtype=a_dtype, mode=args.mode, stream=stream)
-    plan.enable_timing()
     rows = args.estimator == "rows"
-    if rows:
-        plan.set_probes(args.nprobe, 1)       # the error's products ride along in the sketch
+    # the error's products ride along in the sketch: the plan is built with its row probes
+    plan = rid.Plan(m, n, k, l, seed=cfg.seed + rank, dtype=a_dtype, mode=args.mode, stream=stream,
+                    nprobe=args.nprobe if rows else 0, probe_seed=1)
+    plan.enable_timing()
     if args.omega == "srft":
         plan.use_srft(cfg.seed + 1)           # the paper's S F D in place of the Gaussian rows
     if args.omega_bits:
@@ -325,11 +329,14 @@ def run_ours(args, cfg, world, rank, local):
         achieved = tc_flops / t_prod / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": bf16_sust, "unit": "TFLOP/s",
                 "frac": achieved / bf16_sust,
-                "traffic": TC_TRAFFIC.get("bytes_per_launch") if args.mode == "fp64_emulated" and tc_source_unchanged() else None,
+                "traffic": (TC_TRAFFIC.get("bytes_per_launch") if args.mode == "fp64_emulated" and tc_source_unchanged()
+                            and cfg.name == "large_tall" and not (args.m or args.n) and rows else None),
                 "kernel": "sketch_tc_kernel" if args.mode == "fp64_emulated" else "sketch_mixed_kernel",
                 "peak_source": "of measured: MEASURED_PEAKS.json bf16_tflops_sustained (kernel timed inside a long step)",
-                "per_launch": f"{pairs} slice pairs x 2 x (2 ls)(2m)n flops, ls = l + r row probes" if rows else
-                              f"{pairs} slice pairs x 2 x (2l)(2m)n flops", "fp64_equivalent": fp64_equiv}
+                "per_launch": (f"{pairs} slice pairs x 2 x (2 ls)(2m)(n / panels) flops, ls = l + r row probes, "
+                               f"one launch per column panel" if rows else
+                               f"{pairs} slice pairs x 2 x (2l)(2m)(n / panels) flops, one launch per column panel"),
+                "fp64_equivalent": fp64_equiv}
     # whole-ID roofline: sum over steps of max(bytes / HBM, flops / the peak of the pipe used)
     p64 = FP64_PEAK_TFLOPS * 1e12
     a_b = float(cfg.a_bytes)
@@ -369,6 +376,13 @@ def run_ours(args, cfg, world, rank, local):
         line["omega_rounded_24bit"] = time_rounded_omega(args, cfg, A, stream, world, rank)
     if args.mode == "bf16":
         line["vs_fp64_path"] = compare_with_fp64(args, cfg, A, perm, T, stream, rank)
+        # the plan's own verdict on the last ID: rho (the pivoted QR's estimate
+        # of sigma_{k+1} / sigma_1) against the mode's measured floor
+        rho, floor, accepted = plan.accuracy(Y)
+        line["accuracy"] = {"rho": rho, "floor": floor, "accepted": accepted,
+                            "reading": ("above the mixed mode's measured floor: the FP64 path's J and an ID error "
+                                        "within 2x of it" if accepted else
+                                        "below the mixed mode's measured floor: recompute in an FP64 mode")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, cfg, A)
     plan.close()
@@ -452,6 +466,8 @@ def run_select_phase(args, cfg, world, rank, local):
     gen.manual_seed(synth.MASTER_SEED + 11 + rank)
     Y0 = torch.randn((cfg.n, cfg.l), dtype=torch.complex128, device=dev, generator=gen).t()
     plan = rid.Plan(cfg.m, cfg.n, cfg.k, cfg.l, seed=cfg.seed + rank, mode=args.mode)
+    if args.select_ctas is not None:
+        plan.set_select_grid(args.select_ctas)
     Y = rid.colmajor_empty(cfg.l, cfg.n, device=dev)
     perm = torch.empty(cfg.n, dtype=torch.int32, device=dev)
     times = []
@@ -467,8 +483,9 @@ def run_select_phase(args, cfg, world, rank, local):
     plan.sync_status()
     if rank == 0:
         print(json.dumps({"phase": "select", "config": cfg.name, "l": cfg.l, "n": cfg.n, "k": cfg.k,
-                          "select_ms": statistics.mean(times), "select_ms_min": min(times),
-                          "launches": plan.stats()["select_launches"]}), flush=True)
+                          "select_ctas": args.select_ctas, "select_ms": statistics.mean(times),
+                          "select_ms_min": min(times), "launches": plan.stats()["select_launches"],
+                          "perm_head": perm[:4].tolist()}), flush=True)
     plan.close()
 
 
@@ -862,7 +879,8 @@ def serve_sweep(args, rates, requests, rank, local, pool=64):
         sweep.append({"offered_per_s": rate, "requests": len(done), "served_per_s": len(done) / wall,
                       "gb_per_s": a_bytes / 1e9 / wall, "p50_ms": st.get("p50_ms"), "p99_ms": st.get("p99_ms"),
                       "plan_dev_p50_ms": st.get("plan_dev_p50_ms"), "plan_host_p50_ms": st.get("plan_host_p50_ms"),
-                      "id_dev_p50_ms": st.get("id_dev_p50_ms"), "peak_concurrent": srv.peak_running,
+                      "id_dev_p50_ms": st.get("id_dev_p50_ms"), "plans_reused": st.get("plans_reused"),
+                      "peak_concurrent": srv.peak_running,
                       "peak_hbm_gb": srv.peak_used / 1e9, "errors": errs})
     ctas = srv.select_ctas
     select_shape = ("the plan's default (one cooperative launch)" if ctas is None or ctas < 0 else
@@ -934,9 +952,9 @@ def main():
     ap.add_argument("--serving-rates", default="160,320,640,1280,2560",
                     help="offered rates per second of the serving sweep added to the headline line")
     ap.add_argument("--select-ctas", type=int, default=None,
-                    help="launch shape of each served request's select: 0 one launch per step, N > 0 one "
-                         "cooperative launch of at most N CTAs, -1 the plan's default (--config serving; "
-                         "default: the server's, one launch per step)")
+                    help="launch shape of the select: 0 one launch per step, N > 0 one cooperative launch of at "
+                         "most N CTAs through L2, -1 the plan's default (--config serving: each served request's "
+                         "select, default the server's, one launch per step; --phase select: default the plan's)")
     ap.add_argument("--phase", choices=("id", "select"), default="id",
                     help="select: time the pivoted QR alone on a random sketch-shaped Y (l x n of the config; "
                          "profiling without the config's A on the device)")

@@ -229,6 +229,20 @@ RID_API rid_status rid_plan_create_probes(rid_plan_t* plan, int64_t m, int64_t n
                                           rid_dtype dtype, rid_mode mode, uint64_t seed, void* stream,
                                           int32_t nprobe, uint64_t probe_seed);
 
+/* Reuse a plan for another ID of the same shape: redraw its test matrix for
+ * seed (and, if it has row probes, the probes for probe_seed) in place and
+ * re-cut their digits, as rid_plan_create_probes with these seeds would;
+ * nothing is allocated.  Later calls give the bits of a new plan with these
+ * seeds.  Asynchronous on the plan's stream.  RID_EUNSUPPORTED for a plan
+ * whose Omega was replaced or rounded (rid_plan_set_omega, rid_plan_use_srft,
+ * rid_plan_round_omega) and for the mixed-precision modes. */
+RID_API rid_status rid_plan_reseed(rid_plan_t plan, uint64_t seed, uint64_t probe_seed);
+
+/* Move a plan's later work to stream (a cudaStream_t of the plan's device):
+ * the new stream first waits for everything already queued for the plan on
+ * its old stream.  No device work of its own. */
+RID_API rid_status rid_plan_set_stream(rid_plan_t plan, void* stream);
+
 /* Error of the ID from the row probes of the last rid_sketch, without reading
  * A.  E = A - A(:, J) P has E(:, J) = 0 and E(:, perm[k+i]) =
  * A(:, perm[k+i]) - A(:, J) T(:, i), so

@@ -177,6 +177,18 @@ class Plan:
               "rid_plan_set_omega")
         self._keep = omega
 
+    def reseed(self, seed, probe_seed=1):
+        """Redraw Omega (and the row probes) in place for new seeds: the plan
+        then gives the bits of a new plan with these seeds (no allocation)."""
+        check(self._lib.rid_plan_reseed(self._h, int(seed) & (2 ** 64 - 1), int(probe_seed) & (2 ** 64 - 1)),
+              "rid_plan_reseed")
+        self.seed = int(seed)
+
+    def set_stream(self, stream):
+        """Run the plan's later work on `stream` (after its queued work)."""
+        check(self._lib.rid_plan_set_stream(self._h, ctypes.c_void_p(stream.cuda_stream)), "rid_plan_set_stream")
+        self.stream = stream
+
     def use_srft(self, srft_seed):
         """Use the paper's randomization Omega = S F D (subsampled DFT with random phases)."""
         check(self._lib.rid_plan_use_srft(self._h, int(srft_seed) & (2 ** 64 - 1)), "rid_plan_use_srft")

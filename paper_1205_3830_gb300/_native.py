@@ -23,6 +23,8 @@ SIGNATURES = {
     "rid_plan_create_probes": (ctypes.c_int, [ctypes.POINTER(_c_plan), _i64, _i64, _i32, _i32, ctypes.c_int,
                                               ctypes.c_int, _u64, _p, _i32, _u64]),
     "rid_plan_destroy": (ctypes.c_int, [_c_plan]),
+    "rid_plan_reseed": (ctypes.c_int, [_c_plan, _u64, _u64]),
+    "rid_plan_set_stream": (ctypes.c_int, [_c_plan, _p]),
     "rid_plan_footprint": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]),
     "rid_plan_omega": (ctypes.c_int, [_c_plan, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),

@@ -353,6 +353,7 @@ rid_status rid_plan_set_omega(rid_plan_t p, const void* omega, int64_t ldo) {
   cudaError_t e = cudaMemcpy2DAsync(p->omega, p->ldo * sizeof(double2), omega, ldo * sizeof(double2),
                                     p->m * sizeof(double2), p->l, cudaMemcpyDeviceToDevice, p->stream);
   p->omega_bits = 0;                // a caller's Omega is taken as it is
+  p->omega_kind = 1;
   if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
     // the tensor-core paths keep Omega in split form: rebuild it
     rid_tc_plan_free(p);
@@ -367,6 +368,7 @@ rid_status rid_plan_use_srft(rid_plan_t p, uint64_t srft_seed) {
   DeviceGuard g(p->device);
   if (!g.ok) return RID_ECUDA;
   cudaError_t e = rid_launch_srft(p->omega, p->l, p->m, p->ldo, srft_seed, p->stream);
+  p->omega_kind = 2;
   if (e == cudaSuccess && p->omega_bits > 0)
     e = rid_launch_round_rows(p->omega, p->l, p->m, p->ldo, p->omega_bits, p->stream);
   if (e == cudaSuccess && p->mode != RID_FP64_NATIVE) {
@@ -468,6 +470,44 @@ static rid_status set_probes_impl(rid_plan_t p, int32_t nprobe, uint64_t probe_s
 
 rid_status rid_plan_set_probes(rid_plan_t p, int32_t nprobe, uint64_t probe_seed) {
   return set_probes_impl(p, nprobe, probe_seed, true);
+}
+
+rid_status rid_plan_reseed(rid_plan_t p, uint64_t seed, uint64_t probe_seed) {
+  if (!p) return RID_EINVAL;
+  if (p->omega_kind != 0 || p->omega_bits > 0) return RID_EUNSUPPORTED;   // not the plain Gaussian of a seed
+  if (p->mode != RID_FP64_NATIVE && p->mode != RID_FP64_EMULATED) return RID_EUNSUPPORTED;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  // the same draws as rid_plan_create and rid_plan_set_probes, in place
+  cudaError_t e = cudaMemsetAsync(p->status, 0, sizeof(int), p->stream);
+  if (e == cudaSuccess) e = rid_launch_gaussian(p->omega, p->l, p->m, p->ldo, 1, seed, RID_STREAM_OMEGA, p->stream);
+  if (e == cudaSuccess && p->nrow > 0) {
+    e = rid_launch_gaussian(p->omega + (int64_t)p->l * p->ldo, p->nrow, p->m, p->ldo, 1, probe_seed,
+                            RID_STREAM_LPROBES, p->stream);
+    if (e == cudaSuccess) e = rid_launch_row_probe_norms(p);
+  }
+  if (e == cudaSuccess && p->mode == RID_FP64_EMULATED) e = rid_tc_refresh_omega_fp64(p);
+  if (e != cudaSuccess) return from_cuda(e);
+  p->seed = seed;
+  p->x_valid = 0;
+  return RID_OK;
+}
+
+rid_status rid_plan_set_stream(rid_plan_t p, void* stream) {
+  if (!p) return RID_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (s == p->stream) return RID_OK;
+  DeviceGuard g(p->device);
+  if (!g.ok) return RID_ECUDA;
+  // the new stream runs after everything already queued for this plan
+  cudaEvent_t ev;
+  cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev, p->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(s, ev, 0);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return from_cuda(e);
+  p->stream = s;
+  return RID_OK;
 }
 
 rid_status rid_plan_create_probes(rid_plan_t* plan, int64_t m, int64_t n, int32_t k, int32_t l, rid_dtype dtype,

@@ -28,6 +28,7 @@ struct rid_plan_s {
   int64_t ldo;
   int32_t ls;              // rows the sketch computes: l + nrow
   int32_t omega_bits;      // 0, or the bits every row of Omega is rounded to (rid_plan_round_omega)
+  int32_t omega_kind;      // 0: the Gaussian of seed; 1: a caller's (rid_plan_set_omega); 2: the SRFT
   int* status;             // device status word (RID_OK / RID_ERANK)
 
   // sketch (native FP64): split-K partial sums, split_k x ls x n (ld = ls)
@@ -149,6 +150,10 @@ cudaError_t rid_launch_error(const rid_plan_s* p, const void* A, int64_t lda,
 
 // ||g_q||^2 of the row probes (rows l..ls-1 of Omega), once per rid_plan_set_probes.
 cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p);
+
+// Re-cut the FP64-emulated state's digit tiles of Omega after Omega's values
+// changed in place (same shape and row count).
+cudaError_t rid_tc_refresh_omega_fp64(const rid_plan_s* p);
 
 // out[0] = |R(0,0)|, out[1] = max_{c >= k} ||Y(k:l-1, c)|| of a selected Y (device doubles).
 cudaError_t rid_launch_tail_ratio(const rid_plan_s* p, const double2* Y, int64_t ldy, double* out);

@@ -1045,3 +1045,19 @@ int rid_tc_error_word_fp64(const rid_plan_s* p) { return state_error_word(p, (co
 int rid_tc_probe_error_word(const rid_plan_s* p) { return state_error_word(p, (const TcState*)p->tc_probe_state); }
 
 rid_status rid_tc_plan_init_fp64(rid_plan_s* p) { return rid_tc_plan_setup_fp64(p, 0); }
+
+cudaError_t rid_tc_refresh_omega_fp64(const rid_plan_s* p) {
+  const TcState* st = (const TcState*)p->tc_state;
+  if (!st) return cudaErrorNotSupported;
+  // the rows of the state (Omega, then the row probes), cut as at plan time;
+  // the padding rows of the tiles keep the zeros of the setup
+  omega_exp_kernel<<<st->nrows, 256, 0, p->stream>>>(p->omega + (int64_t)st->row0 * p->ldo, p->ldo, p->m, st->om_exp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t blocks = ((int64_t)st->nrows * (st->KP / 2) + 255) / 256;
+  if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
+  omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega + (int64_t)st->row0 * p->ldo, p->ldo, p->m,
+                                                               st->nrows, st->KP, st->tile_w, st->pair, st->om_exp,
+                                                               st->om_slices);
+  return cudaGetLastError();
+}

@@ -15,10 +15,17 @@ results are the same bits).
 Latency is measured from submit() to the moment the result (J, T, the error
 estimate) is available on the host side of the worker.  A request's matrix A
 is on the device when it is submitted (the caller owns it); no host-device
-copy of A is part of the latency.  Every request builds its own plan (the
-test matrix Omega of its seed, its digit tiles and workspace) from the
-library's stream-ordered memory pool; the plan's share of the work is
-reported per request (plan_host_ms, plan_dev_ms beside id_dev_ms).
+copy of A is part of the latency.
+
+Plans are reused: a finished request's plan stays, idle, in a pool keyed by
+its shape (m, n, k, l, dtype, mode, probes), and the next request of that
+shape takes it, moves it to its own stream and redraws its test matrix for
+its own seed in place (rid_plan_reseed); the result is bit for bit that of a
+new plan with that seed.  Idle plans count against the HBM budget and are
+destroyed, least recently used first, when an admission needs their memory.
+The plan's share of the work is reported per request (plan_host_ms,
+plan_dev_ms beside id_dev_ms; reused says whether the plan came from the
+pool).
 """
 from __future__ import annotations
 
@@ -69,10 +76,17 @@ class Request:
         return None if self.t_done is None else self.t_done - self.t_submit
 
 
-class Server:
-    """slots concurrent IDs, admitted by an HBM budget (bytes)."""
+def output_bytes(n, k, l):
+    """Device bytes of one request's outputs Y, perm and T."""
+    return 16 * l * n + 4 * n + 16 * k * max(0, n - k)
 
-    def __init__(self, slots=8, hbm_budget=None, mode="fp64_emulated", device=None, select_ctas=0):
+
+class Server:
+    """slots concurrent IDs, admitted by an HBM budget (bytes); reuse_plans
+    keeps finished requests' plans for later requests of the same shape."""
+
+    def __init__(self, slots=8, hbm_budget=None, mode="fp64_emulated", device=None, select_ctas=0,
+                 reuse_plans=True):
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info(self.device)
@@ -84,6 +98,11 @@ class Server:
         # with a select; a cooperative launch holds every SM it spans for all
         # k steps.  The results are the same either way.
         self.select_ctas = select_ctas
+        # plan reuse (the modes whose test matrix can be redrawn in place)
+        self.reuse = bool(reuse_plans) and mode in ROW_PROBE_MODES
+        self.idle = collections.OrderedDict()     # shape key -> [(plan, bytes)], least recently used first
+        self.idle_bytes = 0
+        self.reused = 0
         self.used = 0
         self.peak_used = 0
         self.running = 0
@@ -125,59 +144,136 @@ class Server:
             self.cv.notify_all()
         for w in self.workers:
             w.join()
+        with self.cv:
+            idle = [p for plans in self.idle.values() for p, _ in plans]
+            self.idle.clear()
+            self.used -= self.idle_bytes
+            self.idle_bytes = 0
+        for p in idle:
+            p.close()
+
+    # -- the pool of idle plans (called with self.cv held) ---------------------------
+    @staticmethod
+    def _key(req, mode):
+        m, n = req.A.shape
+        return (int(m), int(n), req.k, req.l, req.A.dtype, mode, req.nprobe)
+
+    def _evict_for(self, need, keep_key=None):
+        """Take idle plans off the pool, least recently used first (never the
+        plans of keep_key), until `need` more bytes fit in the budget; returns
+        them (destroyed by the caller outside the lock)."""
+        out = []
+        for key in [k for k in self.idle if k != keep_key]:
+            plans = self.idle[key]
+            while plans and self.used + need > self.budget:
+                plan, nbytes = plans.pop(0)
+                self.idle_bytes -= nbytes
+                self.used -= nbytes
+                out.append(plan)
+            if not plans:
+                del self.idle[key]
+            if self.used + need <= self.budget:
+                break
+        return out
+
+    def _checkout(self, key):
+        plans = self.idle.get(key)
+        if not plans:
+            return None
+        plan, nbytes = plans.pop()
+        if not plans:
+            del self.idle[key]
+        self.idle_bytes -= nbytes
+        self.used -= nbytes                  # the request's own bytes already count the plan
+        self.reused += 1
+        return plan
 
     # -- workers -----------------------------------------------------------------------
     def _admit(self):
-        """Pop the head request once it fits (first come, first served)."""
-        with self.cv:
-            while True:
+        """Pop the head request once it fits (first come, first served), with
+        an idle plan of its shape if the pool has one."""
+        while True:
+            victims = []
+            with self.cv:
                 if self.stop and not self.queue:
-                    return None
-                if self.queue and self.used + self.queue[0].bytes <= self.budget:
-                    req = self.queue.popleft()
-                    self.used += req.bytes
-                    self.running += 1
-                    self.peak_used = max(self.peak_used, self.used)
-                    self.peak_running = max(self.peak_running, self.running)
-                    req.t_admit = time.perf_counter()
-                    return req
-                self.cv.wait()
+                    return None, None
+                if self.queue:
+                    head = self.queue[0]
+                    key = self._key(head, self.mode) if self.reuse else None
+                    # an idle plan of its shape passes its bytes on to the request
+                    avail = self.idle[key][-1][1] if key in self.idle else 0
+                    need = head.bytes - avail
+                    if self.used + need > self.budget:
+                        victims = self._evict_for(need, keep_key=key)
+                    if not victims and self.used + need <= self.budget:
+                        req = self.queue.popleft()
+                        plan = self._checkout(key) if avail else None
+                        self.used += req.bytes
+                        self.running += 1
+                        self.peak_used = max(self.peak_used, self.used)
+                        self.peak_running = max(self.peak_running, self.running)
+                        req.t_admit = time.perf_counter()
+                        return req, plan
+                if not victims:
+                    self.cv.wait()
+            for p in victims:                     # outside the lock: destroying a plan waits for its stream
+                p.close()
 
     def _worker(self, slot):
         torch.cuda.set_device(self.device)
         stream = torch.cuda.Stream(self.device)
         while True:
-            req = self._admit()
+            req, plan = self._admit()
             if req is None:
                 return
+            kept = None
             try:
                 with torch.cuda.stream(stream):
                     req.result = run_one(req.A, req.k, req.l, req.seed, req.nprobe, req.probe_seed, self.mode, stream,
-                                         self.select_ctas)
+                                         self.select_ctas, plan=plan, keep=self.reuse)
+                kept = req.result.pop("plan", None)
             except Exception as exc:        # reported with the request, the server keeps running
                 req.error = exc
+                if plan is not None:
+                    plan.close()
             req.t_done = time.perf_counter()
             with self.cv:
                 self.used -= req.bytes
+                if kept is not None:        # back to the pool: its bytes stay counted
+                    m, n = req.A.shape
+                    nbytes = max(0, req.bytes - output_bytes(n, req.k, req.l))
+                    self.idle.setdefault(self._key(req, self.mode), []).append((kept, nbytes))
+                    self.idle.move_to_end(self._key(req, self.mode))
+                    self.idle_bytes += nbytes
+                    self.used += nbytes
                 self.running -= 1
                 self.done.append(req)
                 self.cv.notify_all()
 
 
-def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None, select_ctas=None):
+def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=None, select_ctas=None, plan=None,
+            keep=False):
     """One whole ID on `stream`; returns host copies of J, T and the estimate.
     In the FP64 modes the error comes from row probes that the sketch
     multiplies in its one pass over A; the mixed mode takes column probes.
     select_ctas (None: the plan's default) sets the select's launch shape;
-    the results do not depend on it."""
+    the results do not depend on it.  plan: an idle plan of this shape to
+    reuse (moved to `stream` and reseeded); keep: return the plan in the
+    result ("plan") instead of destroying it."""
     m, n = A.shape
     stream = stream or torch.cuda.current_stream(A.device)
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
     t0 = time.perf_counter()
     ev[0].record(stream)
     rows = mode in ROW_PROBE_MODES
-    with Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream, nprobe=nprobe if rows else 0,
-              probe_seed=probe_seed) as plan:
+    reused = plan is not None
+    if reused:
+        plan.set_stream(stream)
+        plan.reseed(seed, probe_seed)
+    else:
+        plan = Plan(m, n, k, l, seed=seed, dtype=A.dtype, mode=mode, stream=stream, nprobe=nprobe if rows else 0,
+                    probe_seed=probe_seed)
+    try:
         if select_ctas is not None:
             plan.set_select_grid(select_ctas)
         with torch.cuda.stream(stream):
@@ -195,8 +291,16 @@ def run_one(A, k, l, seed, nprobe=8, probe_seed=1, mode="fp64_emulated", stream=
             est, upper = plan.error(A, perm, T, nprobe, probe_seed)
         ev[2].record(stream)
         plan.sync_status()
-        return {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper, "plan_host_ms": plan_host_ms,
-                "plan_dev_ms": ev[0].elapsed_time(ev[1]), "id_dev_ms": ev[1].elapsed_time(ev[2])}
+        out = {"perm": perm.cpu(), "T": T.cpu(), "est": est, "upper": upper, "plan_host_ms": plan_host_ms,
+               "plan_dev_ms": ev[0].elapsed_time(ev[1]), "id_dev_ms": ev[1].elapsed_time(ev[2]), "reused": reused}
+    except BaseException:
+        plan.close()                         # a plan that failed does not go back to the pool
+        raise
+    if keep:
+        out["plan"] = plan
+    else:
+        plan.close()
+    return out
 
 
 def latency_stats(reqs):
@@ -213,4 +317,5 @@ def latency_stats(reqs):
         for key in ("plan_host_ms", "plan_dev_ms", "id_dev_ms"):
             vals = sorted(p[key] for p in parts)
             out[key.replace("_ms", "_p50_ms")] = vals[len(vals) // 2]
+        out["plans_reused"] = sum(1 for p in parts if p.get("reused"))
     return out

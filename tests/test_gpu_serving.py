@@ -80,3 +80,54 @@ def test_admission_waits_for_memory(serve):
     assert srv.peak_running == 1 and srv.peak_used <= biggest
     lat = serve.latency_stats(done)
     assert lat["p99_ms"] >= lat["p50_ms"] > 0
+
+
+def test_reused_plans_give_the_bits_of_new_plans(serve):
+    """Requests of repeated shapes take finished requests' plans from the pool
+    (rid_plan_reseed, rid_plan_set_stream); every result is still bit for bit
+    the solo result of a new plan with its own seed."""
+    shapes = [(900, 700, 12), (600, 1100, 20)]
+    reqs = []
+    for i in range(12):
+        m, n, k = shapes[i % 2]
+        reqs.append((i, synth.lowrank_plus_noise(m, n, k, 1e-10, seed=900 + i), k, k + 10, 3000 + i))
+    dev = {i: to_dev_colmajor(A) for (i, A, k, l, s) in reqs}
+    solo = {i: serve.run_one(dev[i], k, l, s) for (i, A, k, l, s) in reqs}
+    torch.cuda.synchronize()
+    srv = serve.Server(slots=2)
+    try:
+        handles = [srv.submit(i, dev[i], k, l, s) for (i, A, k, l, s) in reqs]
+        done = srv.drain(timeout=300)
+    finally:
+        srv.close()
+    assert len(done) == len(reqs) and srv.reused >= len(reqs) - 4     # at most one new plan per slot and shape
+    assert srv.used == 0 and not srv.idle                                # close() released the pool
+    for h in handles:
+        assert h.error is None, h.error
+        a, b = h.result, solo[h.rid]
+        assert torch.equal(a["perm"], b["perm"]) and torch.equal(a["T"], b["T"])
+        assert a["est"] == b["est"] and a["upper"] == b["upper"]
+
+
+def test_reseeded_plan_matches_new_plan(serve):
+    import paper_1205_3830_gb300 as rid
+    A = synth.lowrank_plus_noise(1500, 2300, 24, 1e-10, seed=77)
+    Ad = to_dev_colmajor(A)
+    for mode in ("fp64_emulated", "fp64"):
+        outs = []
+        with rid.Plan(1500, 2300, 24, 34, seed=1, mode=mode, nprobe=8, probe_seed=2) as plan:
+            plan.reseed(5, 6)
+            side = torch.cuda.Stream()
+            plan.set_stream(side)
+            with torch.cuda.stream(side):
+                Y = plan.sketch(Ad)
+                perm = plan.select(Y)
+                T = plan.solve(Y)
+                outs.append((perm.cpu(), T.cpu(), plan.error_sketched(perm, T)))
+        with rid.Plan(1500, 2300, 24, 34, seed=5, mode=mode, nprobe=8, probe_seed=6) as plan:
+            Y = plan.sketch(Ad)
+            perm = plan.select(Y)
+            T = plan.solve(Y)
+            outs.append((perm.cpu(), T.cpu(), plan.error_sketched(perm, T)))
+        (pa, Ta, ea), (pb, Tb, eb) = outs
+        assert torch.equal(pa, pb) and torch.equal(Ta, Tb) and ea == eb, mode
