@@ -40,14 +40,24 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # 4 x (4.896 + 0.127) GB, scaled by the panel's 4x rows; reported only for the
 # source it was measured on
 TC_TRAFFIC = {"bytes_per_launch": 20.09e9,
-              "source_sha1": "578149bc5400b51fcb31d8cf494e45bf5e468de8"}
+              "source_sha1": "1ebb14eb1645e23229ef3f9ae32ebcdebe8f0026"}
+
+
+TC_SOURCES = ("rid_sketch_tc.cu", "rid_tc_digits.cuh", "rid_tc.cuh")     # the product kernel's source
+
+
+def tc_source_sha1():
+    import hashlib
+    h = hashlib.sha1()
+    for name in TC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1205_3830_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def tc_source_unchanged():
-    import hashlib
     try:
-        with open(os.path.join(ROOT, "paper_1205_3830_gb300", "csrc", "rid_sketch_tc.cu"), "rb") as f:
-            return TC_TRAFFIC["source_sha1"] == hashlib.sha1(f.read()).hexdigest()
+        return TC_TRAFFIC["source_sha1"] == tc_source_sha1()
     except OSError:
         return False
 
@@ -733,10 +743,11 @@ def device_lowrank(m, n, rank, eps, gen, device):
 
 def run_batched(args, world, rank, local):
     """4096 independent complex128 IDs (m, n ~ U[64, 1024], k ~ U[4, 64],
-    l = k + 8, A = X Y + 1e-10 N) per step.  Timed: the tensor-core batch (one
-    FP64-emulated plan per problem, all sketches in one CUDA graph, then one
-    persistent launch of select, solve and the row-probe error); beside it the
-    FP64 persistent batch (one launch, CUDA graph) and the plan path."""
+    l = k + 8, A = X Y + 1e-10 N) per step.  Timed: the tensor-core batch (all
+    sketches in one persistent launch, then one persistent launch of select,
+    solve and the row-probe error, replayed as one CUDA graph, tile shapes
+    from the autotuner); beside it the FP64 persistent batch (one launch, CUDA
+    graph) and the plan path."""
     import torch
     import synth
     import paper_1205_3830_gb300 as rid
@@ -750,7 +761,18 @@ def run_batched(args, world, rank, local):
     problems = [(device_lowrank(m, n, k, 1e-10, gen, dev), k, l, 1000 + i) for i, (m, n, k, l) in enumerate(shapes)]
     r = args.nprobe
     stream = torch.cuda.current_stream(dev)
-    tcb = rid.BatchTC(problems, nprobe=r, probe_seed=1)
+    # tile shapes per size class from the autotuner (its cache file, tuned
+    # here for classes it does not hold yet), outside the timed region
+    tuning = rid.TcTuning(os.path.join(ROOT, "paper_1205_3830_gb300", "_build", "tc_tiles.json"))
+    t_tune = time.perf_counter()
+    tuned = tuning.tune(problems, nprobe=r, probe_seed=1, force=False) if args.tune else {}
+    t_tune = time.perf_counter() - t_tune
+    tcb = rid.BatchTC(problems, nprobe=r, probe_seed=1, tuning=tuning if args.tune else None)
+    tc_info = tcb.info()
+    choices = {}
+    for t, s in zip(tcb.tile_n, tcb.ksplit):
+        key = f"tile_n={t or 128},ksplit={s or 1}"
+        choices[key] = choices.get(key, 0) + 1
     for _ in range(args.warmup):
         tcb.run()
     barrier(world)
@@ -818,14 +840,20 @@ def run_batched(args, world, rank, local):
         "config": {"workload": f"batched: {len(shapes)} complex128 IDs, m, n ~ U[64, 1024], k ~ U[4, 64], l = k + 8, "
                                f"A = X Y + 1e-10 N ({a_bytes / 2**30:.1f} GiB in all)",
                    "count": len(shapes), "nprobe": r, "estimator": "rows",
-                   "path": "tensor-core batch: FP64-emulated plan per problem, sketches in one CUDA graph "
-                           "(64 branches), one persistent launch of select / solve / error",
+                   "path": "tensor-core batch: all sketches in one persistent cooperative launch (waves of "
+                           "digit cutting, grid barrier, longest-first work lists of tcgen05 products), then one "
+                           "persistent launch of select / solve / error; both in one CUDA graph",
                    "cuda_graph": True, "l2": "inputs larger than L2 (%.1f GiB)" % (a_bytes / 2**30)},
         "ids_per_s": world * len(shapes) / (ms / 1e3),
         "phase_ms": {"sketches": sketch_ms, "select_solve_error": post_ms},
+        "workspace": {"device_bytes": tc_info["bytes"], "gib": tc_info["bytes"] / 2**30, "waves": tc_info["waves"],
+                      "work_items": tc_info["items"], "ctas": tc_info["ctas"],
+                      "holds": "Omega and probe rows of every problem, X, two digit buffers of at most 2 GiB"},
+        "tuning": {"autotuned": bool(args.tune), "classes_timed_now": len(tuned), "tune_s": t_tune,
+                   "problems_per_choice": choices},
         "roofline": dominant,
         "roofline_other_phase": other,
-        "gpu_launches": args.steps * (3 * len(shapes) + 1),
+        "gpu_launches": args.steps * 2,
         "ranks_ok": ok,
         "vs_fp64_batch": {"ids_per_s": world * len(shapes) / (fp64_ms / 1e3), "ms_per_step": fp64_ms, "tile": tile,
                           "path": "one persistent FP64 launch (CTA per problem), CUDA graph"},
@@ -941,6 +969,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--count", type=int, default=4096, help="problems per batch (--config batched)")
+    ap.add_argument("--tune", type=int, default=1,
+                    help="--config batched: tile shapes per size class from the autotuner (1) or the defaults (0)")
     ap.add_argument("--requests", type=int, default=1000, help="requests per rate (--config serving)")
     ap.add_argument("--rates", default="40,160,320,640,1280,2560",
                     help="offered request rates per second (--config serving)")

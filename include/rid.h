@@ -377,28 +377,53 @@ RID_API rid_status rid_batch_prepare(const rid_batch_item* items, int32_t count,
 RID_API rid_status rid_batch_launch(int32_t count, int32_t nprobe, uint64_t probe_seed, int32_t tile,
                                     double* err_out, int32_t* status_out, void* workspace, void* stream);
 
-/* Batches on the tensor cores.  rid_batch_tc_create gives every problem its
- * own RID_FP64_EMULATED plan with nprobe row probes (probe_seed), then records,
- * once, a CUDA graph of every plan's sketch (Y = Omega A and X = G A, the
- * problems spread over 64 concurrent branch streams, largest first) followed
- * by one persistent launch that runs the pivoted QR, the solve and the
- * row-probe error estimate (as rid_error_sketched) of every problem, writing
- * err_out (device, double[2 count]) and status_out (device, int32[count]) as
- * rid_batch_run does.  Items and their limits as for rid_batch_run, plus
- * l + nprobe <= 512; A, Y and T 16-byte aligned.  The items' pointers and
- * err_out / status_out must stay valid for the handle's life.  Plan memory is
- * about the sum of rid_plan_footprint over the problems.  Creating
- * synchronizes `stream`; rid_batch_tc_run launches the graph on `stream`
- * (asynchronous).  The results equal those of the problems' own plans with
- * rid_error_sketched, up to the rounding order of the QR. */
+/* Batches on the tensor cores (Sec. 2 sketch, Sec. 3.3 row-probe error, for
+ * many problems at once).  rid_batch_tc_create draws every problem's Omega
+ * (from its seed, exactly as rid_plan_create does) and nprobe row probes
+ * (probe_seed, as rid_plan_set_probes), then records, once, a CUDA graph of
+ * two persistent launches:
+ *   1. one cooperative tensor-core launch computes every problem's sketch
+ *      Y = Omega A and X = G A with the FP64-emulated product (the problems,
+ *      largest first, in waves whose digit tiles fit a workspace buffer; per
+ *      wave all CTAs cut the digits, meet at a grid barrier, then multiply
+ *      their longest-first work lists of (problem, N-tile, column block,
+ *      K-split) items);
+ *   2. one launch runs the pivoted QR, the solve and the row-probe error (as
+ *      rid_error_sketched) of every problem, writing err_out (device,
+ *      double[2 count]) and status_out (device, int32[count]) as
+ *      rid_batch_run does; a problem whose sketch launch gave up a bounded
+ *      wait gets RID_ETIMEOUT and est = upper = -1.
+ * Items and their limits as for rid_batch_run; A, Y and T 16-byte aligned.
+ * The items' pointers and err_out / status_out must stay valid for the
+ * handle's life.  Device memory: each problem's Omega and probe rows (16 (l +
+ * nprobe) m bytes), X, and two digit buffers of at most 2 GiB each (or of
+ * the largest problem's digit tiles, about 14 (2 (l + nprobe) + n) 2m bytes,
+ * if larger); rid_batch_tc_info reports the total.  Creating synchronizes `stream`; rid_batch_tc_run
+ * launches the graph on `stream` (asynchronous).  With one K-split (the
+ * default) a problem's Y has the bits of its own FP64-emulated plan's sketch,
+ * so J and T equal that plan's up to the rounding order of the QR. */
 typedef struct rid_batch_plan_s* rid_batch_plan_t;
 RID_API rid_status rid_batch_tc_create(rid_batch_plan_t* plan, const rid_batch_item* items, int32_t count,
                                        int32_t nprobe, uint64_t probe_seed, double* err_out, int32_t* status_out,
                                        void* stream);
+/* The same with the tile shapes chosen per problem (an autotuner's choice):
+ * tile_n[i] (HOST, may be NULL) the widest N-tile of problem i in rows of the
+ * real test matrix (16 .. 128, a multiple of 16; 0: 128), ksplit[i] (HOST,
+ * may be NULL) its K-splits (0 or 1: none; larger values are capped at the
+ * number of 256-real chunks; partial sums are then added in split order, so
+ * Y differs from a plan's in the last bits), wave_bytes the digit buffer
+ * size (0: 2 GiB).  RID_EINVAL for a tile_n outside those values. */
+RID_API rid_status rid_batch_tc_create_tuned(rid_batch_plan_t* plan, const rid_batch_item* items, int32_t count,
+                                             int32_t nprobe, uint64_t probe_seed, double* err_out,
+                                             int32_t* status_out, const int32_t* tile_n, const int32_t* ksplit,
+                                             size_t wave_bytes, void* stream);
 RID_API rid_status rid_batch_tc_run(rid_batch_plan_t plan, void* stream);
-/* Milliseconds of the last run: out[0] the sketches (all branches), out[1]
- * the finishing launch (HOST double[2]); waits for that run to end. */
+/* Milliseconds of the last run: out[0] the sketch launch, out[1] the
+ * finishing launch (HOST double[2]); waits for that run to end. */
 RID_API rid_status rid_batch_tc_times(rid_batch_plan_t plan, double out[2]);
+/* out (HOST double[4]): device bytes the handle holds, waves, work items of
+ * the sketch launch, its CTAs. */
+RID_API rid_status rid_batch_tc_info(rid_batch_plan_t plan, double out[4]);
 RID_API rid_status rid_batch_tc_destroy(rid_batch_plan_t plan);
 
 /* Static, human-readable name of a status code. */

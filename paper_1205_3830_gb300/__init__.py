@@ -418,21 +418,30 @@ class Batch:
 
 
 class BatchTC:
-    """Many complex128 IDs on the tensor cores: one FP64-emulated plan per
-    problem with nprobe row probes, every sketch captured once in a CUDA graph
-    (concurrent branches), then one persistent launch of select, solve and the
-    row-probe error for all problems (rid_batch_tc_*).
+    """Many complex128 IDs on the tensor cores (rid_batch_tc_*): every
+    problem's sketch Y = Omega A and row-probe products X = G A in one
+    persistent tensor-core launch, then one persistent launch of select, solve
+    and the row-probe error for all problems, replayed as one CUDA graph.
 
-    problems: list of (A, k, l, seed) as for Batch.  run() replays the graph on
-    the current stream; results() as for Batch.
+    problems: list of (A, k, l, seed) as for Batch.  tile_n / ksplit: per
+    problem (lists, or one value for all) the widest N-tile in rows of the real
+    test matrix and the K-splits; tuning: a TcTuning whose per-size-class
+    choice fills in what tile_n / ksplit leave open.  wave_bytes: the size of
+    each of the two digit buffers (0: 2 GiB).  run() replays the graph on the
+    current stream; results() as for Batch; info() the device bytes, waves,
+    work items and CTAs of the sketch launch.
     """
 
-    def __init__(self, problems, nprobe=8, probe_seed=1, device=None):
+    def __init__(self, problems, nprobe=8, probe_seed=1, device=None, tile_n=None, ksplit=None, wave_bytes=0,
+                 tuning=None):
         self._lib = _native.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
         self.nprobe, self.probe_seed = int(nprobe), int(probe_seed)
         self.Y, self.perm, self.T, self.A = [], [], [], []
-        items = (_native.BatchItem * len(problems))()
+        count = len(problems)
+        items = (_native.BatchItem * count)()
+        tn = (ctypes.c_int32 * max(1, count))()
+        ksp = (ctypes.c_int32 * max(1, count))()
         for i, (A, k, l, seed) in enumerate(problems):
             _check_matrix(A, f"problem {i}: A", 1, 1, torch.complex128)
             m, n = A.shape
@@ -447,17 +456,29 @@ class BatchTC:
             it.perm = perm.data_ptr()
             it.T, it.ldt = (T.data_ptr() if T.numel() else 0), max(_ld(T), int(k))
             it.seed = int(seed) & (2 ** 64 - 1)
+            choice = tuning.choice(m, n, int(l) + self.nprobe) if tuning is not None else (0, 0)
+            tn[i] = int(_per_problem(tile_n, i, choice[0]))
+            ksp[i] = int(_per_problem(ksplit, i, choice[1]))
         self.items = items
-        self.count = len(problems)
+        self.count = count
+        self.tile_n, self.ksplit = list(tn)[:count], list(ksp)[:count]
         self.err = torch.empty(2 * max(1, self.count), dtype=torch.float64, device=self.device)
         self.status = torch.empty(max(1, self.count), dtype=torch.int32, device=self.device)
         self._h = ctypes.c_void_p()
         stream = torch.cuda.current_stream(self.device)
-        check(self._lib.rid_batch_tc_create(ctypes.byref(self._h), ctypes.byref(self.items), self.count,
-                                            self.nprobe, self.probe_seed & (2 ** 64 - 1),
-                                            ctypes.c_void_p(self.err.data_ptr()),
-                                            ctypes.c_void_p(self.status.data_ptr()),
-                                            ctypes.c_void_p(stream.cuda_stream)), "rid_batch_tc_create")
+        check(self._lib.rid_batch_tc_create_tuned(ctypes.byref(self._h), ctypes.byref(self.items), self.count,
+                                                  self.nprobe, self.probe_seed & (2 ** 64 - 1),
+                                                  ctypes.c_void_p(self.err.data_ptr()),
+                                                  ctypes.c_void_p(self.status.data_ptr()),
+                                                  ctypes.cast(tn, ctypes.c_void_p), ctypes.cast(ksp, ctypes.c_void_p),
+                                                  int(wave_bytes), ctypes.c_void_p(stream.cuda_stream)),
+              "rid_batch_tc_create_tuned")
+
+    def info(self):
+        """dict: device bytes the handle holds, waves, work items and CTAs of the sketch launch."""
+        out = (ctypes.c_double * 4)()
+        check(self._lib.rid_batch_tc_info(self._h, out), "rid_batch_tc_info")
+        return {"bytes": int(out[0]), "waves": int(out[1]), "items": int(out[2]), "ctas": int(out[3])}
 
     def run(self, stream=None):
         stream = stream or torch.cuda.current_stream(self.device)
@@ -482,6 +503,108 @@ class BatchTC:
             self.close()
         except Exception:
             pass
+
+
+def _per_problem(v, i, default):
+    if v is None:
+        return default
+    if isinstance(v, (list, tuple)):
+        return v[i] if v[i] is not None else default
+    return v
+
+
+class TcTuning:
+    """Tile shapes of the tensor-core batch per size class, chosen by timing.
+
+    A size class is (m class, n class, rows class): the power of two at or
+    above m (at least 256), the column-block count class of n (1, 2, 4 or 8+
+    blocks of 128) and the N-tile count the default 128-row tiles give for
+    2 (l + nprobe) rows.  For each class the candidates are the widest N-tile
+    (128, 96 or 64 rows) and the K-splits (1, 2, 4; only where the problem has
+    at least twice as many 256-real chunks), timed on the sketch launch of a
+    batch of that class's problems; the fastest is kept.  Choices are cached
+    per device name in a JSON file when `path` is given (read at creation,
+    written after tuning).  Results do not depend on the N-tile; a K-split
+    changes a problem's Y in the last bits only (partial sums in split order).
+    """
+
+    TILES = (128, 96, 64)
+    SPLITS = (1, 2, 4)
+
+    def __init__(self, path=None):
+        import json
+        import os
+        self.path = path
+        self.device = torch.cuda.get_device_name() if torch.cuda.is_available() else "cpu"
+        self.table = {}
+        if path and os.path.exists(path):
+            with open(path) as f:
+                self.table = {tuple(json.loads(k)): tuple(v) for k, v in json.load(f).get(self.device, {}).items()}
+
+    @staticmethod
+    def size_class(m, n, rows):
+        mc = 256
+        while mc < m:
+            mc *= 2
+        blocks = (n + 127) // 128
+        nc = 1 if blocks <= 1 else 2 if blocks <= 2 else 4 if blocks <= 4 else 8
+        return (mc, nc, (2 * rows + 127) // 128)
+
+    def choice(self, m, n, rows):
+        """(tile_n, ksplit) for a problem; (0, 0), the defaults, for an untuned class."""
+        return self.table.get(self.size_class(m, n, rows), (0, 0))
+
+    @classmethod
+    def candidates(cls, cls_key):
+        mc, _, _ = cls_key
+        chunks = (2 * mc + 255) // 256
+        return [(t, s) for t in cls.TILES for s in cls.SPLITS if s == 1 or chunks >= 2 * s]
+
+    def tune(self, problems, nprobe=8, probe_seed=1, per_class=256, reps=3, force=True):
+        """Time every candidate on up to per_class problems of each class present
+        in `problems` ((A, k, l, seed) tuples) and keep the fastest; returns
+        {class: (tile_n, ksplit, ms)} for the classes timed.  force=False skips
+        the classes the table (or its cache file) already holds."""
+        groups = {}
+        for p in problems:
+            A, k, l, seed = p
+            key = self.size_class(int(A.shape[0]), int(A.shape[1]), int(l) + int(nprobe))
+            groups.setdefault(key, []).append(p)
+        report = {}
+        for key, probs in sorted(groups.items()):
+            if not force and key in self.table:
+                continue
+            sample = probs[:per_class]
+            best = None
+            for t, s in self.candidates(key):
+                b = BatchTC(sample, nprobe, probe_seed, tile_n=t, ksplit=s)
+                b.run()
+                ms = []
+                for _ in range(reps):
+                    b.run()
+                    ms.append(b.times()[0])
+                b.close()
+                cand = (t, s, min(ms))
+                if best is None or cand[2] < best[2]:
+                    best = cand
+            self.table[key] = (best[0], best[1])
+            report[key] = best
+        self.save()
+        return report
+
+    def save(self):
+        import json
+        import os
+        if not self.path:
+            return
+        data = {}
+        if os.path.exists(self.path):
+            with open(self.path) as f:
+                data = json.load(f)
+        data[self.device] = {json.dumps(list(k)): list(v) for k, v in sorted(self.table.items())}
+        os.makedirs(os.path.dirname(os.path.abspath(self.path)), exist_ok=True)
+        with open(self.path, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
 
 
 def selftest_timeouts(stream=None):

@@ -50,7 +50,10 @@ SIGNATURES = {
     "rid_batch_launch": (ctypes.c_int, [_i32, _i32, _u64, _i32, _p, _p, _p, _p]),
     "rid_batch_tc_create": (ctypes.c_int, [ctypes.POINTER(_p), ctypes.c_void_p, _i32, _i32, _u64, _p, _p, _p]),
     "rid_batch_tc_run": (ctypes.c_int, [_p, _p]),
+    "rid_batch_tc_create_tuned": (ctypes.c_int, [ctypes.POINTER(_p), ctypes.c_void_p, _i32, _i32, _u64, _p, _p, _p,
+                                                  _p, ctypes.c_size_t, _p]),
     "rid_batch_tc_times": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double)]),
+    "rid_batch_tc_info": (ctypes.c_int, [_p, ctypes.POINTER(ctypes.c_double)]),
     "rid_batch_tc_destroy": (ctypes.c_int, [_p]),
     "rid_select_noalloc": (ctypes.c_int, [_p, _i64, _i32, _i64, _i32, _p, _p, _p]),
     "rid_selftest_timeouts": (ctypes.c_int, [_p, _p]),

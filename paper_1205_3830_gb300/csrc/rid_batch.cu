@@ -11,10 +11,10 @@
 //   select   k Householder steps with column pivoting on Y (Sec. 2)
 //   solve    R1 T = R2 by back substitution (Sec. 2)
 //   error    probe estimate of ||A - A(:, J) P||_2 (Sec. 3.3)
-// The tensor-core batch (rid_batch_tc_*, at the end of this file) gives each
-// problem an FP64-emulated plan, records all their sketches in one CUDA graph
-// and finishes every problem (select, solve, row-probe error) in one
-// persistent launch of the same per-CTA QR and solve.
+// The tensor-core batch (rid_batch_tc_*, at the end of this file) sketches
+// every problem in one persistent tensor-core launch (rid_batch_tc.cu) and
+// finishes every problem (select, solve, row-probe error) in one persistent
+// launch of the same per-CTA QR and solve.
 //
 // All arithmetic is FP64; sums run in a fixed order, so a problem's result
 // does not depend on which CTA ran it or what ran beside it.
@@ -432,8 +432,8 @@ __global__ void __launch_bounds__(BT_THREADS) batch_kernel(BatchArgs a) {
 }
 
 // ---- the tensor-core batch: select, solve and the row-probe error after the sketches ----
-// Each problem's Y and X = G A come from its own FP64-emulated plan (captured
-// in one CUDA graph); this persistent kernel finishes every problem.
+// Each problem's Y and X = G A come from the persistent batched sketch
+// (rid_batch_tc.cu); this persistent kernel finishes every problem.
 struct PostItemDev {
   const double2* X;            // r x n, column-major, ld r: the row probes' products
   const double* g_norm2;       // r: ||g_q||^2
@@ -448,6 +448,7 @@ struct PostArgs {
   int r;
   double* err_out;
   int32_t* status_out;
+  const int* sketch_err;       // non-zero: a wait of the sketch launch gave up
 };
 
 // (g_q E)(perm[k+i]) = X(q, perm[k+i]) - sum_a X(q, perm[a]) T(a, i): one warp
@@ -532,7 +533,7 @@ __global__ void __launch_bounds__(BT_THREADS, 4) batch_post_kernel(PostArgs a) {
     const BatchItemDev it = a.items[pid];
     double* nu = (double*)smem;                                   // n doubles
     double2* v = (double2*)(nu + BT_MAX_N);                        // l entries
-    const int st = batch_select(it, tau, nu, red, v);
+    const int st = *a.sketch_err ? (int)RID_ETIMEOUT : batch_select(it, tau, nu, red, v);
     if (st != RID_OK) {
       if (threadIdx.x == 0) {
         a.status_out[pid] = st;
@@ -722,24 +723,22 @@ rid_status rid_batch_run(const rid_batch_item* items, int32_t count, int32_t npr
 }
 
 // ---------------------------------------------------------------------------
-// The tensor-core batch: one FP64-emulated plan per problem, every plan's
-// sketch (Y and the row probes' X) captured once in a CUDA graph fanned out
-// over concurrent branch streams, then one persistent launch of select,
-// solve and the row-probe error for all problems.
+// The tensor-core batch: every problem's sketch (Y and the row probes' X) in
+// one persistent cooperative launch (rid_batch_tc.cu), then one persistent
+// launch of select, solve and the row-probe error for all problems, both
+// recorded once in a CUDA graph.
 // ---------------------------------------------------------------------------
 struct rid_batch_plan_s {
   int device;
   int32_t count;
   int nprobe;
-  rid_plan_t* plans;
+  rid_btc_s* sketch;
   cudaStream_t home;
-  cudaStream_t* branches;
-  int nbranch;
-  cudaEvent_t* events;       // fork, then one join per branch
   cudaEvent_t times[3];      // start, before the finishing launch, end (event-record nodes of the graph)
   cudaGraph_t graph;
   cudaGraphExec_t exec;
   char* dev;                 // items, post items, order, queue counter
+  size_t dev_bytes;
 };
 
 static void batch_plan_release(rid_batch_plan_s* bp) {
@@ -747,30 +746,17 @@ static void batch_plan_release(rid_batch_plan_s* bp) {
   if (bp->home) cudaStreamSynchronize(bp->home);
   if (bp->exec) cudaGraphExecDestroy(bp->exec);
   if (bp->graph) cudaGraphDestroy(bp->graph);
-  if (bp->plans)
-    for (int32_t i = 0; i < bp->count; ++i)
-      if (bp->plans[i]) {
-        bp->plans[i]->stream = bp->home;      // every plan's memory is released in its home stream's order
-        rid_plan_destroy(bp->plans[i]);
-      }
+  if (bp->sketch) rid_btc_destroy(bp->sketch, bp->home);
   if (bp->dev) rid_dev_free(bp->dev, bp->home);
   if (bp->home) cudaStreamSynchronize(bp->home);
-  if (bp->events)
-    for (int i = 0; i < bp->nbranch + 1; ++i)
-      if (bp->events[i]) cudaEventDestroy(bp->events[i]);
   for (int i = 0; i < 3; ++i)
     if (bp->times[i]) cudaEventDestroy(bp->times[i]);
-  if (bp->branches)
-    for (int i = 0; i < bp->nbranch; ++i)
-      if (bp->branches[i]) cudaStreamDestroy(bp->branches[i]);
-  free(bp->plans);
-  free(bp->events);
-  free(bp->branches);
   free(bp);
 }
 
-rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* items, int32_t count, int32_t nprobe,
-                               uint64_t probe_seed, double* err_out, int32_t* status_out, void* stream) {
+rid_status rid_batch_tc_create_tuned(rid_batch_plan_t* out, const rid_batch_item* items, int32_t count,
+                                     int32_t nprobe, uint64_t probe_seed, double* err_out, int32_t* status_out,
+                                     const int32_t* tile_n, const int32_t* ksplit, size_t wave_bytes, void* stream) {
   if (!out) return RID_EINVAL;
   *out = nullptr;
   if (count < 1 || !items || !err_out || !status_out) return RID_EINVAL;
@@ -780,8 +766,10 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
     if (x.m < 1 || x.n < 1 || x.k < 1 || x.l < x.k || x.k > x.m || x.k > x.n || x.lda < x.m || x.ldy < x.l ||
         x.ldt < x.k || !x.A || !x.Y || !x.perm || (x.n > x.k && !x.T))
       return RID_EINVAL;
-    if (x.l > BT_MAX_L || x.k > BT_MAX_K || x.n > BT_MAX_N || x.l + nprobe > 512) return RID_EUNSUPPORTED;
+    if (x.l > BT_MAX_L || x.k > BT_MAX_K || x.n > BT_MAX_N) return RID_EUNSUPPORTED;
     if (((uintptr_t)x.A & 15u) || ((uintptr_t)x.Y & 15u) || (x.T && ((uintptr_t)x.T & 15u))) return RID_EINVAL;
+    if (tile_n && tile_n[i] != 0 && (tile_n[i] < 16 || tile_n[i] > 128 || tile_n[i] % 16)) return RID_EINVAL;
+    if (ksplit && ksplit[i] < 0) return RID_EINVAL;
   }
   rid_batch_plan_s* bp = (rid_batch_plan_s*)calloc(1, sizeof(rid_batch_plan_s));
   if (!bp) return RID_ENOMEM;
@@ -789,19 +777,19 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
   bp->nprobe = nprobe;
   bp->home = (cudaStream_t)stream;
   cudaGetDevice(&bp->device);
-  bp->plans = (rid_plan_t*)calloc((size_t)count, sizeof(rid_plan_t));
-  if (!bp->plans) {
-    free(bp);
-    return RID_ENOMEM;
-  }
   rid_status st = RID_OK;
-  // one FP64-emulated plan per problem, with its row probes
-  for (int32_t i = 0; i < count && st == RID_OK; ++i) {
-    const rid_batch_item& x = items[i];
-    st = rid_plan_create(&bp->plans[i], x.m, x.n, x.k, x.l, RID_C128, RID_FP64_EMULATED, x.seed, stream);
-    if (st == RID_OK) st = rid_plan_set_probes(bp->plans[i], nprobe, probe_seed);
+  {
+    rid_btc_problem* probs = (rid_btc_problem*)malloc(sizeof(rid_btc_problem) * (size_t)count);
+    if (!probs) st = RID_ENOMEM;
+    for (int32_t i = 0; st == RID_OK && i < count; ++i) {
+      const rid_batch_item& x = items[i];
+      probs[i] = rid_btc_problem{(const double2*)x.A, x.lda, x.m, x.n, (double2*)x.Y, x.ldy, x.l, x.seed,
+                                 tile_n ? tile_n[i] : 0, ksplit ? ksplit[i] : 0};
+    }
+    if (st == RID_OK) st = rid_btc_create(&bp->sketch, probs, count, nprobe, probe_seed, wave_bytes, bp->home);
+    free(probs);
   }
-  // the queue order (largest first) and the device descriptors
+  // the finishing launch's queue order (largest first) and descriptors
   int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
   double* cost = (double*)malloc(sizeof(double) * (size_t)count);
   int32_t* tmp = (int32_t*)malloc(sizeof(int32_t) * (size_t)count);
@@ -813,9 +801,9 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
       const rid_batch_item& x = items[i];
       hitems[i] = BatchItemDev{x.m, x.n, x.k, x.l, (const double2*)x.A, x.lda, (double2*)x.Y, x.ldy, x.perm,
                                (double2*)x.T, x.ldt, x.seed};
-      hpost[i] = PostItemDev{bp->plans[i]->xrow, bp->plans[i]->grow_norm2};
+      hpost[i] = PostItemDev{rid_btc_x(bp->sketch, i), rid_btc_gnorm2(bp->sketch, i)};
       order[i] = i;
-      cost[i] = 8.0 * (x.l + nprobe) * (double)x.m * (double)x.n + 16.0 * (double)x.n * x.l * x.k;
+      cost[i] = 16.0 * (double)x.n * x.l * x.k + 8.0 * (double)x.n * x.k * nprobe;   // QR, solve and error flops
     }
     for (int32_t w = 1; w < count; w *= 2) {
       for (int32_t lo = 0; lo < count; lo += 2 * w) {
@@ -831,9 +819,10 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
   const size_t off_post = (size_t)count * sizeof(BatchItemDev);
   const size_t off_order = off_post + (size_t)count * sizeof(PostItemDev);
   const size_t off_next = off_order + (size_t)count * sizeof(int32_t);
+  bp->dev_bytes = off_next + 256;
   cudaError_t e = cudaSuccess;
   if (st == RID_OK) {
-    if (rid_dev_alloc((void**)&bp->dev, off_next + 256, bp->home, bp->device) != cudaSuccess) st = RID_ENOMEM;
+    if (rid_dev_alloc((void**)&bp->dev, bp->dev_bytes, bp->home, bp->device) != cudaSuccess) st = RID_ENOMEM;
   }
   if (st == RID_OK) {
     e = cudaMemcpyAsync(bp->dev, hitems, off_post, cudaMemcpyHostToDevice, bp->home);
@@ -844,19 +833,8 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
     if (e == cudaSuccess) e = cudaStreamSynchronize(bp->home);     // the host arrays are pageable
     if (e != cudaSuccess) st = RID_ECUDA;
   }
-  // branch streams and events
-  if (st == RID_OK) {
-    bp->nbranch = count < 64 ? count : 64;
-    bp->branches = (cudaStream_t*)calloc((size_t)bp->nbranch, sizeof(cudaStream_t));
-    bp->events = (cudaEvent_t*)calloc((size_t)bp->nbranch + 1, sizeof(cudaEvent_t));
-    if (!bp->branches || !bp->events) st = RID_ENOMEM;
-    for (int i = 0; st == RID_OK && i < bp->nbranch; ++i)
-      if (cudaStreamCreateWithFlags(&bp->branches[i], cudaStreamNonBlocking) != cudaSuccess) st = RID_ECUDA;
-    for (int i = 0; st == RID_OK && i < bp->nbranch + 1; ++i)
-      if (cudaEventCreateWithFlags(&bp->events[i], cudaEventDisableTiming) != cudaSuccess) st = RID_ECUDA;
-    for (int i = 0; st == RID_OK && i < 3; ++i)
-      if (cudaEventCreate(&bp->times[i]) != cudaSuccess) st = RID_ECUDA;
-  }
+  for (int i = 0; st == RID_OK && i < 3; ++i)
+    if (cudaEventCreate(&bp->times[i]) != cudaSuccess) st = RID_ECUDA;
   // the persistent finishing launch
   int per_sm = 1, sms = 0;
   if (st == RID_OK) {
@@ -864,33 +842,20 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_post_kernel, BT_THREADS, batch_post_smem_bytes());
     if (per_sm < 1) per_sm = 1;
   }
-  // capture: every plan's sketch on its branch, then the finishing kernel
+  // capture: the sketch launch, then the finishing launch
   cudaStream_t cap = nullptr;
   if (st == RID_OK && cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) st = RID_ECUDA;
   if (st == RID_OK) {
     bool capturing = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     if (!capturing) st = RID_ECUDA;
     if (st == RID_OK && cudaEventRecordWithFlags(bp->times[0], cap, cudaEventRecordExternal) != cudaSuccess) st = RID_ECUDA;
-    if (st == RID_OK && cudaEventRecord(bp->events[0], cap) != cudaSuccess) st = RID_ECUDA;
-    for (int b = 0; st == RID_OK && b < bp->nbranch; ++b)
-      if (cudaStreamWaitEvent(bp->branches[b], bp->events[0], 0) != cudaSuccess) st = RID_ECUDA;
-    for (int32_t t = 0; st == RID_OK && t < count; ++t) {
-      const int32_t i = order[t];
-      rid_plan_s* pl = bp->plans[i];
-      pl->stream = bp->branches[t % bp->nbranch];
-      st = rid_sketch(pl, items[i].A, items[i].lda, items[i].Y, items[i].ldy);
-    }
-    for (int b = 0; st == RID_OK && b < bp->nbranch; ++b) {
-      if (cudaEventRecord(bp->events[b + 1], bp->branches[b]) != cudaSuccess ||
-          cudaStreamWaitEvent(cap, bp->events[b + 1], 0) != cudaSuccess)
-        st = RID_ECUDA;
-    }
+    if (st == RID_OK && rid_btc_launch(bp->sketch, cap) != cudaSuccess) st = RID_ECUDA;
     if (st == RID_OK && cudaEventRecordWithFlags(bp->times[1], cap, cudaEventRecordExternal) != cudaSuccess) st = RID_ECUDA;
     if (st == RID_OK && cudaMemsetAsync(bp->dev + off_next, 0, sizeof(unsigned), cap) != cudaSuccess) st = RID_ECUDA;
     if (st == RID_OK) {
       PostArgs args{(const BatchItemDev*)bp->dev, (const PostItemDev*)(bp->dev + off_post),
                     (const int32_t*)(bp->dev + off_order), count, (unsigned*)(bp->dev + off_next), nprobe, err_out,
-                    status_out};
+                    status_out, rid_btc_error_word(bp->sketch)};
       const int grid = sms * per_sm < count ? sms * per_sm : count;
       batch_post_kernel<<<grid, BT_THREADS, batch_post_smem_bytes(), cap>>>(args);
       if (cudaGetLastError() != cudaSuccess) st = RID_ECUDA;
@@ -908,8 +873,6 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
       }
       cudaGetLastError();
     }
-    for (int32_t i = 0; i < count; ++i)
-      if (bp->plans[i]) bp->plans[i]->stream = bp->home;
   }
   if (cap) cudaStreamDestroy(cap);
   free(order);
@@ -923,6 +886,12 @@ rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* item
   }
   *out = bp;
   return RID_OK;
+}
+
+rid_status rid_batch_tc_create(rid_batch_plan_t* out, const rid_batch_item* items, int32_t count, int32_t nprobe,
+                               uint64_t probe_seed, double* err_out, int32_t* status_out, void* stream) {
+  return rid_batch_tc_create_tuned(out, items, count, nprobe, probe_seed, err_out, status_out, nullptr, nullptr, 0,
+                                   stream);
 }
 
 rid_status rid_batch_tc_run(rid_batch_plan_t bp, void* stream) {
@@ -939,6 +908,13 @@ rid_status rid_batch_tc_times(rid_batch_plan_t bp, double out[2]) {
     return RID_ECUDA;
   out[0] = a;
   out[1] = b;
+  return RID_OK;
+}
+
+rid_status rid_batch_tc_info(rid_batch_plan_t bp, double out[4]) {
+  if (!bp || !out || !bp->sketch) return RID_EINVAL;
+  rid_btc_info(bp->sketch, out);
+  out[0] += (double)bp->dev_bytes;
   return RID_OK;
 }
 

@@ -160,6 +160,32 @@ cudaError_t rid_launch_tail_ratio(const rid_plan_s* p, const double2* Y, int64_t
 // est / upper from X of the last sketch, perm and T, into p->err_out.
 cudaError_t rid_launch_error_sketched(const rid_plan_s* p, const int32_t* perm, const double2* T, int64_t ldt);
 
+// The batched tensor-core sketch (rid_batch_tc.cu): Y = Omega A and the row
+// probes' X = G A of every problem in one persistent cooperative launch.
+struct rid_btc_problem {
+  const double2* A;
+  int64_t lda, m, n;
+  double2* Y;
+  int64_t ldy;
+  int32_t l;
+  uint64_t seed;
+  int32_t tile_n;          // widest N-tile (rows of Omega', 16 .. 128); 0: 128
+  int32_t ksplit;          // K-splits; 0: 1
+};
+struct rid_btc_s;
+// Draws every problem's Omega' (seed; the probe rows from probe_seed) and
+// lays out the waves and work lists; synchronizes `stream`.
+rid_status rid_btc_create(rid_btc_s** out, const rid_btc_problem* probs, int32_t count, int32_t nprobe,
+                          uint64_t probe_seed, size_t wave_bytes, cudaStream_t stream);
+// Clears the work counters and launches the persistent kernel (capturable).
+cudaError_t rid_btc_launch(const rid_btc_s* h, cudaStream_t stream);
+const double2* rid_btc_x(const rid_btc_s* h, int32_t i);       // r x n, ld r, of problem i (input order)
+const double* rid_btc_gnorm2(const rid_btc_s* h, int32_t i);   // ||g_q||^2 of problem i
+const int* rid_btc_error_word(const rid_btc_s* h);             // non-zero after a wait gave up
+// out: device bytes, waves, work items, CTAs
+void rid_btc_info(const rid_btc_s* h, double out[4]);
+void rid_btc_destroy(rid_btc_s* h, cudaStream_t stream);
+
 // ---------------------------------------------------------------------------
 // Device helpers shared by the kernels.
 // ---------------------------------------------------------------------------

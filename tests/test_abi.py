@@ -107,3 +107,35 @@ def test_plain_c99_consumer_compiles_links_and_runs(lib):
     r = subprocess.run([exe], capture_output=True, text=True, timeout=60)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "ok"
+
+
+def test_batch_tc_calls_reject_bad_arguments_before_cuda_work(lib):
+    """The tensor-core batch checks its items and tile choices on the host
+    (fake, aligned device pointers: nothing is dereferenced before the checks)."""
+    from paper_1205_3830_gb300 import _native
+    E = _native.RID_EINVAL
+    h = ctypes.c_void_p()
+    out = (ctypes.c_double * 4)()
+    assert lib.rid_batch_tc_info(None, out) == E
+    assert lib.rid_batch_tc_run(None, None) == E
+    assert lib.rid_batch_tc_times(None, out) == E
+    items = (_native.BatchItem * 1)()
+    it = items[0]
+    it.m, it.n, it.k, it.l = 100, 80, 4, 12
+    it.A, it.lda, it.Y, it.ldy, it.perm, it.T, it.ldt, it.seed = 256, 100, 512, 12, 768, 1024, 4, 1
+    err, status = ctypes.c_void_p(2048), ctypes.c_void_p(4096)
+    call = lambda tn, ks, cnt=1, npr=8: lib.rid_batch_tc_create_tuned(
+        ctypes.byref(h), ctypes.byref(items), cnt, npr, 1, err, status,
+        ctypes.cast(tn, ctypes.c_void_p) if tn is not None else None,
+        ctypes.cast(ks, ctypes.c_void_p) if ks is not None else None, 0, None)
+    for bad in (8, 129, 100):
+        assert call((ctypes.c_int32 * 1)(bad), None) == E and not h.value
+    assert call(None, (ctypes.c_int32 * 1)(-1)) == E
+    assert call(None, None, cnt=0) == E
+    assert call(None, None, npr=0) == E and call(None, None, npr=17) == E
+    it.k = 70                                                   # k > 64: beyond the batch's limit
+    it.l = 72
+    it.ldy = 72
+    it.ldt = 70
+    assert lib.rid_batch_tc_create_tuned(ctypes.byref(h), ctypes.byref(items), 1, 8, 1, err, status, None, None, 0,
+                                         None) == _native.RID_EUNSUPPORTED

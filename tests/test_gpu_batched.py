@@ -166,3 +166,98 @@ def test_batch_tc_replays_and_reports_rank_deficiency(rid):
         assert a["est"] == c["est"] and a["status"] == c["status"] == 0
     assert second[6]["status"] == 4 and second[6]["est"] == -1.0
     b.close()
+
+
+def test_batch_tc_is_independent_of_tiles_waves_and_company(rid):
+    """The persistent tensor-core sketch: the N-tile width, the number of
+    waves (a small digit buffer forces one problem or two per wave) and the
+    other problems of the batch change nothing, bit for bit; a K-split moves
+    T by rounding only."""
+    probs = make_problems(14, seed=21, m_range=(64, 700), n_range=(64, 420), k_range=(4, 40))
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+
+    def run(**kw):
+        b = rid.BatchTC(dev if "sub" not in kw else kw.pop("sub"), nprobe=8, probe_seed=3, **kw)
+        res = [dict(x, T=x["T"].clone(), perm=x["perm"].clone()) for x in b.run().results()]
+        info = b.info()
+        b.close()
+        return res, info
+
+    ref, info0 = run()
+    assert info0["waves"] == 1
+    narrow, _ = run(tile_n=64)
+    waves, info_w = run(wave_bytes=1 << 20)
+    assert info_w["waves"] >= 4 and info_w["bytes"] < info0["bytes"]
+    for a, b2, c in zip(ref, narrow, waves):
+        assert a["status"] == b2["status"] == c["status"] == 0
+        for x in (b2, c):
+            assert torch.equal(a["perm"], x["perm"]) and torch.equal(a["T"], x["T"])
+            assert a["est"] == x["est"] and a["upper"] == x["upper"]
+    alone, _ = run(sub=[dev[4]])
+    assert torch.equal(alone[0]["perm"], ref[4]["perm"]) and torch.equal(alone[0]["T"], ref[4]["T"])
+    assert alone[0]["est"] == ref[4]["est"]
+    split, _ = run(ksplit=2)
+    from gpu_util import row_probe_tolerances
+    for (A, k, l, s), a, x in zip(probs, ref, split):
+        assert torch.equal(a["perm"], x["perm"])
+        if a["T"].numel():
+            assert (a["T"] - x["T"]).abs().max().item() <= 1e-12 * a["T"].abs().max().item()
+        # the estimate cancels down to ~1e-8 of |G| |A|: two sketches' rounding
+        # moves it by up to twice the row-probe bound
+        perm, T = to_host(a["perm"]), to_host(a["T"])
+        G = oracle.left_probe_matrix(8, A.shape[0], 3)
+        tol_est, _ = row_probe_tolerances(A, perm, T, G, "fp64_emulated")
+        assert abs(a["est"] - x["est"]) <= 2 * tol_est + 1e-14 * a["est"]
+
+
+def test_batch_tc_tall_problems_with_k_splits_match_oracle(rid):
+    """Tall problems (many 256-real chunks per column) split over K: J as the
+    oracle's, T within 1e-10, est within the row-probe bound."""
+    from gpu_util import row_probe_tolerances
+    shapes = [(5000, 130, 6, 14), (3000, 64, 10, 18), (4100, 200, 20, 28)]
+    probs = [(synth.lowrank_plus_noise(m, n, k, 1e-10, seed=40 + i), k, l, 900 + i) for i, (m, n, k, l) in enumerate(shapes)]
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    b = rid.BatchTC(dev, nprobe=6, probe_seed=2, ksplit=[4, 8, 3], tile_n=[0, 64, 96])
+    res = b.run().results()
+    for (A, k, l, s), r in zip(probs, res):
+        assert r["status"] == 0
+        out = oracle.rid(A, k, l, seed=s)
+        perm, T = to_host(r["perm"]), to_host(r["T"])
+        assert np.array_equal(perm[:k], out["J"])
+        assert np.abs(T - out["T"]).max() <= 1e-10 * np.abs(out["T"]).max()
+        G = oracle.left_probe_matrix(6, A.shape[0], 2)
+        est_o, up_o, _ = oracle.error_estimate_left(A, perm, T, G)
+        tol_est, tol_up = row_probe_tolerances(A, perm, T, G, "fp64_emulated")
+        assert abs(r["est"] - est_o) <= tol_est + 1e-14 * est_o
+        assert abs(r["upper"] - up_o) <= tol_up + 1e-14 * up_o
+    b.close()
+
+
+def test_batch_tc_argument_checks(rid):
+    from paper_1205_3830_gb300._native import RIDError
+    probs = make_problems(2, seed=22)
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    for bad in (8, 130, 100):
+        with pytest.raises(RIDError, match="EINVAL"):
+            rid.BatchTC(dev, nprobe=4, tile_n=bad)
+    with pytest.raises(RIDError, match="EINVAL"):
+        rid.BatchTC(dev, nprobe=4, ksplit=-1)
+
+
+def test_tc_tuning_picks_and_caches_a_choice_per_class(rid, tmp_path):
+    probs = make_problems(24, seed=23, m_range=(64, 700), n_range=(64, 300), k_range=(4, 30))
+    dev = [(to_dev_colmajor(A), k, l, s) for (A, k, l, s) in probs]
+    path = str(tmp_path / "tc_tiles.json")
+    tun = rid.TcTuning(path)
+    report = tun.tune(dev, nprobe=8, probe_seed=1, per_class=8, reps=1)
+    classes = {rid.TcTuning.size_class(int(A.shape[0]), int(A.shape[1]), l + 8) for (A, k, l, s) in dev}
+    assert set(report) == classes
+    for key, (t, s, ms) in report.items():
+        assert (t, s) in rid.TcTuning.candidates(key) and ms > 0
+    again = rid.TcTuning(path)                    # read back from the cache file
+    assert again.table == tun.table
+    b = rid.BatchTC(dev, nprobe=8, probe_seed=1, tuning=again)
+    for r, (A, k, l, s) in zip(b.run().results(), probs):
+        assert r["status"] == 0
+        assert np.array_equal(to_host(r["perm"])[:k], oracle.rid(A, k, l, seed=s)["J"])
+    b.close()

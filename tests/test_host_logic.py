@@ -189,3 +189,23 @@ def test_layout_rejects_wrong_shape_and_dtype():
         _layout(x, 5, 3)
     with pytest.raises(ValueError, match="complex128"):
         _layout(x.to(torch.complex64), 4, 3)
+
+
+def test_tc_tuning_size_classes_and_candidates():
+    """The autotuner's size classes (m to a power of two, column blocks, N-tiles
+    at 128 rows) and its candidate list (K-splits only where the problem has
+    twice the chunks)."""
+    import paper_1205_3830_gb300 as rid
+    T = rid.TcTuning
+    assert T.size_class(64, 64, 12) == (256, 1, 1)
+    assert T.size_class(257, 129, 64) == (512, 2, 1)
+    assert T.size_class(1024, 1000, 65) == (1024, 8, 2)
+    assert T.size_class(5000, 300, 40) == (8192, 4, 1)
+    small = T.candidates((256, 1, 1))                       # 2 chunks: no K-split
+    assert small == [(128, 1), (96, 1), (64, 1)]
+    big = T.candidates((1024, 8, 1))                        # 8 chunks: 2 and 4 splits
+    assert (64, 4) in big and len(big) == 9
+    tun = T(None)
+    assert tun.choice(300, 300, 20) == (0, 0)               # untuned class: the defaults
+    tun.table[T.size_class(300, 300, 20)] = (96, 2)
+    assert tun.choice(300, 300, 20) == (96, 2) and tun.choice(300, 300, 80) == (0, 0)
