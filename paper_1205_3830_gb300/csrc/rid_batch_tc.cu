@@ -149,6 +149,18 @@ struct TaskQueue {
   int64_t p_lo, p_hi;
 };
 
+// What cutting one wave reads, passed by value (kept in registers: a
+// reference to the kernel's argument block would put it in local memory).
+struct CutWave {
+  const BtcProb* probs;
+  const int64_t* a_pref;
+  const int64_t* o_pref;
+  unsigned char* buf;
+  unsigned* ctr;
+  int p_lo, p_hi;
+  int64_t ta, tend;         // A' tasks, all tasks of the wave
+};
+
 __device__ __forceinline__ void queue_init(TaskQueue& q, unsigned* ctr) {
   q.nxt = (int64_t)atomicAdd(ctr, (unsigned)BTC_GRAB);
   q.lim = q.nxt + BTC_GRAB;
@@ -157,65 +169,72 @@ __device__ __forceinline__ void queue_init(TaskQueue& q, unsigned* ctr) {
   q.p_lo = q.p_hi = 0;
 }
 
-// Next task (relative to the wave's first) and its problem; -1 past the end.
-// pref: the wave's A' task prefix for t < ta, its Omega' prefix (shifted by
-// ta) beyond.
-__device__ __forceinline__ int64_t queue_next(TaskQueue& q, unsigned* ctr, const BtcArgs& a, int wp_lo, int wp_hi,
-                                              int64_t ta, int64_t tend, int& p) {
+// Next task's number within its problem (and kind) and the problem; p = -1
+// past the wave's end.  Tasks below ta are A' tasks, the others Omega' tasks.
+__device__ __forceinline__ int64_t queue_next(TaskQueue& q, const CutWave& cw, int& p) {
   if (q.nxt == q.lim) {
     q.nxt = q.pre;
     q.lim = q.pre + BTC_GRAB;
-    q.pre = (int64_t)atomicAdd(ctr, (unsigned)BTC_GRAB);
+    q.pre = (int64_t)atomicAdd(cw.ctr, (unsigned)BTC_GRAB);
   }
   const int64_t t = q.nxt++;
-  if (t >= tend) {
+  if (t >= cw.tend) {
     p = -1;
     return t;
   }
   if (t < q.p_lo || t >= q.p_hi) {
     // the problem's task range, in wave-relative task numbers
-    if (t < ta) {
-      const int64_t g = a.a_pref[wp_lo] + t;
-      q.p = find_prob(a.a_pref, wp_lo, wp_hi, g);
-      q.p_lo = a.a_pref[q.p] - a.a_pref[wp_lo];
-      q.p_hi = a.a_pref[q.p + 1] - a.a_pref[wp_lo];
+    if (t < cw.ta) {
+      const int64_t base = cw.a_pref[cw.p_lo];
+      q.p = find_prob(cw.a_pref, cw.p_lo, cw.p_hi, base + t);
+      q.p_lo = cw.a_pref[q.p] - base;
+      q.p_hi = cw.a_pref[q.p + 1] - base;
     } else {
-      const int64_t g = a.o_pref[wp_lo] + (t - ta);
-      q.p = find_prob(a.o_pref, wp_lo, wp_hi, g);
-      q.p_lo = ta + a.o_pref[q.p] - a.o_pref[wp_lo];
-      q.p_hi = ta + a.o_pref[q.p + 1] - a.o_pref[wp_lo];
+      const int64_t base = cw.o_pref[cw.p_lo];
+      q.p = find_prob(cw.o_pref, cw.p_lo, cw.p_hi, base + (t - cw.ta));
+      q.p_lo = cw.ta + cw.o_pref[q.p] - base;
+      q.p_hi = cw.ta + cw.o_pref[q.p + 1] - base;
     }
   }
   p = q.p;
-  return t - q.p_lo;          // the task's number within its problem (and kind)
+  return t - q.p_lo;
 }
 
 struct CutTask {
   int p;                    // problem; -1: none
   bool omega;               // an Omega' task (else A')
-  int64_t local;            // task number within the problem
+  int c;                    // chunk
+  int idx;                  // column j of A' / row i of Omega
 };
 
-// A' task `local` = (column j, chunk c), chunk-major; Omega' task = (row i, chunk c).
-__device__ __forceinline__ void cut_load(const BtcArgs& a, const CutTask& t, int lane, double2 (&x)[4]) {
-  if (t.p < 0) return;
-  const BtcProb& P = a.probs[t.p];
-  const double2* src;
-  int64_t r0;
-  bool ok = true;
-  if (!t.omega) {
-    const int c = (int)(t.local / P.n);
-    const int64_t j = t.local - (int64_t)c * P.n;
-    src = P.A + j * P.lda;
-    r0 = (int64_t)c * 128 + 4 * lane;
+// A' task number = c n + j (chunk-major); Omega' task number = i NC + c.
+// Decoded once by lane 0 (32-bit division: a problem has fewer than 2^31
+// tasks) and broadcast.
+__device__ __forceinline__ void cut_decode(const CutWave& cw, int p, bool omega, int64_t local, CutTask& t) {
+  t.p = p;
+  t.omega = omega;
+  t.c = t.idx = 0;
+  if (p < 0) return;
+  const BtcProb& P = cw.probs[p];
+  const unsigned u = (unsigned)local;
+  if (!omega) {
+    const unsigned n = (unsigned)P.n;
+    t.c = (int)(u / n);
+    t.idx = (int)(u - (unsigned)t.c * n);
   } else {
-    const int i = (int)(t.local / P.NC);
-    const int c = (int)(t.local - (int64_t)i * P.NC);
-    src = P.om + (int64_t)i * P.ldo;
-    r0 = (int64_t)c * 128 + 4 * lane;
+    const unsigned nc = (unsigned)P.NC;
+    t.idx = (int)(u / nc);
+    t.c = (int)(u - (unsigned)t.idx * nc);
   }
+}
+
+__device__ __forceinline__ void cut_load(const CutWave& cw, const CutTask& t, int lane, double2 (&x)[4]) {
+  if (t.p < 0) return;
+  const BtcProb& P = cw.probs[t.p];
+  const double2* src = !t.omega ? P.A + (int64_t)t.idx * P.lda : P.om + (int64_t)t.idx * P.ldo;
+  const int64_t r0 = (int64_t)t.c * 128 + 4 * lane;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) x[u] = (ok && r0 + u < P.m) ? __ldg(src + r0 + u) : make_double2(0.0, 0.0);
+  for (int u = 0; u < 4; ++u) x[u] = r0 + u < P.m ? __ldg(src + r0 + u) : make_double2(0.0, 0.0);
 }
 
 __device__ __forceinline__ void store_pieces(uint16_t* base, int64_t tile_elems, int off, const uint32_t (&w)[4][TC_S]) {
@@ -224,15 +243,19 @@ __device__ __forceinline__ void store_pieces(uint16_t* base, int64_t tile_elems,
     *(uint4*)(base + s * tile_elems + off) = make_uint4(w[0][s], w[1][s], w[2][s], w[3][s]);
 }
 
-__device__ __forceinline__ void cut_store(const BtcArgs& a, int w, const CutTask& t, int lane, const double2 (&x)[4]) {
-  const BtcProb& P = a.probs[t.p];
-  unsigned char* buf = wave_buf(a, w);
+// -x by its sign bit (no FP64 instruction)
+__device__ __forceinline__ double neg_bits(double x) {
+  return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
+__device__ __forceinline__ void cut_store(const CutWave& cw, const CutTask& t, int lane, const double2 (&x)[4]) {
+  const BtcProb& P = cw.probs[t.p];
   const int st_in_chunk = lane >> 2;
   const int k = 8 * (lane & 3);
+  const int c = t.c;
   uint32_t wd[4][TC_S];
   if (!t.omega) {
-    const int c = (int)(t.local / P.n);
-    const int64_t j = t.local - (int64_t)c * P.n;
+    const int64_t j = t.idx;
     int e = TC_EXP_ZERO;
 #pragma unroll
     for (int u = 0; u < 4; ++u) e = max(e, max(exp_of(x[u].x), exp_of(x[u].y)));
@@ -240,20 +263,20 @@ __device__ __forceinline__ void cut_store(const BtcArgs& a, int w, const CutTask
 #pragma unroll
     for (int u = 0; u < 4; ++u) digit_words(x[u], e, wd[u]);
     // tiles [column block][K stage][digit] of 128 rows; column j is row j % 128
-    uint16_t* base = (uint16_t*)(buf + P.a_off) +
+    uint16_t* base = (uint16_t*)(cw.buf + P.a_off) +
                      (((j >> 7) * P.nst + (int64_t)c * TC_SPC + st_in_chunk) * TC_S) * TC_TILE_ELEMS;
     store_pieces(base, TC_TILE_ELEMS, tile_offset((int)(j & 127), k) / 2, wd);
-    if (lane == 0) ((int*)(buf + P.e_off))[j * P.NC + c] = e;
+    if (lane == 0) ((int*)(cw.buf + P.e_off))[j * P.NC + c] = e;
   } else {
-    const int i = (int)(t.local / P.NC);
-    const int c = (int)(t.local - (int64_t)i * P.NC);
+    const int i = t.idx;
     const int e = P.om_exp[i];
     // Omega' row 2i: (Re w, -Im w); row 2i + 1: (Im w, Re w)
     const int R = 2 * i, nt = R / P.tile_w, rr = R - nt * P.tile_w;
     const int64_t tile_elems = (int64_t)P.tile_w * TC_KS;
-    uint16_t* base = (uint16_t*)(buf + P.o_off) + (((int64_t)nt * P.nst + (int64_t)c * TC_SPC + st_in_chunk) * TC_S) * tile_elems;
+    uint16_t* base = (uint16_t*)(cw.buf + P.o_off) +
+                     (((int64_t)nt * P.nst + (int64_t)c * TC_SPC + st_in_chunk) * TC_S) * tile_elems;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) digit_words(make_double2(x[u].x, -x[u].y), e, wd[u]);
+    for (int u = 0; u < 4; ++u) digit_words(make_double2(x[u].x, neg_bits(x[u].y)), e, wd[u]);
     store_pieces(base, tile_elems, tile_offset(rr, k) / 2, wd);
 #pragma unroll
     for (int u = 0; u < 4; ++u) digit_words(make_double2(x[u].y, x[u].x), e, wd[u]);
@@ -261,32 +284,32 @@ __device__ __forceinline__ void cut_store(const BtcArgs& a, int w, const CutTask
   }
 }
 
-// All 16 warps cut wave w's digits.
+// All 16 warps cut one wave's digits.
 // (out of line: its registers are allocated apart from the product's flush loop)
-__device__ __noinline__ void cut_wave(const BtcArgs& a, int w) {
+__device__ __noinline__ void cut_wave(const CutWave cw) {
   const int lane = threadIdx.x & 31;
-  const int p_lo = a.wave_first[w], p_hi = a.wave_first[w + 1];
-  const int64_t ta = a.a_pref[p_hi] - a.a_pref[p_lo];
-  const int64_t tend = ta + a.o_pref[p_hi] - a.o_pref[p_lo];
-  unsigned* ctr = a.ctr + 1 + w;
   TaskQueue q;
-  CutTask cur{-1, false, 0}, nxt{-1, false, 0};
+  CutTask cur{-1, false, 0, 0}, nxt{-1, false, 0, 0};
   auto next = [&](CutTask& dst) {
-    int64_t local = 0;
-    int p = -1;
-    if (lane == 0) local = queue_next(q, ctr, a, p_lo, p_hi, ta, tend, p);
-    dst.p = __shfl_sync(0xffffffffu, p, 0);
-    dst.local = __shfl_sync(0xffffffffu, local, 0);
-    dst.omega = dst.p >= 0 && __shfl_sync(0xffffffffu, q.p_lo, 0) >= ta;
+    CutTask t{-1, false, 0, 0};
+    if (lane == 0) {
+      int p = -1;
+      const int64_t local = queue_next(q, cw, p);
+      cut_decode(cw, p, q.p_lo >= cw.ta, local, t);
+    }
+    dst.p = __shfl_sync(0xffffffffu, t.p, 0);
+    dst.omega = __shfl_sync(0xffffffffu, (int)t.omega, 0) != 0;
+    dst.c = __shfl_sync(0xffffffffu, t.c, 0);
+    dst.idx = __shfl_sync(0xffffffffu, t.idx, 0);
   };
-  if (lane == 0) queue_init(q, ctr);
+  if (lane == 0) queue_init(q, cw.ctr);
   next(cur);
   double2 x[4], xn[4];
-  cut_load(a, cur, lane, x);
+  cut_load(cw, cur, lane, x);
   while (cur.p >= 0) {
     next(nxt);
-    cut_load(a, nxt, lane, xn);
-    cut_store(a, w, cur, lane, x);
+    cut_load(cw, nxt, lane, xn);
+    cut_store(cw, cur, lane, x);
     cur = nxt;
 #pragma unroll
     for (int u = 0; u < 4; ++u) x[u] = xn[u];
@@ -338,7 +361,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) batch_sketch_tc_kernel(BtcArgs 
   uint32_t pit = 0, mit = 0, mcl = 0, fcl = 0;
   for (int w = 0; w < a.waves; ++w) {
     // ---------------- 1. cut wave w's digits ----------------
-    cut_wave(a, w);
+    {
+      const int p_lo = a.wave_first[w], p_hi = a.wave_first[w + 1];
+      const int64_t ta = a.a_pref[p_hi] - a.a_pref[p_lo];
+      cut_wave(CutWave{a.probs, a.a_pref, a.o_pref, wave_buf(a, w), a.ctr + 1 + w, p_lo, p_hi, ta,
+                       ta + a.o_pref[p_hi] - a.o_pref[p_lo]});
+    }
     fence_proxy_async_global();          // the digits are read by other CTAs' bulk copies
     __syncthreads();
     // ---------------- 2. every CTA's digits of the wave are in place ----------------
