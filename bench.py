@@ -39,8 +39,8 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # 2048 columns): the 65536 x 2048 capture of profiles/sketch_tc_kernel_65536x2048.md,
 # 4 x (4.896 + 0.127) GB, scaled by the panel's 4x rows; reported only for the
 # source it was measured on
-TC_TRAFFIC = {"bytes_per_launch": 20.09e9,
-              "source_sha1": "1ebb14eb1645e23229ef3f9ae32ebcdebe8f0026"}
+TC_TRAFFIC = {"bytes_per_launch": 20.11e9,
+              "source_sha1": "58cf1dd9ee758232488a32aa59e7c8015435e2ce"}
 
 
 TC_SOURCES = ("rid_sketch_tc.cu", "rid_tc_digits.cuh", "rid_tc.cuh")     # the product kernel's source

@@ -414,30 +414,28 @@ __global__ void __launch_bounds__(TC_THREADS, 1) batch_sketch_tc_kernel(BtcArgs 
         }
       }
     } else if (warp == 13) {
-      if (lane == 0) {
-        // ---- MMA issuer ----
-        for (int q = q0; q < q1 && !s_abort; ++q) {
-          const BtcItem it = a.items[q];
-          const BtcProb& P = a.probs[it.p];
-          const int c_begin = it.ks * P.cps, c_end = min(P.NC, c_begin + P.cps);
-          const uint32_t idesc = idesc_bf16_f32(128, tile_mma_n(P.tile_w, P.l2, it.nt, false));
-          const uint64_t o_step = (uint64_t)(P.tile_w * TC_KS * 2) >> 4;
-          for (int c = c_begin; c < c_end && !s_abort; ++c, ++mcl) {
-            for (int b = 0; b < TC_SPC; ++b) {
-              const uint32_t slot = mit & 1u, round = mit >> 1;
-              if (!mbar_wait(&full_bar[slot], round & 1u, TC_WAIT_BUDGET)) {
-                fail(21);
-                break;
-              }
-              tc_fence_after();
-              const uint64_t da0 = tile_desc(ring + slot * BTC_SLOT), db0 = tile_desc(ring + slot * BTC_SLOT + BTC_A_STAGE);
-              if (!mma_stage<TC_S, false>(tmem, da0, db0, o_step, idesc, b, (int)mcl, TC_SPC, acc_empty, acc_full)) {
-                fail(22);
-                break;
-              }
-              mma_commit(&empty_bar[slot]);
-              ++mit;
+      // ---- MMA issuer: the whole warp runs the loop, one elected lane issues ----
+      for (int q = q0; q < q1 && !s_abort; ++q) {
+        const BtcItem it = a.items[q];
+        const BtcProb& P = a.probs[it.p];
+        const int c_begin = it.ks * P.cps, c_end = min(P.NC, c_begin + P.cps);
+        const uint32_t idesc = idesc_bf16_f32(128, tile_mma_n(P.tile_w, P.l2, it.nt, false));
+        const uint64_t o_step = (uint64_t)(P.tile_w * TC_KS * 2) >> 4;
+        for (int c = c_begin; c < c_end && !s_abort; ++c, ++mcl) {
+          for (int b = 0; b < TC_SPC; ++b) {
+            const uint32_t slot = mit & 1u, round = mit >> 1;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[slot], round & 1u, TC_WAIT_BUDGET))) {
+              if (lane == 0) fail(21);
+              break;
             }
+            tc_fence_after();
+            const uint64_t da0 = tile_desc(ring + slot * BTC_SLOT), db0 = tile_desc(ring + slot * BTC_SLOT + BTC_A_STAGE);
+            if (!mma_stage<TC_S, false>(tmem, da0, db0, o_step, idesc, b, (int)mcl, TC_SPC, acc_empty, acc_full)) {
+              if (lane == 0) fail(22);
+              break;
+            }
+            mma_commit_w(&empty_bar[slot]);
+            ++mit;
           }
         }
       }
@@ -568,7 +566,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) batch_sketch_tc_kernel(BtcArgs 
   // ---------------- teardown ----------------
   __syncthreads();
   if (warp == 13) {
-    if (lane == 0) mma_commit(&mma_done);
+    mma_commit_w(&mma_done);
     __syncwarp();
     if (!mbar_wait(&mma_done, 0, TC_WAIT_BUDGET)) fail(91);
     __syncwarp();

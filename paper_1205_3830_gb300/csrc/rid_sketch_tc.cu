@@ -348,8 +348,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
                                 : mbar_wait(&empty_bar[k % NS], (k / NS) & 1, TC_WAIT_BUDGET);
         if (!ok) fail(12);
       }
-    } else if (warp == 13 && lane == 0 && leader) {
-      // ---------------- MMA issuer ----------------
+    } else if (warp == 13 && leader) {
+      // ---------------- MMA issuer (the whole warp; one elected lane issues) ----------------
       const uint32_t idesc = idesc_bf16_f32(PAIR ? 256 : 128, n_mma);
       const int stages_per_chunk = TC_SPC;
       // descriptor start addresses are in 16-byte units (low 14 bits): a tile
@@ -359,9 +359,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
       for (int cl = 0; cl < nchunks && !s_abort; ++cl) {
         for (int b = 0; b < stages_per_chunk && !s_abort; ++b) {
           // this CTA's tiles, and for a pair the other CTA's (relayed)
-          if (!mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET) ||
-              (PAIR && !mbar_wait_cluster(&peer_full[slot], round & 1, TC_WAIT_BUDGET))) {
-            fail(21);
+          if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[slot], round & 1, TC_WAIT_BUDGET) &&
+                                        (!PAIR || mbar_wait_cluster(&peer_full[slot], round & 1, TC_WAIT_BUDGET)))) {
+            if (lane == 0) fail(21);
             break;
           }
           tc_fence_after();
@@ -376,19 +376,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sketch_tc_kernel(TcArgs a) {
             default: ok = false;
           }
           if (!ok) {
-            fail(22);
+            if (lane == 0) fail(22);
             break;
           }
-          if (PAIR) mma_commit_pair_multicast(&empty_bar[slot], all_mask);
-          else mma_commit(&empty_bar[slot]);
+          if (PAIR) mma_commit_pair_multicast_w(&empty_bar[slot], all_mask);
+          else mma_commit_w(&empty_bar[slot]);
           if (++slot == NS) {
             slot = 0;
             ++round;
           }
         }
       }
-      if (PAIR) mma_commit_pair_multicast(&mma_done, all_mask);
-      else mma_commit(&mma_done);
+      if (PAIR) mma_commit_pair_multicast_w(&mma_done, all_mask);
+      else mma_commit_w(&mma_done);
     } else if (PAIR && warp == 13 && lane == 0) {
       // ---------------- relay (odd CTA of a pair) ----------------
       // the leader's MMAs read this CTA's tiles: tell it when each stage has landed

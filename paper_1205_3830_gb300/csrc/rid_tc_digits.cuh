@@ -155,6 +155,7 @@ __device__ __forceinline__ uint64_t tile_desc(const void* p) { return desc_sw64(
 // the smallest (group 3 holds d >= 3), each group waiting for its flush before
 // its first product of a chunk.  Descriptor start addresses are in 16-byte
 // units (low 14 bits): a tile offset within shared memory adds without carry.
+// Called by the whole MMA warp (converged); one elected lane issues.
 template <int SO, bool PAIR>
 __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t db0, uint64_t o_step, uint32_t idesc,
                                           int b, int cl, int stages_per_chunk, uint64_t* acc_empty,
@@ -168,7 +169,7 @@ __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t 
       // a pair's barrier also counts the other CTA's flush warps
       const bool ok = PAIR ? mbar_wait_cluster(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET)
                            : mbar_wait(&acc_empty[g], (cl - 1) & 1, TC_WAIT_BUDGET);
-      if (!ok) return false;
+      if (!__all_sync(0xffffffffu, ok)) return false;
       tc_fence_after();
     }
 #pragma unroll
@@ -179,14 +180,14 @@ __device__ __forceinline__ bool mma_stage(uint32_t tmem, uint64_t da0, uint64_t 
 #pragma unroll
       for (int kk = 0; kk < TC_KS / 16; ++kk) {   // K16 steps are 32 bytes apart in a row
         const uint32_t acc = (b == 0 && group_start && s == 0 && kk == 0) ? 0u : 1u;
-        if (PAIR) mma_bf16_pair(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
-        else mma_bf16(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+        if (PAIR) mma_bf16_pair_w(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
+        else mma_bf16_w(tmem + (uint32_t)(g * 128), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, acc);
       }
     }
     const bool group_end = (d <= 3);     // last diagonal of its group in this stage
     if (b == stages_per_chunk - 1 && group_end) {
-      if (PAIR) mma_commit_pair_multicast(&acc_full[g], 3);   // both CTAs flush their rows
-      else mma_commit(&acc_full[g]);
+      if (PAIR) mma_commit_pair_multicast_w(&acc_full[g], 3);   // both CTAs flush their rows
+      else mma_commit_w(&acc_full[g]);
     }
   }
   return true;
