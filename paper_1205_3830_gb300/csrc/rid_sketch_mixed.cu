@@ -205,33 +205,32 @@ sketch_mixed_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_cons
         if (!mbar_wait(&full_bar[k % MX_STAGES], (k / MX_STAGES) & 1, MX_WAIT_BUDGET)) fail(42);
     }
   } else if (warp == 1) {
-    if (lane == 0) {
-      const uint32_t idesc = idesc_bf16_f32(128, n_mma);
-      bool first = true;
-      for (int it = 0; it < nst && !s_abort; ++it) {
-        const int slot = it % MX_STAGES, round = it / MX_STAGES;
-        if (!mbar_wait(&full_bar[slot], round & 1, MX_WAIT_BUDGET)) {
-          fail(43);
-          break;
-        }
-        tc_fence_after();
+    // the whole warp runs the issue loop; elect.sync picks the lane that issues
+    const uint32_t idesc = idesc_bf16_f32(128, n_mma);
+    bool first = true;
+    for (int it = 0; it < nst && !s_abort; ++it) {
+      const int slot = it % MX_STAGES, round = it / MX_STAGES;
+      if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[slot], round & 1, MX_WAIT_BUDGET))) {
+        if (lane == 0) fail(43);
+        break;
+      }
+      tc_fence_after();
 #pragma unroll
-        for (int d = 2; d >= 0; --d) {           // smallest terms first
+      for (int d = 2; d >= 0; --d) {           // smallest terms first
 #pragma unroll
-          for (int s = 0; s <= d; ++s) {
-            const int t = d - s;
-            const uint64_t da = desc_sw64(a_tile(slot, t)), db = desc_sw64(o_tile(slot, s));
+        for (int s = 0; s <= d; ++s) {
+          const int t = d - s;
+          const uint64_t da = desc_sw64(a_tile(slot, t)), db = desc_sw64(o_tile(slot, s));
 #pragma unroll
-            for (int kk = 0; kk < MX_KS / 16; ++kk) {
-              mma_bf16(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, first ? 0u : 1u);
-              first = false;
-            }
+          for (int kk = 0; kk < MX_KS / 16; ++kk) {
+            mma_bf16_w(tmem, da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc, first ? 0u : 1u);
+            first = false;
           }
         }
-        mma_commit(&empty_bar[slot]);
       }
-      mma_commit(&acc_done);
+      mma_commit_w(&empty_bar[slot]);
     }
+    mma_commit_w(&acc_done);
   } else {
     // epilogue (warps 2-5): the accumulator rows of this warp's lane quarter
     const int quarter = warp & 3;
