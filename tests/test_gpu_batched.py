@@ -261,3 +261,39 @@ def test_tc_tuning_picks_and_caches_a_choice_per_class(rid, tmp_path):
         assert r["status"] == 0
         assert np.array_equal(to_host(r["perm"])[:k], oracle.rid(A, k, l, seed=s)["J"])
     b.close()
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1, 1), (1, 50, 1, 5), (50, 1, 1, 3), (777, 129, 64, 64),
+                                   (300, 4096, 64, 128), (20000, 200, 10, 20)], ids=str)
+def test_batch_tc_edge_shapes_match_oracle(rid, shape):
+    """Degenerate and extreme problems in one batch with ordinary ones: one
+    row, one column, k = l, the largest n, k and l the batch takes (3 N-tiles
+    of Omega' rows), and a tall problem of 157 chunks."""
+    from gpu_util import row_probe_tolerances
+    m, n, k, l = shape
+    probs = [(synth.lowrank_plus_noise(m, n, k, 1e-10, seed=60 + m + n), k, l, 4242)] + \
+        make_problems(3, seed=24)
+    dev = [(to_dev_colmajor(A), kk, ll, s) for (A, kk, ll, s) in probs]
+    b = rid.BatchTC(dev, nprobe=8, probe_seed=3)
+    res = b.run().results()
+    for (A, kk, ll, s), r in zip(probs, res):
+        assert r["status"] == 0
+        out = oracle.rid(A, kk, ll, seed=s)
+        perm, T = to_host(r["perm"]), to_host(r["T"])
+        assert np.array_equal(perm[:kk], out["J"])
+        assert sorted(perm.tolist()) == list(range(A.shape[1]))
+        if T.size:
+            # two FP64 evaluations differ in rounding by ~u per entry of Y; the
+            # triangular solve amplifies that by kappa(R11) (large for k = l,
+            # where R11 comes from a square sketch): first-order bound
+            # 8 l sqrt(n) u kappa(R11), at least the 1e-10 of the other tests
+            kappa = np.linalg.cond(np.triu(out["R"][:kk, :kk]))
+            tol_T = max(1e-10, 8 * ll * np.sqrt(A.shape[1]) * 2.0 ** -53 * kappa)
+            assert np.abs(T - out["T"]).max() <= tol_T * np.abs(out["T"]).max()
+            G = oracle.left_probe_matrix(8, A.shape[0], 3)
+            est_o, up_o, _ = oracle.error_estimate_left(A, perm, T, G)
+            tol_est, tol_up = row_probe_tolerances(A, perm, T, G, "fp64_emulated")
+            assert abs(r["est"] - est_o) <= tol_est + 1e-14 * est_o
+        else:
+            assert r["est"] == 0.0 and r["upper"] == 0.0
+    b.close()
