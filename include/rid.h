@@ -212,12 +212,22 @@ RID_API rid_status rid_sketch_cols(rid_plan_t plan, const void* A, int64_t lda, 
  * the same pass as Y = Omega A; Y is unchanged.  nprobe = 0 removes them.
  *   1 <= nprobe <= 16 and l + nprobe <= 512 (RID_EINVAL / RID_EUNSUPPORTED).
  *   X is FP64-grade in every mode: RID_MIXED_BF16 plans multiply the probe
- *   rows by the complex64 A (exact in FP64) on the FP64-emulated path while Y
- *   takes the BF16x3 product, so their error estimate stays FP64.
+ *   rows by the complex64 A with the exact-slice emulation of the
+ *   FP64-emulated mode (in a kernel of their own that cuts A's digits in
+ *   shared memory) while Y takes the BF16x3 product, so their error estimate
+ *   stays FP64.
  *   Allocates (l + nprobe) x m complex128 for Omega and G plus small buffers
  *   (RID_ENOMEM if that fails; the plan is then unchanged) and synchronizes
  *   the stream.  rid_plan_omega still returns the l rows of the test matrix. */
 RID_API rid_status rid_plan_set_probes(rid_plan_t plan, int32_t nprobe, uint64_t probe_seed);
+
+/* Device pointer to the row probes' products X = G A of the last sketch
+ * (Sec. 3.3: the estimate is formed from them): nprobe x n complex128,
+ * column-major with leading dimension *ldx = nprobe, in plan memory and
+ * overwritten by the next sketch.  Read-only for the caller; read it in the
+ * plan's stream order.  RID_EINVAL without probes or before a sketch since
+ * they were set. */
+RID_API rid_status rid_plan_probe_products(rid_plan_t plan, const void** X, int64_t* ldx);
 
 /* rid_plan_create and rid_plan_set_probes(plan, nprobe, probe_seed) in one
  * call: the plan is built with its nprobe row probes (0 <= nprobe <= 16) from

@@ -167,6 +167,16 @@ class Plan:
         self.stream.synchronize()
         return torch.as_tensor(view, device=self.device).clone()
 
+    def probe_products(self):
+        """A copy of the row probes' products X = G A of the last sketch
+        (nprobe x n complex128)."""
+        ptr, ldx = ctypes.c_void_p(), ctypes.c_int64()
+        check(self._lib.rid_plan_probe_products(self._h, ctypes.byref(ptr), ctypes.byref(ldx)),
+              "rid_plan_probe_products")
+        view = _CudaView(ptr.value, (ldx.value, self.n), (16, 16 * ldx.value), "<c16")
+        self.stream.synchronize()
+        return torch.as_tensor(view, device=self.device).clone()
+
     def set_omega(self, omega):
         """Use a caller-supplied l x m complex128 Omega (row-major, on the device)."""
         omega = omega.to(device=self.device, dtype=torch.complex128)

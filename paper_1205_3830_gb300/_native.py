@@ -28,6 +28,7 @@ SIGNATURES = {
     "rid_plan_footprint": (ctypes.c_int, [_i64, _i64, _i32, _i32, ctypes.c_int, ctypes.c_int,
                                           ctypes.POINTER(ctypes.c_size_t)]),
     "rid_plan_omega": (ctypes.c_int, [_c_plan, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
+    "rid_plan_probe_products": (ctypes.c_int, [_c_plan, ctypes.POINTER(_p), ctypes.POINTER(_i64)]),
     "rid_plan_set_omega": (ctypes.c_int, [_c_plan, _p, _i64]),
     "rid_plan_use_srft": (ctypes.c_int, [_c_plan, _u64]),
     "rid_sketch": (ctypes.c_int, [_c_plan, _p, _i64, _p, _i64]),

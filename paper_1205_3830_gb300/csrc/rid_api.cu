@@ -346,6 +346,14 @@ rid_status rid_plan_omega(rid_plan_t p, const void** omega, int64_t* ldo) {
   return RID_OK;
 }
 
+rid_status rid_plan_probe_products(rid_plan_t p, const void** X, int64_t* ldx) {
+  if (!p || !X || !ldx) return RID_EINVAL;
+  if (p->nrow < 1 || !p->x_valid) return RID_EINVAL;
+  *X = p->xrow;
+  *ldx = p->nrow;
+  return RID_OK;
+}
+
 rid_status rid_plan_set_omega(rid_plan_t p, const void* omega, int64_t ldo) {
   if (!p || !omega || ldo < p->m) return RID_EINVAL;
   DeviceGuard g(p->device);

@@ -155,6 +155,17 @@ cudaError_t rid_launch_row_probe_norms(const rid_plan_s* p);
 // changed in place (same shape and row count).
 cudaError_t rid_tc_refresh_omega_fp64(const rid_plan_s* p);
 
+// Digit tiles of nrows rows of Omega' (rows 2i, 2i + 1 of each complex row),
+// as the exact-slice products read them: [N-tile][K stage][digit] tiles of
+// tile_w rows x 32 bf16 in the 64-byte swizzle (pairs: [half] before
+// [digit]), and the row exponents om_exp[2 nrows].  Rows past 2 nrows are
+// left as the caller set them.
+cudaError_t rid_tc_cut_omega(const double2* om, int64_t ldo, int64_t m, int nrows, int64_t KP, int tile_w, bool pair,
+                             int* om_exp, uint16_t* tiles, int num_sms, cudaStream_t stream);
+// K-splits of NC chunks so that `units` CTAs (or clusters) per split fill whole
+// waves of `slots` resident ones.
+int rid_tc_choose_ksplit(int units, int NC, int slots);
+
 // out[0] = |R(0,0)|, out[1] = max_{c >= k} ||Y(k:l-1, c)|| of a selected Y (device doubles).
 cudaError_t rid_launch_tail_ratio(const rid_plan_s* p, const double2* Y, int64_t ldy, double* out);
 // est / upper from X of the last sketch, perm and T, into p->err_out.

@@ -50,7 +50,6 @@ namespace {
 struct TcState {
   int S;
   int row0, nrows;        // the rows of Omega this state multiplies
-  bool a_c64;             // A is complex64 (converted exactly to FP64 before slicing)
   int nstages;            // pipeline stages that fit in shared memory
   uint32_t stage_smem, o_off, o_tile_smem;   // o_tile_smem: tile_w (pairs: tile_w / 2) rows x 64 bytes
   int dyn_smem;           // dynamic shared memory of the product kernel
@@ -542,6 +541,19 @@ int choose_ksplit(int units, int NC, int sms) {
 
 }  // namespace
 
+int rid_tc_choose_ksplit(int units, int NC, int slots) { return choose_ksplit(units, NC, slots); }
+
+cudaError_t rid_tc_cut_omega(const double2* om, int64_t ldo, int64_t m, int nrows, int64_t KP, int tile_w, bool pair,
+                             int* om_exp, uint16_t* tiles, int num_sms, cudaStream_t stream) {
+  omega_exp_kernel<<<nrows, 256, 0, stream>>>(om, ldo, m, om_exp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int64_t blocks = ((int64_t)nrows * (KP / 2) + 255) / 256;
+  if (blocks > (int64_t)num_sms * 32) blocks = (int64_t)num_sms * 32;
+  omega_slice_kernel<<<(unsigned)blocks, 256, 0, stream>>>(om, ldo, m, nrows, KP, tile_w, pair, om_exp, tiles);
+  return cudaGetLastError();
+}
+
 void rid_tc_plan_free_fp64(rid_plan_s* p);
 
 // dry_run: compute p->tc_bytes (the device bytes the state needs) and return
@@ -557,7 +569,7 @@ void tc_free_state(rid_plan_s* p, TcState* st) {
 // A tensor-core state for rows row0 .. row0 + nrows - 1 of Omega: their digit
 // tiles, the A digit tile buffer, exponents and partial sums.  dry_run: only
 // the device bytes.
-rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64, TcState** out,
+rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, TcState** out,
                     size_t* bytes_out) {
   *out = nullptr;
   TcState* st = (TcState*)calloc(1, sizeof(TcState));
@@ -565,7 +577,6 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
   st->S = TC_S;
   st->row0 = row0;
   st->nrows = nrows;
-  st->a_c64 = a_c64;
   // a rounded Omega holds omega_bits / 8 digits relative to its row exponent,
   // the same exponent omega_exp_kernel takes, so the others are exactly zero
   st->so = p->omega_bits > 0 ? (p->omega_bits + 7) / 8 : TC_S;
@@ -672,18 +683,9 @@ rid_status tc_setup(rid_plan_s* p, int dry_run, int row0, int nrows, bool a_c64,
 
   cudaError_t e = cudaMemsetAsync(st->err, 0, 4, p->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(st->om_slices, 0, om_bytes, p->stream);   // padding rows
-  if (e == cudaSuccess) {
-    omega_exp_kernel<<<nrows, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m, st->om_exp);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) {
-    int64_t blocks = ((int64_t)nrows * (st->KP / 2) + 255) / 256;
-    if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m,
-                                                                 nrows, st->KP, st->tile_w, st->pair,
-                                                                 st->om_exp, st->om_slices);
-    e = cudaGetLastError();
-  }
+  if (e == cudaSuccess)
+    e = rid_tc_cut_omega(p->omega + (int64_t)row0 * p->ldo, p->ldo, p->m, nrows, st->KP, st->tile_w, st->pair,
+                         st->om_exp, st->om_slices, p->num_sms, p->stream);
   const void* fn = st->pair ? (const void*)sketch_tc_kernel<true> : (const void*)sketch_tc_kernel<false>;
   if (e == cudaSuccess) e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_DYN_SMEM_MAX);
   if (e == cudaSuccess) {
@@ -711,7 +713,7 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   if (p->mode != RID_FP64_EMULATED || p->dtype != RID_C128) return RID_EUNSUPPORTED;
   TcState* st = nullptr;
   size_t bytes = 0;
-  const rid_status s = tc_setup(p, dry_run, 0, p->ls, false, &st, &bytes);   // the test matrix and the row probes
+  const rid_status s = tc_setup(p, dry_run, 0, p->ls, &st, &bytes);   // the test matrix and the row probes
   if (s != RID_OK) return s;
   p->tc_bytes = bytes;
   if (!dry_run) {
@@ -727,24 +729,6 @@ void rid_tc_plan_free_fp64(rid_plan_s* p) {
   p->tc_bytes = 0;
 }
 
-// Mixed-precision plans with row probes: an FP64-emulated state for the probe
-// rows alone, multiplied into X from the complex64 A (exact in FP64), so the
-// error estimate keeps FP64 grade while Y takes the BF16x3 product.
-rid_status rid_tc_probe_init(rid_plan_s* p) {
-  TcState* st = nullptr;
-  size_t bytes = 0;
-  const rid_status s = tc_setup(p, 0, p->l, p->nrow, p->dtype == RID_C64, &st, &bytes);
-  if (s != RID_OK) return s;
-  p->tc_probe_state = st;
-  p->tc_probe_bytes = bytes;
-  return RID_OK;
-}
-
-void rid_tc_probe_free(rid_plan_s* p) {
-  tc_free_state(p, (TcState*)p->tc_probe_state);
-  p->tc_probe_state = nullptr;
-  p->tc_probe_bytes = 0;
-}
 
 namespace {
 
@@ -778,12 +762,7 @@ cudaError_t tc_sketch(const rid_plan_s* p, const TcState* st, const void* A_, in
       const int64_t n_pad = st->pair ? (pcols + 255) / 256 * 256 : (pcols + 127) / 128 * 128;
       int64_t blocks = n_pad / 8 * (int64_t)st->NC;          // a block per 8 columns of one chunk
       if (blocks > (int64_t)p->num_sms * 16) blocks = (int64_t)p->num_sms * 16;
-      if (st->a_c64)
-        a_slice_kernel<float2><<<(unsigned)blocks, 256, 0, p->stream>>>(
-            (const float2*)A_ + c0 * lda, lda, p->m, pcols, n_pad, st->NC, st->a_slices, st->a_exp + c0 * st->NC,
-            st->a_exp_max + c0);
-      else
-        a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
+      a_slice_kernel<double2><<<(unsigned)blocks, 256, 0, p->stream>>>(
             (const double2*)A_ + c0 * lda, lda, p->m, pcols, n_pad, st->NC, st->a_slices, st->a_exp + c0 * st->NC,
             st->a_exp_max + c0);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -841,16 +820,6 @@ cudaError_t rid_tc_sketch_fp64(const rid_plan_s* p, const void* A_, int64_t lda,
   return rid_tc_sketch_cols_fp64(p, A_, lda, Y, ldy, 0, p->n);
 }
 
-// X = G A for a mixed-precision plan's row probes (every row goes to X),
-// columns col0 .. col0 + ncols - 1.
-cudaError_t rid_tc_probe_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda, int64_t col0, int64_t ncols) {
-  return tc_sketch(p, (const TcState*)p->tc_probe_state, A_, lda, nullptr, 0, 0, p->xrow, p->nrow, col0, ncols,
-                   false);
-}
-
-cudaError_t rid_tc_probe_sketch(const rid_plan_s* p, const void* A_, int64_t lda) {
-  return rid_tc_probe_sketch_cols(p, A_, lda, 0, p->n);
-}
 
 namespace {
 int state_error_word(const rid_plan_s* p, const TcState* st) {
@@ -864,7 +833,6 @@ int state_error_word(const rid_plan_s* p, const TcState* st) {
 
 int rid_tc_error_word_fp64(const rid_plan_s* p) { return state_error_word(p, (const TcState*)p->tc_state); }
 
-int rid_tc_probe_error_word(const rid_plan_s* p) { return state_error_word(p, (const TcState*)p->tc_probe_state); }
 
 rid_status rid_tc_plan_init_fp64(rid_plan_s* p) { return rid_tc_plan_setup_fp64(p, 0); }
 
@@ -873,13 +841,6 @@ cudaError_t rid_tc_refresh_omega_fp64(const rid_plan_s* p) {
   if (!st) return cudaErrorNotSupported;
   // the rows of the state (Omega, then the row probes), cut as at plan time;
   // the padding rows of the tiles keep the zeros of the setup
-  omega_exp_kernel<<<st->nrows, 256, 0, p->stream>>>(p->omega + (int64_t)st->row0 * p->ldo, p->ldo, p->m, st->om_exp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  int64_t blocks = ((int64_t)st->nrows * (st->KP / 2) + 255) / 256;
-  if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-  omega_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(p->omega + (int64_t)st->row0 * p->ldo, p->ldo, p->m,
-                                                               st->nrows, st->KP, st->tile_w, st->pair, st->om_exp,
-                                                               st->om_slices);
-  return cudaGetLastError();
+  return rid_tc_cut_omega(p->omega + (int64_t)st->row0 * p->ldo, p->ldo, p->m, st->nrows, st->KP, st->tile_w,
+                          st->pair, st->om_exp, st->om_slices, p->num_sms, p->stream);
 }

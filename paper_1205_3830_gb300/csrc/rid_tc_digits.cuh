@@ -145,6 +145,17 @@ __device__ __forceinline__ void digit_words(double2 x, int e, uint32_t (&w)[TC_S
 #undef RID_DIGIT_PAIR
 }
 
+// exp_of of a float converted to double (exact), from the float bits: a
+// float is its 24-bit significand times 2^(ex - 150), or the raw field times
+// 2^-149 when subnormal; infinities and NaNs take their double's exponent.
+__device__ __forceinline__ int exp_of_f(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int ex = (int)((b >> 23) & 0xFF);
+  const uint32_t mant = b & 0x7FFFFFu;
+  if (ex == 0) return mant ? (32 - __clz((int)mant)) - 149 : TC_EXP_ZERO;
+  return ex == 255 ? 1025 : ex - 126;
+}
+
 __device__ __forceinline__ int group_of(int d) { return d >= 3 ? 3 : d; }
 
 // Descriptor of a tile of TC_KS bf16 per row (the swizzle of tile_offset).

@@ -87,6 +87,8 @@ def test_calls_reject_null_plan(lib):
     assert lib.rid_sync_status(None) == E
     assert lib.rid_plan_set_omega(None, None, 1) == E
     assert lib.rid_plan_set_select_grid(None, 0) == E
+    ptr, ld = ctypes.c_void_p(), ctypes.c_int64()
+    assert lib.rid_plan_probe_products(None, ctypes.byref(ptr), ctypes.byref(ld)) == E
     assert lib.rid_plan_destroy(None) == _native.RID_OK
 
 

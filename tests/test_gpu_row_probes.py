@@ -20,7 +20,7 @@ import torch
 
 import oracle
 import synth
-from gpu_util import row_probe_tolerances, to_dev_colmajor, to_host
+from gpu_util import dot_bound, row_probe_tolerances, to_dev_colmajor, to_host
 
 pytestmark = pytest.mark.gpu
 
@@ -222,3 +222,94 @@ def test_plan_created_with_probes_matches_set_probes(rid, mode):
     (Ya, pa, Ta, ea), (Yb, pb, Tb, eb) = outs
     assert np.array_equal(Ya, Yb) and np.array_equal(pa, pb) and np.array_equal(Ta, Tb)
     assert ea == eb
+
+
+# ---- the probe products X = G A themselves -------------------------------------
+# X is read back through rid_plan_probe_products and compared entry by entry
+# with the oracle's G A (one library product on the upcast A).  Bound: the
+# FP64 dot-product bound, 2^-46 (2m) max|g_q| max|A_j| for the emulated
+# products (56-bit digits, double-FP32 sums), and 1e-14 |G| |A| for the two
+# generators of G.
+def probe_products_bound(G, A):
+    m = A.shape[0]
+    return (dot_bound(G, A) + 2.0 ** -46 * (2 * m) * np.outer(np.abs(G).max(axis=1), np.abs(A).max(axis=0))
+            + 1e-14 * (np.abs(G) @ np.abs(A)))
+
+
+def probe_products(rid, A, mode, nprobe, probe_seed, panel=None):
+    m, n = A.shape
+    dtype = torch.complex64 if mode == "bf16" else torch.complex128
+    k = min(3, m, n)
+    with rid.Plan(m, n, k, k + 2, seed=1, dtype=dtype, mode=mode, nprobe=nprobe, probe_seed=probe_seed) as plan:
+        Ad = to_dev_colmajor(A, dtype)
+        if panel is None:
+            plan.sketch(Ad)
+        else:                                       # column panels, last first
+            Y = rid.colmajor_empty(k + 2, n)
+            for c0 in reversed(range(0, n, panel)):
+                plan.sketch_cols(Ad, Y, c0, min(panel, n - c0))
+        X = to_host(plan.probe_products())
+        plan.sync_status()
+    return X
+
+
+@pytest.mark.parametrize("mode", MODES + ["bf16"])
+@pytest.mark.parametrize("shape,nprobe", [((1000, 777), 8), ((8192, 300), 13), ((333, 129), 1), ((5, 1), 16),
+                                          ((4096, 1030), 16), ((2048, 256), 7)], ids=str)
+def test_probe_products_match_oracle(rid, mode, shape, nprobe):
+    """X = G A of every mode (the mixed mode's from the complex64 A) against
+    the oracle: several column blocks with a ragged last one, K ranges of one
+    and of several chunks with a ragged tail, K-splits (m = 8192), and both
+    widths of the mixed mode's probe kernel (2 nprobe <= 16 and <= 32)."""
+    m, n = shape
+    A = lowrank(m, n, min(5, m, n), eps=1e-3, seed=nprobe)
+    if mode == "bf16":
+        A = A.astype(np.complex64).astype(np.complex128)
+    X = probe_products(rid, A, mode, nprobe, 5)
+    G = oracle.left_probe_matrix(nprobe, m, 5)
+    assert X.shape == (nprobe, n)
+    d = np.abs(X - G @ A)
+    bound = probe_products_bound(G, A)
+    print(f"{mode} {shape} r={nprobe}: max |dX| / bound = {np.max(d / bound):.2e}")
+    assert np.all(d <= bound)
+
+
+def scaled_c64(m, n, direction, seed):
+    """Complex64 A whose chunk exponents change along K (rising or falling by
+    2^12 over the column), with a zero chunk, one column of subnormal floats
+    and one column whose first half is zero."""
+    rng = np.random.default_rng(seed)
+    A = (rng.standard_normal((m, n)) + 1j * rng.standard_normal((m, n))).astype(np.complex128)
+    t = np.arange(m) / m
+    s = 2.0 ** (12 * t if direction == "rising" else 12 * (1 - t))
+    A *= s[:, None]
+    A[1024:1152, :] = 0                      # a whole chunk of zeros
+    A[:, 5] = (1e-40 * (rng.integers(-40, 40, m) + 1j * rng.integers(-40, 40, m)))   # subnormal floats
+    A[: m // 2, 9] = 0
+    return np.asfortranarray(A.astype(np.complex64).astype(np.complex128))
+
+
+@pytest.mark.parametrize("direction", ["rising", "falling"])
+def test_mixed_probe_products_chunk_exponents(rid, direction):
+    """The mixed mode's probe kernel keeps a running exponent per column and
+    K-split: chunk exponents that grow along K (the sums are rescaled), that
+    shrink, zero chunks and subnormal floats, against the oracle."""
+    m, n = 8192, 260
+    A = scaled_c64(m, n, direction, 3)
+    X = probe_products(rid, A, "bf16", 8, 4)
+    G = oracle.left_probe_matrix(8, m, 4)
+    Xo = G @ A
+    d = np.abs(X - Xo)
+    bound = probe_products_bound(G, A)
+    print(f"{direction}: max |dX| / bound = {np.max(d / bound):.2e}")
+    assert np.all(d <= bound)
+    assert np.all(np.abs(Xo[:, 5]) < 1e-36) and np.all(np.abs(X[:, 5] - Xo[:, 5]) <= bound[:, 5])
+
+
+def test_mixed_probe_products_panels(rid):
+    """Column panels of a mixed plan give the one-call X bit for bit."""
+    m, n = 4096, 1000
+    A = lowrank(m, n, 5, eps=1e-3, seed=2).astype(np.complex64).astype(np.complex128)
+    X0 = probe_products(rid, A, "bf16", 8, 3)
+    X1 = probe_products(rid, A, "bf16", 8, 3, panel=384)
+    assert np.array_equal(X0, X1)
