@@ -162,6 +162,9 @@ cudaError_t rid_tc_refresh_omega_fp64(const rid_plan_s* p);
 // left as the caller set them.
 cudaError_t rid_tc_cut_omega(const double2* om, int64_t ldo, int64_t m, int nrows, int64_t KP, int tile_w, bool pair,
                              int* om_exp, uint16_t* tiles, int num_sms, cudaStream_t stream);
+// The chunk exponents of a mixed plan's row-probe state, [*nc][n] (set by
+// the BF16x3 slicer, read by the probe product); null without row probes.
+int* rid_tc_probe_chunk_exp(const rid_plan_s* p, int* nc);
 // K-splits of NC chunks so that `units` CTAs (or clusters) per split fill whole
 // waves of `slots` resident ones.
 int rid_tc_choose_ksplit(int units, int NC, int slots);

@@ -16,6 +16,7 @@
 
 #include "rid_internal.cuh"
 #include "rid_tc.cuh"
+#include "rid_tc_digits.cuh"
 
 using namespace rid_tc;
 
@@ -100,28 +101,56 @@ __device__ __forceinline__ void split3f(float x, uint16_t (&t)[MX_S]) {
 
 // A' columns (complex64 A read as 2m floats), split into 3 terms; zero padding
 // to KP.  A thread takes two consecutive complex entries: two 8-byte loads and
-// one 8-byte store per term.
+// one 8-byte store per term.  With cexp (plans with row probes), the pass also
+// takes the exponent of every chunk of 128 complex rows of every column (the
+// largest entry's, exp_of_f) into cexp[chunk * ldce + column], which the
+// caller set below every exponent: the row probes' product cuts A's digits
+// relative to it (rid_probe_tc.cu).  A warp whose 64 entries lie in one
+// chunk of one column reduces them first; others update entry by entry.
 __global__ void __launch_bounds__(256) mx_a_slice_kernel(const float2* __restrict__ A, int64_t lda, int64_t m,
                                                          int64_t n, int64_t KP, int64_t slice_stride,
-                                                         uint16_t* __restrict__ slices) {
-  // A and slices start at the first of the n columns of the range; the term
-  // planes of the whole matrix are slice_stride apart
+                                                         uint16_t* __restrict__ slices, int* __restrict__ cexp,
+                                                         int64_t ldce) {
+  // A, slices and cexp start at the first of the n columns of the range; the
+  // term planes of the whole matrix are slice_stride apart
   const int64_t per_col = KP / 4;                      // pairs of complex entries per column
   const int64_t total = n * per_col;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = e / per_col, r = 2 * (e - j * per_col);
+  const int lane = threadIdx.x & 31;
+  // whole warps iterate, so the warp-wide steps below see every lane
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < total;
+       e0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = e0 + lane;
+    const bool act = e < total;
+    const int64_t j = act ? e / per_col : 0, r = act ? 2 * (e - j * per_col) : 0;
     const float2* col = A + j * lda;
-    const float2 x0 = r < m ? __ldcs(col + r) : make_float2(0.f, 0.f);
-    const float2 x1 = r + 1 < m ? __ldcs(col + r + 1) : make_float2(0.f, 0.f);
-    uint16_t re0[MX_S], im0[MX_S], re1[MX_S], im1[MX_S];
-    split3f(x0.x, re0);
-    split3f(x0.y, im0);
-    split3f(x1.x, re1);
-    split3f(x1.y, im1);
+    const float2 x0 = act && r < m ? __ldcs(col + r) : make_float2(0.f, 0.f);
+    const float2 x1 = act && r + 1 < m ? __ldcs(col + r + 1) : make_float2(0.f, 0.f);
+    if (act) {
+      uint16_t re0[MX_S], im0[MX_S], re1[MX_S], im1[MX_S];
+      split3f(x0.x, re0);
+      split3f(x0.y, im0);
+      split3f(x1.x, re1);
+      split3f(x1.y, im1);
 #pragma unroll
-    for (int s = 0; s < MX_S; ++s) {
-      const uint2 w = make_uint2((uint32_t)re0[s] | ((uint32_t)im0[s] << 16), (uint32_t)re1[s] | ((uint32_t)im1[s] << 16));
-      *(uint2*)(slices + s * slice_stride + j * KP + 2 * r) = w;
+      for (int s = 0; s < MX_S; ++s) {
+        const uint2 w = make_uint2((uint32_t)re0[s] | ((uint32_t)im0[s] << 16), (uint32_t)re1[s] | ((uint32_t)im1[s] << 16));
+        *(uint2*)(slices + s * slice_stride + j * KP + 2 * r) = w;
+      }
+    }
+    if (cexp) {
+      // |x| orders as the bit pattern of |x| does
+      uint32_t mx = max(max(__float_as_uint(x0.x) & 0x7FFFFFFFu, __float_as_uint(x0.y) & 0x7FFFFFFFu),
+                        max(__float_as_uint(x1.x) & 0x7FFFFFFFu, __float_as_uint(x1.y) & 0x7FFFFFFFu));
+      const int c = (int)(r >> 7);
+      const int64_t j_first = __shfl_sync(0xffffffffu, j, 0);    // every lane takes part in both
+      const int c_first = __shfl_sync(0xffffffffu, c, 0);
+      const bool one = __all_sync(0xffffffffu, act && j == j_first && c == c_first);
+      if (one) {
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) atomicMax(cexp + c * ldce + j, exp_of_f(__uint_as_float(mx)));
+      } else if (act) {
+        atomicMax(cexp + c * ldce + j, exp_of_f(__uint_as_float(mx)));
+      }
     }
   }
 }
@@ -400,8 +429,15 @@ cudaError_t rid_mx_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda,
     const int64_t total = ncols * (st->KP / 4);
     int64_t blocks = (total + 255) / 256;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
+    // with row probes, the chunk exponents of these columns, from below every exponent
+    int nc = 0;
+    int* cexp = p->nrow > 0 ? rid_tc_probe_chunk_exp(p, &nc) : nullptr;
+    if (cexp && (e = cudaMemset2DAsync(cexp + col0, (size_t)p->n * 4, 0x80, (size_t)ncols * 4, (size_t)nc,
+                                       p->stream)) != cudaSuccess)
+      return e;
     mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, ncols, st->KP, p->n * st->KP,
-                                                              st->a_slices + col0 * st->KP);
+                                                              st->a_slices + col0 * st->KP,
+                                                              cexp ? cexp + col0 : nullptr, p->n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   if (p->timing) cudaEventRecord(p->ev[1], p->stream);
