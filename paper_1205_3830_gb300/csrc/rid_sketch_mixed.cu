@@ -100,57 +100,62 @@ __device__ __forceinline__ void split3f(float x, uint16_t (&t)[MX_S]) {
 }
 
 // A' columns (complex64 A read as 2m floats), split into 3 terms; zero padding
-// to KP.  A thread takes two consecutive complex entries: two 8-byte loads and
-// one 8-byte store per term.  With cexp (plans with row probes), the pass also
-// takes the exponent of every chunk of 128 complex rows of every column (the
-// largest entry's, exp_of_f) into cexp[chunk * ldce + column], which the
-// caller set below every exponent: the row probes' product cuts A's digits
-// relative to it (rid_probe_tc.cu).  A warp whose 64 entries lie in one
-// chunk of one column reduces them first; others update entry by entry.
+// to KP.  A warp takes one chunk of 128 complex rows of one column, lane l
+// the rows 4l .. 4l + 3: 8-byte or (every column 16-byte aligned: vec) 16-byte
+// loads and one 16-byte store per term.  With cexp (plans with row probes),
+// the warp also stores the chunk's exponent (the largest entry's, exp_of_f)
+// at cexp[chunk * ldce + column]: the row probes' product cuts A's digits
+// relative to it (rid_probe_tc.cu).  Every chunk of every column of the range
+// is written.
 __global__ void __launch_bounds__(256) mx_a_slice_kernel(const float2* __restrict__ A, int64_t lda, int64_t m,
-                                                         int64_t n, int64_t KP, int64_t slice_stride,
+                                                         int64_t n, int64_t KP, int64_t slice_stride, bool vec,
                                                          uint16_t* __restrict__ slices, int* __restrict__ cexp,
                                                          int64_t ldce) {
   // A, slices and cexp start at the first of the n columns of the range; the
   // term planes of the whole matrix are slice_stride apart
-  const int64_t per_col = KP / 4;                      // pairs of complex entries per column
-  const int64_t total = n * per_col;
+  const int64_t rows_p = KP / 2;                      // complex rows with the padding (a multiple of 16)
+  const int64_t cpc = (rows_p + 127) / 128;           // chunks per column
+  const int64_t units = n * cpc;
   const int lane = threadIdx.x & 31;
-  // whole warps iterate, so the warp-wide steps below see every lane
-  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); e0 < total;
-       e0 += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t e = e0 + lane;
-    const bool act = e < total;
-    const int64_t j = act ? e / per_col : 0, r = act ? 2 * (e - j * per_col) : 0;
-    const float2* col = A + j * lda;
-    const float2 x0 = act && r < m ? __ldcs(col + r) : make_float2(0.f, 0.f);
-    const float2 x1 = act && r + 1 < m ? __ldcs(col + r + 1) : make_float2(0.f, 0.f);
-    if (act) {
-      uint16_t re0[MX_S], im0[MX_S], re1[MX_S], im1[MX_S];
-      split3f(x0.x, re0);
-      split3f(x0.y, im0);
-      split3f(x1.x, re1);
-      split3f(x1.y, im1);
+  const int64_t wstride = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < units; u += wstride) {
+    const int64_t j = u / cpc;
+    const int c = (int)(u - j * cpc);
+    const int64_t r0 = (int64_t)c * 128 + 4 * lane;
+    const float2* col = A + j * lda + r0;
+    float2 x[4];
+    if (vec && r0 + 4 <= m) {
+      const float4 f0 = __ldcs((const float4*)col), f1 = __ldcs((const float4*)col + 1);
+      x[0] = make_float2(f0.x, f0.y);
+      x[1] = make_float2(f0.z, f0.w);
+      x[2] = make_float2(f1.x, f1.y);
+      x[3] = make_float2(f1.z, f1.w);
+    } else {
 #pragma unroll
-      for (int s = 0; s < MX_S; ++s) {
-        const uint2 w = make_uint2((uint32_t)re0[s] | ((uint32_t)im0[s] << 16), (uint32_t)re1[s] | ((uint32_t)im1[s] << 16));
-        *(uint2*)(slices + s * slice_stride + j * KP + 2 * r) = w;
+      for (int q = 0; q < 4; ++q) x[q] = r0 + q < m ? __ldcs(col + q) : make_float2(0.f, 0.f);
+    }
+    if (r0 < rows_p) {                                 // rows_p is a multiple of 4: all four or none
+      uint32_t w[MX_S][4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint16_t re[MX_S], im[MX_S];
+        split3f(x[q].x, re);
+        split3f(x[q].y, im);
+#pragma unroll
+        for (int s = 0; s < MX_S; ++s) w[s][q] = (uint32_t)re[s] | ((uint32_t)im[s] << 16);
       }
+#pragma unroll
+      for (int s = 0; s < MX_S; ++s)
+        *(uint4*)(slices + s * slice_stride + j * KP + 2 * r0) = make_uint4(w[s][0], w[s][1], w[s][2], w[s][3]);
     }
     if (cexp) {
       // |x| orders as the bit pattern of |x| does
-      uint32_t mx = max(max(__float_as_uint(x0.x) & 0x7FFFFFFFu, __float_as_uint(x0.y) & 0x7FFFFFFFu),
-                        max(__float_as_uint(x1.x) & 0x7FFFFFFFu, __float_as_uint(x1.y) & 0x7FFFFFFFu));
-      const int c = (int)(r >> 7);
-      const int64_t j_first = __shfl_sync(0xffffffffu, j, 0);    // every lane takes part in both
-      const int c_first = __shfl_sync(0xffffffffu, c, 0);
-      const bool one = __all_sync(0xffffffffu, act && j == j_first && c == c_first);
-      if (one) {
-        mx = __reduce_max_sync(0xffffffffu, mx);
-        if (lane == 0) atomicMax(cexp + c * ldce + j, exp_of_f(__uint_as_float(mx)));
-      } else if (act) {
-        atomicMax(cexp + c * ldce + j, exp_of_f(__uint_as_float(mx)));
-      }
+      uint32_t mx = 0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        mx = max(mx, max(__float_as_uint(x[q].x) & 0x7FFFFFFFu, __float_as_uint(x[q].y) & 0x7FFFFFFFu));
+      mx = __reduce_max_sync(0xffffffffu, mx);
+      if (lane == 0) cexp[c * ldce + j] = exp_of_f(__uint_as_float(mx));
     }
   }
 }
@@ -426,16 +431,14 @@ cudaError_t rid_mx_sketch_cols(const rid_plan_s* p, const void* A_, int64_t lda,
   }
   cudaError_t e;
   {
-    const int64_t total = ncols * (st->KP / 4);
-    int64_t blocks = (total + 255) / 256;
+    const int64_t units = ncols * ((st->KP / 2 + 127) / 128);   // a warp per chunk of a column
+    int64_t blocks = (units + 7) / 8;
     if (blocks > (int64_t)p->num_sms * 32) blocks = (int64_t)p->num_sms * 32;
-    // with row probes, the chunk exponents of these columns, from below every exponent
+    // with row probes, also the chunk exponents of these columns
     int nc = 0;
     int* cexp = p->nrow > 0 ? rid_tc_probe_chunk_exp(p, &nc) : nullptr;
-    if (cexp && (e = cudaMemset2DAsync(cexp + col0, (size_t)p->n * 4, 0x80, (size_t)ncols * 4, (size_t)nc,
-                                       p->stream)) != cudaSuccess)
-      return e;
-    mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, ncols, st->KP, p->n * st->KP,
+    const bool vec = ((uintptr_t)A_ & 15u) == 0 && lda % 2 == 0;
+    mx_a_slice_kernel<<<(unsigned)blocks, 256, 0, p->stream>>>(A, lda, p->m, ncols, st->KP, p->n * st->KP, vec,
                                                               st->a_slices + col0 * st->KP,
                                                               cexp ? cexp + col0 : nullptr, p->n);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
