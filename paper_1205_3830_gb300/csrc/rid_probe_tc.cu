@@ -17,14 +17,14 @@
 //
 // Seven MMAs per K16 step instead of 28.  G' has only 2 r <= 32 rows (W rows
 // per digit, W = 16 or 32), so a product of one A digit tile t with one G
-// digit block s is a narrow MMA.  Each stage's G digit blocks sit in shared
-// memory behind six zero blocks: B_t = [0 (t blocks), G_0, ..., G_(6-t)]
-// (7 W rows) starts (6 - t) blocks before G_0.  One MMA A_t x B_t (N = 7 W)
-// adds the product of digit pair (s, t) to columns W (s + t) .. of the
-// accumulator, so column block d holds diagonal d = s + t; the pairs with
-// s + t > 6 are not formed, as in the wide product.  Every diagonal has its
-// own columns (the wide product shares one group for d >= 3), which keeps
-// every chunk sum of a diagonal exact.
+// digit block s is a narrow MMA.  Each stage's G digit blocks sit one after
+// the other in shared memory, so B_t = [G_0, ..., G_(6-t)] is one operand of
+// W (7 - t) rows; one MMA A_t x B_t, whose accumulator starts at column W t,
+// adds the product of digit pair (s, t) to columns W (s + t) .. + W - 1.  So
+// column block d holds diagonal d = s + t, and the pairs with s + t > 6 are
+// not formed, as in the wide product.  Every diagonal has its own columns
+// (the wide product shares one group for d >= 3), which keeps every chunk
+// sum of a diagonal exact.
 //
 // Each CTA keeps its own running exponent per column (the largest chunk
 // exponent it has seen; the double-FP32 sums are rescaled by a power of two
@@ -48,10 +48,9 @@ constexpr int PB_RAW_ROWS = 16;              // complex rows of A per K stage
 constexpr uint32_t PB_RAW_BYTES = 128 * PB_RAW_ROWS * 8;   // one raw stage: 128 columns x 128 bytes
 
 // Shared memory of one digit stage: seven A digit tiles (128 rows x 64
-// bytes), six zero blocks and seven G digit blocks of W rows x 64 bytes.
+// bytes), then seven G digit blocks of W rows x 64 bytes.
 __host__ __device__ constexpr uint32_t pb_block_bytes(int W) { return (uint32_t)W * TC_KS * 2; }
-__host__ __device__ constexpr uint32_t pb_zero_off() { return (uint32_t)(TC_S * TC_TILE_BYTES); }
-__host__ __device__ constexpr uint32_t pb_om_off(int W) { return pb_zero_off() + (TC_S - 1) * pb_block_bytes(W); }
+__host__ __device__ constexpr uint32_t pb_om_off(int) { return (uint32_t)(TC_S * TC_TILE_BYTES); }
 __host__ __device__ constexpr uint32_t pb_om_bytes(int W) { return TC_S * pb_block_bytes(W); }
 __host__ __device__ constexpr uint32_t pb_slot_bytes(int W) { return (pb_om_off(W) + pb_om_bytes(W) + 1023) / 1024 * 1024; }
 // raw stages: what shared memory holds after the digit stages (2 KB for the
@@ -177,8 +176,8 @@ probe_tc_kernel(const __grid_constant__ CUtensorMap map_a, PbArgs a) {
   constexpr int NS = PB_NS, R = pb_raw_stages(W);
   constexpr int FW = pb_flush_warps(W);
   constexpr int SLICER0 = FW, PRODUCER = FW + PB_SLICE_WARPS, MMA = PRODUCER + 1;
-  constexpr uint32_t SLOT = pb_slot_bytes(W), ZOFF = pb_zero_off(), OOFF = pb_om_off(W), OBYTES = pb_om_bytes(W);
-  constexpr uint32_t BLK = pb_block_bytes(W), ROFF = pb_raw_off(W);
+  constexpr uint32_t SLOT = pb_slot_bytes(W), OOFF = pb_om_off(W), OBYTES = pb_om_bytes(W);
+  constexpr uint32_t ROFF = pb_raw_off(W);
   static_assert(N <= 256 && N % 16 == 0, "MMA N");
   static_assert(R >= 2, "two raw stages at least");
   static_assert(PB_SLICE_WARPS == 16, "a slicer thread per 16-byte piece of a stage row");
@@ -267,7 +266,6 @@ probe_tc_kernel(const __grid_constant__ CUtensorMap map_a, PbArgs a) {
     }
   } else if (warp == MMA) {
     // ---------------- MMA issuer ----------------
-    const uint32_t idesc = idesc_bf16_f32(128, N);
     for (int it = 0; it < iters && !s_abort; ++it) {
       const int cl = it / TC_SPC, b = it - cl * TC_SPC, g = cl % NB, ds = it % NS;
       if (!__all_sync(0xffffffffu, mbar_wait(&full_bar[ds], (it / NS) & 1, TC_WAIT_BUDGET))) {
@@ -281,13 +279,14 @@ probe_tc_kernel(const __grid_constant__ CUtensorMap map_a, PbArgs a) {
       }
       tc_fence_after();
       unsigned char* base = smem + ds * SLOT;
+      const uint64_t db = tile_desc(base + OOFF);                   // B_t = G_0 .. G_(6-t)
 #pragma unroll
       for (int t = 0; t < TC_S; ++t) {
         const uint64_t da = tile_desc(base + t * TC_TILE_BYTES);
-        const uint64_t db = tile_desc(base + ZOFF + (TC_S - 1 - t) * BLK);   // B_t: t zero blocks, then G_0 ..
+        const uint32_t idesc = idesc_bf16_f32(128, W * (TC_S - t));
 #pragma unroll
         for (int kk = 0; kk < TC_KS / 16; ++kk)
-          mma_bf16_w(tmem + (uint32_t)(g * BUF), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
+          mma_bf16_w(tmem + (uint32_t)(g * BUF + W * t), da + (uint64_t)(2 * kk), db + (uint64_t)(2 * kk), idesc,
                      (b == 0 && t == 0 && kk == 0) ? 0u : 1u);
       }
       mma_commit_w(&empty_bar[ds]);
@@ -301,11 +300,6 @@ probe_tc_kernel(const __grid_constant__ CUtensorMap map_a, PbArgs a) {
     const int64_t j = jbase + jl;
     const bool j_ok = j < a.j_end;
     const float2* col = a.A + (j_ok ? j : 0) * a.lda;
-    // the zero blocks of both digit stages (generic stores, read by the MMAs:
-    // the proxy fence before each stage's arrival covers them)
-    for (int s = 0; s < NS; ++s)
-      for (uint32_t o = (uint32_t)ti * 16; o < (TC_S - 1) * BLK; o += 32 * PB_SLICE_WARPS * 16)
-        *(uint4*)(smem + s * SLOT + ZOFF + o) = make_uint4(0u, 0u, 0u, 0u);
     // the chunk exponent of this thread's column, a chunk ahead
     auto chunk_exp = [&](int cl) { return (j_ok && cl < nchunks) ? __ldg(a.cexp + (c_begin + cl) * a.n + j) : TC_EXP_ZERO; };
     const int pc = (q4 ^ ((jl >> 1) & 3)) << 4;  // the piece's swizzled place in its row
