@@ -156,7 +156,8 @@ __device__ __forceinline__ void digit_words_fp(float2 x, float sc, uint32_t (&w)
 __device__ __forceinline__ float pow2f_or_zero(int k) { return k >= -126 ? __int_as_float((127 + k) << 23) : 0.f; }
 
 // A 2-D tensor copy of rows x .. x + 15 of columns y .. y + 127 of A (8-byte
-// elements) into a raw stage: 128 rows of 128 bytes, column after column;
+// elements) into a raw stage: 128 rows of 128 bytes, column after column, in
+// the 128-byte swizzle (so the slicers' reads are free of bank conflicts);
 // out-of-range rows and columns arrive as zeros.
 __device__ __forceinline__ void tma_load_raw(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
   asm volatile(
@@ -319,8 +320,10 @@ probe_tc_kernel(const __grid_constant__ CUtensorMap map_a, PbArgs a) {
           if (lane == 0) fail(43);
           break;
         }
-        const float4* rp = (const float4*)(smem + ROFF + rs * PB_RAW_BYTES + jl * (PB_RAW_ROWS * 8) + q4 * 32);
-        const float4 f0 = rp[0], f1 = rp[1];
+        // the copy's 128-byte swizzle: 16-byte piece c of column jl sits at c ^ (jl % 8)
+        const unsigned char* row = smem + ROFF + rs * PB_RAW_BYTES + jl * (PB_RAW_ROWS * 8);
+        const float4 f0 = *(const float4*)(row + (((2 * q4) ^ (jl & 7)) << 4));
+        const float4 f1 = *(const float4*)(row + (((2 * q4 + 1) ^ (jl & 7)) << 4));
         x[0] = make_float2(f0.x, f0.y);
         x[1] = make_float2(f0.z, f0.w);
         x[2] = make_float2(f1.x, f1.y);
@@ -464,7 +467,8 @@ const void* probe_kernel_fn(int W, bool tma) {
 }
 
 // The tensor map of A for the raw stages: A as m x n 8-byte elements (columns
-// lda apart), boxes of 16 rows x 128 columns.  False if A's base or column
+// lda apart), boxes of 16 rows x 128 columns, 128-byte swizzle (the raw
+// stages start on 1024-byte boundaries).  False if A's base or column
 // stride is not 16-byte aligned (the slicers then load A themselves).
 bool make_map_a(CUtensorMap* map, const void* A, int64_t lda, int64_t m, int64_t n) {
   if (((uintptr_t)A & 15u) != 0 || lda % 2 != 0) return false;
@@ -483,7 +487,7 @@ bool make_map_a(CUtensorMap* map, const void* A, int64_t lda, int64_t m, int64_t
   cuuint32_t box[2] = {PB_RAW_ROWS, 128};
   cuuint32_t es[2] = {1, 1};
   return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, (void*)A, gdim, gstride, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-             CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
