@@ -33,14 +33,13 @@ METRIC = "complex ID GB-of-A/s & fraction of roofline; served IDs/s at p99 laten
 # FP64 FMA peak of GB300 from unit counts and clocks: 152 SMs x 2 DFMA/clock
 # x 2 flops x 2.07 GHz maximum SM clock (a DFMA probe measured 1.20 TF/s).
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
-# DRAM traffic of one sketch_tc_kernel launch from an ncu capture (profiles/),
-# valid only for the kernel source it was taken on (hash of rid_sketch_tc.cu).
-# DRAM bytes of one product launch of the 32 GiB workload (one column panel of
-# 2048 columns): the 65536 x 2048 capture of profiles/sketch_tc_kernel_65536x2048.md,
-# 4 x (4.896 + 0.127) GB, scaled by the panel's 4x rows; reported only for the
-# source it was measured on
+# DRAM bytes of one sketch_tc_kernel launch of the 32 GiB workload (one column
+# panel of 2048 columns): the 65536 x 2048 capture of
+# profiles/sketch_tc_kernel_65536x2048.md, 4 x (4.897 + 0.129) GB, scaled by
+# the panel's 4x rows; reported only for the sources it was measured on (hash
+# of rid_sketch_tc.cu, rid_tc_digits.cuh and rid_tc.cuh)
 TC_TRAFFIC = {"bytes_per_launch": 20.11e9,
-              "source_sha1": "58cf1dd9ee758232488a32aa59e7c8015435e2ce"}
+              "source_sha1": "850bc0de193cd7922e9877d38e80aa660ccd4976"}
 
 
 TC_SOURCES = ("rid_sketch_tc.cu", "rid_tc_digits.cuh", "rid_tc.cuh")     # the product kernel's source
@@ -371,7 +370,11 @@ def run_ours(args, cfg, world, rank, local):
         "gflops": world * (sketch_flops + 16.0 * n * (l * k - k * k / 2) + 4.0 * k * k * (n - k) +
                            (8.0 * k * (n - k) * args.nprobe if rows else 8.0 * m * n * args.nprobe)) / (ms_step / 1e3) / 1e9,
         "step_ms": per,
-        "sketch_kernel_ms": {"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2]},
+        "sketch_kernel_ms": ({"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2]} if args.mode != "bf16" else
+                             {"slice": k_ms[0], "product": k_ms[1], "reduce": k_ms[2],
+                              # the rest of the sketch: the row probes' own product (digits of
+                              # A cut on chip) and its reduction
+                              "probe_rows": max(0.0, per["sketch"] - k_ms[0] - k_ms[1] - k_ms[2])}),
         "gpu_launches": launches,
         "error_estimate": {"est": est, "upper": upper,
                            "estimator": ("row probes multiplied in the sketch's pass over A" if rows

@@ -652,7 +652,9 @@ rid_status rid_plan_set_select_grid(rid_plan_t p, int32_t ctas) {
 
 rid_status rid_plan_stats(rid_plan_t p, int64_t out[8]) {
   if (!p || !out) return RID_EINVAL;
-  out[0] = p->mode == RID_FP64_NATIVE ? (p->split_k > 1 ? 2 : 1) : p->tc_sketch_launches;
+  // a mixed plan's row probes add their product and its reduction
+  out[0] = p->mode == RID_FP64_NATIVE ? (p->split_k > 1 ? 2 : 1)
+                                      : p->tc_sketch_launches + (p->tc_probe_state ? 2 : 0);
   out[1] = p->sel_grid > 0 ? 1 : 1 + p->k;           // one cooperative launch, or one per step
   out[2] = p->n > p->k ? 1 : 0;
   out[3] = p->n > p->k ? 6 : 5;

@@ -718,7 +718,8 @@ rid_status rid_tc_plan_setup_fp64(rid_plan_s* p, int dry_run) {
   p->tc_bytes = bytes;
   if (!dry_run) {
     p->tc_state = st;
-    p->tc_sketch_launches = 3;
+    // a whole-matrix sketch: slicing and product per column panel, then the reduction
+    p->tc_sketch_launches = 2 * ((st->nblocks + st->panel_blocks - 1) / st->panel_blocks) + 1;
   }
   return RID_OK;
 }
