@@ -39,7 +39,7 @@ FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 # the panel's 4x rows; reported only for the sources it was measured on (hash
 # of rid_sketch_tc.cu, rid_tc_digits.cuh and rid_tc.cuh)
 TC_TRAFFIC = {"bytes_per_launch": 20.11e9,
-              "source_sha1": "850bc0de193cd7922e9877d38e80aa660ccd4976"}
+              "source_sha1": "c6a5aef34e42c6854aab596daa3b9c8175c2a33d"}
 
 
 TC_SOURCES = ("rid_sketch_tc.cu", "rid_tc_digits.cuh", "rid_tc.cuh")     # the product kernel's source
