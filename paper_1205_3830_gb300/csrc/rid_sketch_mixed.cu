@@ -29,7 +29,8 @@ constexpr int MX_STAGES = 3;
 constexpr int MX_THREADS = 192;            // warp 0 TMA, 1 MMA + TMEM, 2-5 epilogue
 // K stages one FP32 accumulator sums at most (2048 reals): the rounding of the
 // FP32 sums grows with the square root of their length, so the K-split is
-// raised until every split is this short; the splits are summed in FP64.
+// raised until every split is this short; the splits are summed in
+// double-FP32 pairs (mx_reduce_kernel).
 constexpr int MX_MAX_STAGES_PER_SPLIT = 64;
 constexpr long long MX_WAIT_BUDGET = 4000000000ll;
 constexpr int MX_SMEM_MAX = MX_STAGES * MX_S * (128 + 256) * MX_KS * 2 + 1024;   // 222208 bytes
@@ -306,13 +307,32 @@ __global__ void mx_reduce_kernel(const float* __restrict__ partial, int ksplit, 
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t j = j0 + e / l;
     const int i = (int)(e - (j - j0) * l);
-    double re = 0.0, im = 0.0;
-    for (int s = 0; s < ksplit; ++s) {
-      const float* p = partial + ((int64_t)s * n + j) * l2p + 2 * i;
-      re += (double)p[0];
-      im += (double)p[1];
+    // The splits in order, their loads batched ahead of the additions, summed
+    // as double-FP32 pairs (hi + lo; TwoSum keeps each addition's rounding
+    // error): about 48 bits, far below the FP32 grade of the partials, on
+    // the FP32 pipe rather than GB300's narrow FP64 one.
+    float re_h = 0.f, re_l = 0.f, im_h = 0.f, im_l = 0.f;
+    auto two_sum = [](float& h, float& lo, float v) {
+      const float s = __fadd_rn(h, v);
+      const float bp = __fsub_rn(s, h);
+      lo = __fadd_rn(lo, __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(v, bp)));
+      h = s;
+    };
+    const float2* p = (const float2*)(partial + j * l2p) + i;
+    const int64_t split_stride = n * l2p / 2;                     // float2 units
+    for (int s0 = 0; s0 < ksplit; s0 += 8) {
+      float2 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < ksplit) q[u] = __ldcs(p + (int64_t)(s0 + u) * split_stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (s0 + u < ksplit) {
+          two_sum(re_h, re_l, q[u].x);
+          two_sum(im_h, im_l, q[u].y);
+        }
     }
-    Y[i + j * ldy] = make_double2(re, im);
+    Y[i + j * ldy] = make_double2((double)re_h + (double)re_l, (double)im_h + (double)im_l);
   }
 }
 
