@@ -119,10 +119,11 @@ __device__ __forceinline__ void load_rows(const float2* __restrict__ col, int64_
 // multiple of 2^(-8s) (adding and subtracting M = 1.5 2^(23-8s) rounds to
 // that grid, ties to even) and t -= v_s (exact).  So v_0 in [-256, 256],
 // |v_s| <= 2^(-8s) 128, every v_s is exact in BF16, and sum v_s is
-// x 2^(8-e) rounded to 2^-48: the digits the integer cutter of
-// rid_sketch_tc.cu forms, up to a different choice between equal sums and
-// ties of the last digit rounded to even.  Where 2^(8-e) is not a normal
-// float (chunks of subnormals), x is first scaled by part of it.
+// x 2^(8-e) rounded to 2^-48: the value the integer cutter of
+// rid_sketch_tc.cu forms, except at ties of the last digit (to even here,
+// half up in magnitude there), under the same digit bounds.  Where 2^(8-e)
+// is not a normal float (chunks of subnormals), x is first scaled by part
+// of it.
 struct ChunkScale {
   float pre;     // applied to x first when `split`
   float s;       // x (pre) s = x 2^(8-e)
